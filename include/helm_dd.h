@@ -1,0 +1,168 @@
+/*
+ * helm_dd.h -- C ABI of a GB300 (sm_103a) solver for the 2-D/3-D Helmholtz
+ * equation  -Lap u - k^2 u = f,  k = omega / c,  truncated by a PML, with the
+ * double-sweep PML-transmission preconditioner of
+ *
+ *   C. C. Stolk, "A rapidly converging domain decomposition method for the
+ *   Helmholtz equation", arXiv:1208.3956  (Sections 2.1-2.3, Algorithms 1-5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.      The interior grid has n[0] x n[1] (x n[2]) points with spacing h.
+ *            A PML of w_outer points is added outside it on every side, so the
+ *            padded grid has N[a] = n[a] + 2*w_outer points per axis.  The speed
+ *            is clamp-extended into the added layer.
+ * Fields.    rhs / u / in / out are complex128 arrays on the PADDED grid,
+ *            interleaved (re, im) doubles, x fastest, one right-hand side after
+ *            another: element (b, z, y, x) sits at complex offset
+ *            ((b*N[2] + z)*N[1] + y)*N[0] + x   (N[2] = 1 in 2-D).
+ *            Speeds c and gradients are real doubles on the INTERIOR grid, x
+ *            fastest.
+ * Pointers.  Every array argument may be a host pointer or a CUDA device pointer
+ *            (detected per call).  Host arrays are copied in and out inside the
+ *            call.  Buffers are borrowed for the duration of the call only.
+ * Sync.      Calls are synchronous on return.  A handle is not thread-safe;
+ *            separate handles are independent.
+ * Errors.    Every call returns a helm_status and never aborts or throws across
+ *            the ABI.  helm_dd_last_error() gives a human-readable reason for the
+ *            last failure on a handle.
+ * Operator.  A is the paper-form finite-difference operator of Section 2.2
+ *            (5-point in 2-D, 7-point in 3-D; inside a layer
+ *            alpha(x_i)[alpha(x_{i+1/2})(u_{i+1}-u_i) - alpha(x_{i-1/2})(u_i-u_{i-1})]/h^2
+ *            with alpha = 1/(1 + i sigma/omega)); u = 0 one point beyond the
+ *            padded grid.  The PML profile is sigma(d) = sigma0 (d/L)^2 with
+ *            L = w*h and sigma0 = 3 c_ref ln(1e6) / (2L); c_ref defaults to the
+ *            maximum of c.
+ */
+#ifndef HELM_DD_H
+#define HELM_DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_dd helm_dd;   /* opaque; owns all device memory it allocates */
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_EINVAL = -1,     /* invalid argument (sizes, c <= 0 or NaN, omega <= 0, ...) */
+    HELM_ENOMEM = -2,     /* device allocation failed                                 */
+    HELM_ECUDA = -3,      /* a CUDA call failed                                       */
+    HELM_ESTATE = -4,     /* call out of order (e.g. apply before factor)            */
+    HELM_ENOTCONV = -5,   /* GMRES hit maxit; the best iterate and info are written   */
+    HELM_ENUMERIC = -6,   /* tiny pivot in a block inverse, or NaN/Inf in a norm      */
+    HELM_ETIMEOUT = -7    /* a bounded device wait gave up                            */
+} helm_status;
+
+typedef struct {
+    int dim;          /* 2 or 3                                        */
+    int64_t n[3];     /* interior points per axis (x, y, z); n[2]=1 in 2-D */
+    double h;         /* grid spacing                                  */
+} helm_grid;
+
+typedef enum {
+    HELM_PREC_FP64 = 0,   /* complex128 factors and sweeps, FP64 GMRES                  */
+    HELM_PREC_MIXED = 1   /* complex64 factors and sweeps (FP32 accumulate), FP64 FGMRES */
+} helm_prec;
+
+typedef struct {
+    int iters;        /* Arnoldi steps (= preconditioner applications in the Krylov loop) */
+    double rel_res;   /* true final ||f - A u||_2 / ||f||_2 over the padded grid           */
+    double t_ms;      /* wall time of the whole batch solve                               */
+} helm_rhs_info;
+
+/* Create a problem on the padded grid and validate its parameters
+ * (Section 2.1: strips D^(j) along x with J subdomains; Eq. define_beta_j,
+ * read as an even split of the interior: beta_j = w_outer-1 + floor(j n_x/J + 1/2),
+ * the first and last strips also owning the outer layer).
+ *   g        grid; dim 2 or 3, n[a] >= 1, h > 0
+ *   c        speed on the interior grid (x fastest), all finite and > 0; copied
+ *   omega    angular frequency > 0
+ *   w_outer  outer PML width in points (>= 0)
+ *   w_sub    added PML width of each strip on its internal sides (>= 1 if J > 1)
+ *   J        number of strips (>= 1); every strip core must have >= 2 columns
+ *   prec     arithmetic of factors and sweeps
+ *   out      receives the handle (NULL on failure)
+ * Returns HELM_EINVAL on bad arguments, HELM_ENOMEM / HELM_ECUDA on device errors. */
+helm_status helm_dd_create(const helm_grid* g, const double* c, double omega,
+                           int w_outer, int w_sub, int J, helm_prec prec, helm_dd** out);
+
+/* Fix the speed c_ref that sets the PML strength sigma0 (default: max of c).
+ * Must be called before helm_dd_factor; c_ref > 0. */
+helm_status helm_dd_set_pml_speed(helm_dd* h, double c_ref);
+
+/* Number of chunks P the y-axis of every strip is cut into for the partitioned
+ * block-tridiagonal factorisation (1 = plain sequential block LU).  0 selects the
+ * built-in choice.  Must be called before helm_dd_factor. */
+helm_status helm_dd_set_chunks(helm_dd* h, int P);
+
+/* Algorithm 1 (preparation): assemble every strip operator A^(j) on the grid of
+ * Eq. grid_A_j (physical columns beta_{j-1}+1 .. beta_j+1 plus w_sub added PML
+ * columns on internal sides, k held constant in x across an added layer) in its
+ * complex-symmetric form S^(j) A^(j), and factor it as a block-tridiagonal
+ * matrix along y.  Factors stay on the device.  Returns HELM_ENUMERIC on a
+ * numerically singular block. */
+helm_status helm_dd_factor(helm_dd* h);
+
+/* out = P in for nrhs right-hand sides (Section 2.1, Eqs. solve_upward and
+ * solve_downward; Algorithm 4 without u~): forward sweep j = 1..J with the
+ * single-layer-potential transfer -2 delta(x-b_{j-1}) d_x v^(j-1), residual
+ * g = f - A v, backward sweep j = J-1..1 with +2 delta(x-b~_j) d_x w^(j+1) on
+ * g restricted to D~^(j), and out = v + w.  HELM_ESTATE before helm_dd_factor. */
+helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int nrhs);
+
+/* out = A in (paper form, FP64) for nrhs fields. */
+helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs);
+
+/* Solve A u = rhs for nrhs right-hand sides (Algorithm 5, full-space form):
+ * right-preconditioned GMRES(restart) on A P v = f, u = P v (flexible form in
+ * mixed precision), x0 = 0, stopping when the Givens estimate reaches
+ * tol*||f|| and the true residual confirms it.  info (nrhs entries, may be NULL)
+ * receives per-RHS iterations, true relative residual and the batch time.
+ * Returns HELM_ENOTCONV (with u and info written) when maxit is reached. */
+helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs,
+                          double tol, int restart, int maxit, helm_rhs_info* info);
+
+/* Least-squares misfit J = 1/2 sum_s ||R u_s - d_s||^2 and its gradient with
+ * respect to m = 1/c^2 on the interior grid (not in the paper: the adjoint of
+ * A(m) = L - omega^2 diag(m)).  Sources are discrete deltas 1/h^dim at the
+ * padded linear indices src_idx; R samples u at rec_idx; d is complex128
+ * [nsrc][nrec] interleaved.  Forward and adjoint solves (A mu_s =
+ * S^-1 conj(R^T r_s)) share the factors; grad = omega^2 Re sum_s S mu_s u_s,
+ * folded from the padded grid onto the interior through the clamp extension.
+ * The PML profile is held fixed.  misfit and grad_m (interior size) are
+ * written; tol is the GMRES tolerance of both solves. */
+helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc,
+                             const int64_t* rec_idx, int nrec, const double* d,
+                             double tol, double* misfit, double* grad_m);
+
+/* Run all device work of the handle on this cudaStream_t (NULL = the handle's
+ * own stream).  The caller keeps ownership of the stream. */
+helm_status helm_dd_set_stream(helm_dd* h, void* stream);
+
+/* Per-kernel timing of the calls that follow: when enabled, each launch of the
+ * library's kernels is bracketed by CUDA events on the launching stream and its
+ * duration accumulated by kernel name.  helm_dd_kernel_stats copies up to cap
+ * entries (name, launches, total ms) and returns how many exist. */
+helm_status helm_dd_set_timing(helm_dd* h, int enable);
+int helm_dd_kernel_stats(helm_dd* h, char (*names)[48], int64_t* launches,
+                         double* total_ms, int cap);
+
+/* Bytes of factor data one preconditioner application reads by the method's
+ * own count (2 passes x sum over strip solves of N_y W_j^2 x element size). */
+double helm_dd_precond_factor_bytes(const helm_dd* h);
+
+/* Padded sizes N[0..2]; strip widths W_j (J entries) when W != NULL. */
+void helm_dd_dims(const helm_dd* h, int64_t N[3]);
+int helm_dd_strip_widths(const helm_dd* h, int* W, int cap);
+int helm_dd_interfaces(const helm_dd* h, int* beta, int cap);
+
+void helm_dd_destroy(helm_dd* h);
+const char* helm_dd_last_error(const helm_dd* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_DD_H */

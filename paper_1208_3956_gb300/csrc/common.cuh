@@ -1,0 +1,104 @@
+// Shared device-side definitions of the helm_dd library: complex arithmetic on
+// float2 / double2, strip descriptors and kernel argument blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace helm {
+
+// ---------------------------------------------------------------- complex ops
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b with fused multiply-adds
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+__host__ __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// 1 / a, scaled to avoid overflow of |a|^2
+__host__ __device__ __forceinline__ float2 cinv(float2 a) {
+    float s = fmaxf(fabsf(a.x), fabsf(a.y));
+    float ar = a.x / s, ai = a.y / s;
+    float d = s * (ar * ar + ai * ai);
+    return make_float2(ar / d, -ai / d);
+}
+__host__ __device__ __forceinline__ double2 cinv(double2 a) {
+    double s = fmax(fabs(a.x), fabs(a.y));
+    double ar = a.x / s, ai = a.y / s;
+    double d = s * (ar * ar + ai * ai);
+    return make_double2(ar / d, -ai / d);
+}
+
+template <typename C> struct CT;
+template <> struct CT<float2> {
+    using R = float;
+    __host__ __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __host__ __device__ static float2 from(double2 a) { return make_float2((float)a.x, (float)a.y); }
+};
+template <> struct CT<double2> {
+    using R = double;
+    __host__ __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __host__ __device__ static double2 from(double2 a) { return a; }
+};
+__host__ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+
+// ------------------------------------------------------------ problem layout
+// One strip of the decomposition along x (0-based j = 0..J-1).  Its grid is
+// lpml added PML columns, the physical padded columns lo..hi (hi is the overlap
+// column beta_{j+1}+1 for j < J-1), then rpml added columns.  Strip-local column
+// c corresponds to padded column lo - lpml + c.
+struct StripDev {
+    int W, lo, hi, lpml, rpml, j;
+    int64_t tab;   // offset of this strip's x tables: alpha at integer points (W), then half points (W+1)
+    int64_t fac;   // element offset of this strip's blocks in the factor pools (Ny blocks of BS)
+    int64_t red;   // element offset of this strip's reduced-system blocks ((P-1) blocks of BS)
+    int64_t bs;    // elements per stored W x W block (column-major, padded to 16 bytes)
+};
+
+// Global geometry and tables (device pointers, FP64).
+struct Geom {
+    int dim;
+    int Nx, Ny, Nz;
+    int J, P;                  // strips, chunks along y
+    double h, inv_h2, omega;
+    const double* k2;          // [Nz][Ny][Nx]
+    const double2* gx_int;     // alpha at integer points, x / y / z
+    const double2* gx_half;    // alpha at half points m-1/2, m = 0..N
+    const double2* gy_int;
+    const double2* gy_half;
+    const double2* gz_int;
+    const double2* gz_half;
+    const double2* stab;       // per-strip x tables (see StripDev::tab)
+    const StripDev* strips;
+    const int* r0;             // chunk p covers rows r0[p] .. r1[p]-1; separator p is row r1[p]
+    const int* r1;
+    const int* rowmap;         // row k -> chunk p (>= 0) or separator q as -(q+1)
+};
+
+__host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
+
+}  // namespace helm

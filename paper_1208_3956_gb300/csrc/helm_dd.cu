@@ -1,0 +1,925 @@
+// Host side of the helm_dd C ABI: problem set-up, PML tables, strip geometry,
+// device memory, the double-sweep driver, flexible GMRES and the misfit
+// gradient.  All arithmetic on fields runs in the kernels of factor.cu,
+// sweep.cu and field.cu; the host computes O(N) one-dimensional tables and the
+// O(restart^2) Hessenberg/Givens work of GMRES.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "helm_dd.h"
+#include "internal.h"
+
+using namespace helm;
+typedef std::complex<double> cd;
+
+namespace {
+
+// ---- PML (Section 2.1): d/dx -> (1 + i sigma/omega)^-1 d/dx, quadratic profile.
+struct Pml {
+    double sigma0 = 0.0;
+    int w = 0;
+    double h = 1.0, omega = 1.0;
+    // alpha at a point whose distance into the layer is d2 half-steps (d = d2 h / 2)
+    cd alpha(int d2) const {
+        if (w <= 0 || d2 <= 0) return cd(1.0, 0.0);
+        const double L = w * h;
+        const double d = std::min(0.5 * d2 * h, L);
+        const double s = sigma0 * (d / L) * (d / L);
+        return 1.0 / cd(1.0, s / omega);
+    }
+};
+
+double pml_sigma0(double c_ref, int w, double h) {
+    if (w <= 0) return 0.0;
+    return 3.0 * c_ref * log(1.0e6) / (2.0 * w * h);
+}
+
+// alpha on a padded axis of Np points with a w-point layer at both ends, as a
+// function of position in half-steps x2 (integer point i at x2 = 2i, half point
+// i+1/2 at x2 = 2i+1).  Interfaces at x_{w-1/2} and x_{Np-w-1/2}.
+cd axis_alpha_at(const Pml& p, int Np, int x2) {
+    if (p.w <= 0) return cd(1.0, 0.0);
+    const int lo2 = 2 * p.w - 1, hi2 = 2 * (Np - p.w) - 1;
+    const int d2 = std::max(std::max(lo2 - x2, x2 - hi2), 0);
+    return p.alpha(d2);
+}
+
+}  // namespace
+
+struct helm_dd {
+    // problem
+    int dim = 2;
+    int64_t n[3] = {1, 1, 1};
+    int64_t N[3] = {1, 1, 1};
+    double h = 1.0, omega = 1.0, c_ref = 0.0;
+    int w_outer = 0, w_sub = 0, J = 1, P_req = 0;
+    helm_prec prec = HELM_PREC_FP64;
+    std::vector<double> c;
+    // geometry
+    std::vector<int> beta;
+    std::vector<StripDev> strips;
+    int P = 1, Wmax = 0;
+    std::vector<int> r0, r1, rowmap;
+    std::vector<cd> gx_int, gx_half, gy_int, gy_half, gz_int, gz_half;
+    // device
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    Geom geom{};
+    double* d_c = nullptr;
+    double* d_k2 = nullptr;
+    double2* d_tab = nullptr;       // global axis tables + per-strip x tables
+    StripDev* d_strips = nullptr;
+    int* d_ints = nullptr;          // r0 | r1 | rowmap
+    void* d_pool[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Sinv GT GB Rinv E F
+    int* d_status = nullptr;
+    size_t esize = 16;
+    bool factored = false;
+    bool prepared = false;
+    bool dev_ready = false;
+    // workspaces
+    struct Ws { void* p = nullptr; size_t bytes = 0; };
+    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
+    KernelTimer timer;
+    std::string err;
+};
+
+namespace {
+
+helm_status fail(helm_dd* h, helm_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+helm_status fail_cuda(helm_dd* h, const char* what, cudaError_t e) {
+    return fail(h, e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(h, call)                                                    \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return fail_cuda((h), #call, e_);       \
+    } while (0)
+
+helm_status ws_reserve(helm_dd* h, helm_dd::Ws& w, size_t bytes) {
+    if (w.bytes >= bytes) return HELM_OK;
+    if (w.p) cudaFree(w.p);
+    w.p = nullptr;
+    w.bytes = 0;
+    cudaError_t e = cudaMalloc(&w.p, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail_cuda(h, "cudaMalloc(workspace)", e); }
+    w.bytes = bytes;
+    return HELM_OK;
+}
+void ws_free(helm_dd::Ws& w) {
+    if (w.p) cudaFree(w.p);
+    w.p = nullptr;
+    w.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t nvol(const helm_dd* h) { return h->N[0] * h->N[1] * h->N[2]; }
+
+// Strip geometry (Section 2.1, Eq. grid_A_j) and its x tables.
+void build_geometry(helm_dd* h) {
+    const int Nx = (int)h->N[0];
+    const int nx = (int)h->n[0];
+    h->beta.assign(h->J + 1, 0);
+    for (int j = 0; j <= h->J; ++j) h->beta[j] = h->w_outer - 1 + (int)floor((double)j * nx / h->J + 0.5);
+    h->beta[0] = -1;
+    h->beta[h->J] = Nx - 1;
+    h->strips.assign(h->J, StripDev{});
+    h->Wmax = 0;
+    for (int j = 0; j < h->J; ++j) {
+        StripDev& s = h->strips[j];
+        s.j = j;
+        s.lo = h->beta[j] + 1;
+        s.hi = (j < h->J - 1) ? h->beta[j + 1] + 1 : Nx - 1;
+        s.lpml = j > 0 ? h->w_sub : 0;
+        s.rpml = j < h->J - 1 ? h->w_sub : 0;
+        s.W = s.lpml + (s.hi - s.lo + 1) + s.rpml;
+        h->Wmax = std::max(h->Wmax, s.W);
+    }
+}
+
+void build_tables(helm_dd* h) {
+    Pml po;
+    po.w = h->w_outer;
+    po.h = h->h;
+    po.omega = h->omega;
+    po.sigma0 = pml_sigma0(h->c_ref, h->w_outer, h->h);
+    Pml ps = po;
+    ps.w = h->w_sub;
+    ps.sigma0 = pml_sigma0(h->c_ref, h->w_sub, h->h);
+    auto axis = [&](int Np, std::vector<cd>& ai, std::vector<cd>& ah) {
+        ai.resize(Np);
+        ah.resize(Np + 1);
+        for (int i = 0; i < Np; ++i) ai[i] = axis_alpha_at(po, Np, 2 * i);
+        for (int m = 0; m <= Np; ++m) ah[m] = axis_alpha_at(po, Np, 2 * m - 1);
+    };
+    axis((int)h->N[0], h->gx_int, h->gx_half);
+    axis((int)h->N[1], h->gy_int, h->gy_half);
+    if (h->dim == 3) axis((int)h->N[2], h->gz_int, h->gz_half);
+    else { h->gz_int.assign(1, cd(1.0, 0.0)); h->gz_half.assign(2, cd(1.0, 0.0)); }
+}
+
+// alpha along x at strip-local half-step position x2 (column c at 2c, half point
+// m-1/2 at 2m-1): inside an added layer measured from the subdomain interface,
+// otherwise the global table.
+cd strip_alpha_at(const helm_dd* h, const StripDev& s, int x2) {
+    const int g2 = x2 + 2 * (s.lo - s.lpml);          // padded half-step position
+    const int lo_if2 = 2 * s.lo - 1, hi_if2 = 2 * s.hi + 1;
+    Pml ps;
+    ps.w = h->w_sub;
+    ps.h = h->h;
+    ps.omega = h->omega;
+    ps.sigma0 = pml_sigma0(h->c_ref, h->w_sub, h->h);
+    if (s.lpml > 0 && g2 < lo_if2) return ps.alpha(lo_if2 - g2);
+    if (s.rpml > 0 && g2 > hi_if2) return ps.alpha(g2 - hi_if2);
+    Pml po = ps;
+    po.w = h->w_outer;
+    po.sigma0 = pml_sigma0(h->c_ref, h->w_outer, h->h);
+    return axis_alpha_at(po, (int)h->N[0], g2);
+}
+
+void chunk_layout(helm_dd* h) {
+    const int Ny = (int)h->N[1];
+    int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(sqrt(Ny / 2.0)));
+    P = std::min(P, (Ny + 1) / 2);
+    h->P = std::max(P, 1);
+    const int rows = Ny - (h->P - 1);
+    const int base = rows / h->P, rem = rows % h->P;
+    h->r0.assign(h->P, 0);
+    h->r1.assign(h->P, 0);
+    h->rowmap.assign(Ny, 0);
+    int k = 0;
+    for (int p = 0; p < h->P; ++p) {
+        h->r0[p] = k;
+        h->r1[p] = k + base + (p < rem ? 1 : 0);
+        for (int r = h->r0[p]; r < h->r1[p]; ++r) h->rowmap[r] = p;
+        k = h->r1[p];
+        if (p < h->P - 1) { h->rowmap[k] = -(p + 1); k += 1; }
+    }
+}
+
+double2 to_d2h(cd v) { return make_double2(v.real(), v.imag()); }
+
+// First device use of a handle: stream, medium upload and k^2 (a1).  Creating
+// a handle touches no GPU, so its host-side geometry is usable without one.
+helm_status ensure_device(helm_dd* h) {
+    if (h->dev_ready) return HELM_OK;
+    if (!h->own_stream) CK(h, cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    if (!h->stream) h->stream = h->own_stream;
+    const int64_t nint = (int64_t)h->c.size();
+    CK(h, cudaMalloc(&h->d_c, nint * sizeof(double)));
+    CK(h, cudaMalloc(&h->d_k2, nvol(h) * sizeof(double)));
+    CK(h, cudaMalloc(&h->d_status, sizeof(int)));
+    CK(h, cudaMemcpyAsync(h->d_c, h->c.data(), nint * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_k2(h->d_c, h->d_k2, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->omega,
+                    h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->dev_ready = true;
+    return HELM_OK;
+}
+
+// Build the PML tables, strip geometry and chunk layout and upload them; fills
+// h->geom.  Idempotent until helm_dd_set_chunks / set_pml_speed change inputs.
+helm_status prepare_geom(helm_dd* h) {
+    helm_status ds = ensure_device(h);
+    if (ds != HELM_OK) return ds;
+    build_tables(h);
+    chunk_layout(h);
+    std::vector<cd> tabs;
+    auto append = [&](const std::vector<cd>& v) { tabs.insert(tabs.end(), v.begin(), v.end()); };
+    append(h->gx_int);
+    append(h->gx_half);
+    append(h->gy_int);
+    append(h->gy_half);
+    append(h->gz_int);
+    append(h->gz_half);
+    const int64_t stab0 = (int64_t)tabs.size();
+    const int Ny = (int)h->N[1];
+    for (auto& s : h->strips) {
+        s.tab = (int64_t)tabs.size() - stab0;
+        for (int c = 0; c < s.W; ++c) tabs.push_back(strip_alpha_at(h, s, 2 * c));
+        for (int m = 0; m <= s.W; ++m) tabs.push_back(strip_alpha_at(h, s, 2 * m - 1));
+    }
+    std::vector<double2> tab2(tabs.size());
+    for (size_t i = 0; i < tabs.size(); ++i) tab2[i] = to_d2h(tabs[i]);
+    if (h->d_tab) cudaFree(h->d_tab);
+    if (h->d_strips) cudaFree(h->d_strips);
+    if (h->d_ints) cudaFree(h->d_ints);
+    h->d_tab = nullptr; h->d_strips = nullptr; h->d_ints = nullptr;
+    CK(h, cudaMalloc(&h->d_tab, tab2.size() * sizeof(double2)));
+    CK(h, cudaMalloc(&h->d_strips, h->strips.size() * sizeof(StripDev)));
+    CK(h, cudaMalloc(&h->d_ints, (2 * h->P + Ny) * sizeof(int)));
+    CK(h, cudaMemcpyAsync(h->d_tab, tab2.data(), tab2.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
+                          cudaMemcpyHostToDevice, h->stream));
+    std::vector<int> ints;
+    ints.insert(ints.end(), h->r0.begin(), h->r0.end());
+    ints.insert(ints.end(), h->r1.begin(), h->r1.end());
+    ints.insert(ints.end(), h->rowmap.begin(), h->rowmap.end());
+    CK(h, cudaMemcpyAsync(h->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    Geom& g = h->geom;
+    g.dim = h->dim;
+    g.Nx = (int)h->N[0];
+    g.Ny = (int)h->N[1];
+    g.Nz = (int)h->N[2];
+    g.J = h->J;
+    g.P = h->P;
+    g.h = h->h;
+    g.inv_h2 = 1.0 / (h->h * h->h);
+    g.omega = h->omega;
+    g.k2 = h->d_k2;
+    int64_t o = 0;
+    g.gx_int = h->d_tab + o; o += h->gx_int.size();
+    g.gx_half = h->d_tab + o; o += h->gx_half.size();
+    g.gy_int = h->d_tab + o; o += h->gy_int.size();
+    g.gy_half = h->d_tab + o; o += h->gy_half.size();
+    g.gz_int = h->d_tab + o; o += h->gz_int.size();
+    g.gz_half = h->d_tab + o; o += h->gz_half.size();
+    g.stab = h->d_tab + stab0;
+    g.strips = h->d_strips;
+    g.r0 = h->d_ints;
+    g.r1 = h->d_ints + h->P;
+    g.rowmap = h->d_ints + 2 * h->P;
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->prepared = true;
+    return HELM_OK;
+}
+
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+helm_status helm_dd_create(const helm_grid* g, const double* c, double omega, int w_outer, int w_sub, int J,
+                           helm_prec prec, helm_dd** out) {
+    if (out) *out = nullptr;
+    if (!g || !c || !out) return HELM_EINVAL;
+    if (g->dim != 2 && g->dim != 3) return HELM_EINVAL;
+    if (!(g->h > 0) || !(omega > 0) || !isfinite(omega) || w_outer < 0 || J < 1) return HELM_EINVAL;
+    if (J > 1 && w_sub < 1) return HELM_EINVAL;
+    if (prec != HELM_PREC_FP64 && prec != HELM_PREC_MIXED) return HELM_EINVAL;
+    for (int a = 0; a < g->dim; ++a)
+        if (g->n[a] < 1 || g->n[a] > (1 << 20)) return HELM_EINVAL;
+    const int64_t nz = g->dim == 3 ? g->n[2] : 1;
+    const int64_t nint = g->n[0] * g->n[1] * nz;
+    double cmax = 0.0;
+    for (int64_t i = 0; i < nint; ++i) {
+        if (!(c[i] > 0.0) || !isfinite(c[i])) return HELM_EINVAL;
+        cmax = std::max(cmax, c[i]);
+    }
+    helm_dd* h = new helm_dd();
+    h->dim = g->dim;
+    for (int a = 0; a < 3; ++a) h->n[a] = (a < g->dim) ? g->n[a] : 1;
+    for (int a = 0; a < 3; ++a) h->N[a] = (a < g->dim) ? h->n[a] + 2 * w_outer : 1;
+    h->h = g->h;
+    h->omega = omega;
+    h->c_ref = cmax;
+    h->w_outer = w_outer;
+    h->w_sub = w_sub;
+    h->J = J;
+    h->prec = prec;
+    h->esize = prec == HELM_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+    h->c.assign(c, c + nint);
+    if (J > h->n[0]) { delete h; return HELM_EINVAL; }
+    build_geometry(h);
+    for (int j = 0; j < J; ++j) {
+        const StripDev& s = h->strips[j];
+        const int core = h->beta[j + 1] - h->beta[j];
+        // strip blocks are dense W x W in shared memory: W <= 64
+        if ((J > 1 && core < 2) || s.W > 64) { delete h; return HELM_EINVAL; }
+    }
+    *out = h;
+    return HELM_OK;
+}
+
+helm_status helm_dd_set_pml_speed(helm_dd* h, double c_ref) {
+    if (!h || !(c_ref > 0) || !isfinite(c_ref)) return HELM_EINVAL;
+    if (h->factored) return fail(h, HELM_ESTATE, "set_pml_speed after factor");
+    h->c_ref = c_ref;
+    h->prepared = false;
+    return HELM_OK;
+}
+
+helm_status helm_dd_set_chunks(helm_dd* h, int P) {
+    if (!h || P < 0) return HELM_EINVAL;
+    if (h->factored) return fail(h, HELM_ESTATE, "set_chunks after factor");
+    if (P > 0 && 2 * P - 1 > h->N[1]) return fail(h, HELM_EINVAL, "too many chunks for the y extent");
+    h->P_req = P;
+    h->prepared = false;
+    return HELM_OK;
+}
+
+helm_status helm_dd_set_stream(helm_dd* h, void* stream) {
+    if (!h) return HELM_EINVAL;
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;   // null until first device use
+    return HELM_OK;
+}
+
+helm_status helm_dd_set_timing(helm_dd* h, int enable) {
+    if (!h) return HELM_EINVAL;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->timer.flush();
+    if (enable) h->timer.reset();
+    h->timer.enabled = enable != 0;
+    return HELM_OK;
+}
+
+int helm_dd_kernel_stats(helm_dd* h, char (*names)[48], int64_t* launches, double* total_ms, int cap) {
+    if (!h) return 0;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->timer.flush();
+    const int n = (int)h->timer.names.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) { strncpy(names[i], h->timer.names[i].c_str(), 47); names[i][47] = 0; }
+        if (launches) launches[i] = h->timer.counts[i];
+        if (total_ms) total_ms[i] = h->timer.total_ms[i];
+    }
+    return n;
+}
+
+helm_status helm_dd_factor(helm_dd* h) {
+    if (!h) return HELM_EINVAL;
+    helm_status ps = prepare_geom(h);
+    if (ps != HELM_OK) return ps;
+    if (h->dim != 2) return fail(h, HELM_EINVAL, "strip factorisation is implemented for 2-D grids");
+    const int Ny = (int)h->N[1];
+    int64_t fac = 0, red = 0;
+    for (auto& s : h->strips) {
+        s.bs = (int64_t)s.W * s.W;
+        if (h->esize == sizeof(float2) && (s.bs & 1)) s.bs += 1;   // keep blocks 16-byte aligned
+        s.fac = fac;
+        s.red = red;
+        fac += (int64_t)Ny * s.bs;
+        red += (int64_t)std::max(h->P - 1, 1) * s.bs;
+    }
+    for (auto& p : h->d_pool) { if (p) cudaFree(p); p = nullptr; }
+    h->factored = false;
+    const size_t facb = (size_t)fac * h->esize, redb = (size_t)red * h->esize;
+    CK(h, cudaMalloc(&h->d_pool[0], facb));
+    CK(h, cudaMalloc(&h->d_pool[1], facb));
+    CK(h, cudaMalloc(&h->d_pool[2], facb));
+    CK(h, cudaMalloc(&h->d_pool[3], redb));
+    CK(h, cudaMalloc(&h->d_pool[4], redb));
+    CK(h, cudaMalloc(&h->d_pool[5], redb));
+    CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
+                          cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    Geom& g = h->geom;
+    cudaError_t e;
+    if (h->prec == HELM_PREC_MIXED)
+        e = launch_factor<float2>(g, h->Wmax, h->d_pool[0], h->d_pool[1], h->d_pool[2], h->d_pool[3],
+                                  h->d_pool[4], h->d_pool[5], h->d_status, h->stream, &h->timer);
+    else
+        e = launch_factor<double2>(g, h->Wmax, h->d_pool[0], h->d_pool[1], h->d_pool[2], h->d_pool[3],
+                                   h->d_pool[4], h->d_pool[5], h->d_status, h->stream, &h->timer);
+    if (e != cudaSuccess) return fail_cuda(h, "factor kernels", e);
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st != 0) return fail(h, HELM_ENUMERIC, "singular block in the strip factorisation");
+    h->factored = true;
+    return HELM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// out = A u (f == null) or f - A u, device fields [B][N]
+helm_status dev_stencil(helm_dd* h, const double2* u, const double2* f, double2* out, int B) {
+    CK(h, launch_stencil(h->geom, u, f, out, B, h->stream, &h->timer));
+    return HELM_OK;
+}
+
+// P applied to B device fields (Section 2.1): in -> out (distinct buffers).
+helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
+    const int64_t NV = nvol(h);
+    const int Ny = (int)h->N[1], Nx = (int)h->N[0];
+    helm_status s;
+    if ((s = ws_reserve(h, h->ws_V, (size_t)B * NV * sizeof(double2))) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_G, (size_t)B * NV * sizeof(double2))) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_T0, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_T1, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_Y, (size_t)B * Ny * h->Wmax * h->esize)) != HELM_OK) return s;
+    double2* V = (double2*)h->ws_V.p;
+    double2* G = (double2*)h->ws_G.p;
+    double2* Tin = (double2*)h->ws_T0.p;
+    double2* Tout = (double2*)h->ws_T1.p;
+    SweepWork wk{h->ws_Y.p, h->Wmax, B};
+    const int J = h->J;
+    const auto& beta = h->beta;
+    const double ih2 = 1.0 / (h->h * h->h);
+    auto strip_solve = [&](int j, const SweepStep& sp) -> cudaError_t {
+        if (h->prec == HELM_PREC_MIXED)
+            return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool[0], h->d_pool[1],
+                                              h->d_pool[2], h->d_pool[3], h->d_pool[4], h->d_pool[5],
+                                              h->stream, &h->timer);
+        return launch_strip_solve<double2>(h->geom, j, h->strips[j], sp, wk, h->d_pool[0], h->d_pool[1],
+                                           h->d_pool[2], h->d_pool[3], h->d_pool[4], h->d_pool[5], h->stream,
+                                           &h->timer);
+    };
+    // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1)
+    for (int j = 0; j < J; ++j) {
+        const StripDev& st = h->strips[j];
+        SweepStep sp{};
+        sp.src = in;
+        sp.mlo = beta[j] + 1;
+        sp.mhi = beta[j + 1];
+        sp.tin = j > 0 ? Tin : nullptr;
+        sp.t0 = beta[j];
+        sp.tcoef = -ih2;
+        sp.dst = (J == 1) ? out : V;
+        sp.base = nullptr;
+        sp.olo = beta[j] + 1;
+        sp.ohi = beta[j + 1];
+        sp.tout = j < J - 1 ? Tout : nullptr;
+        sp.to1 = st.lpml + (st.hi - st.lo);
+        sp.to0 = sp.to1 - 1;
+        CK(h, strip_solve(j, sp));
+        std::swap(Tin, Tout);
+    }
+    if (J == 1) return HELM_OK;
+    // residual g = f - A v
+    if ((s = dev_stencil(h, V, in, G, B)) != HELM_OK) return s;
+    // backward sweep j = J-1..1 (Eq. solve_downward), w^(J) = 0, out = v + w on D~^(j)
+    for (int j = J - 2; j >= 0; --j) {
+        const StripDev& st = h->strips[j];
+        SweepStep sp{};
+        sp.src = G;
+        sp.mlo = j > 0 ? beta[j] + 2 : 0;
+        sp.mhi = beta[j + 1] + 1;
+        sp.tin = (j + 1 <= J - 2) ? Tin : nullptr;
+        sp.t0 = beta[j + 1] + 1;
+        sp.tcoef = ih2;
+        sp.dst = out;
+        sp.base = V;
+        sp.olo = sp.mlo;
+        sp.ohi = sp.mhi;
+        sp.tout = j > 0 ? Tout : nullptr;
+        sp.to0 = st.lpml;
+        sp.to1 = st.lpml + 1;
+        CK(h, strip_solve(j, sp));
+        std::swap(Tin, Tout);
+    }
+    // D~^(J) keeps v (w = 0 there)
+    CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream));
+    return HELM_OK;
+}
+
+struct IoField {
+    const double* user_in = nullptr;
+    double* user_out = nullptr;
+    bool dev_in = false, dev_out = false;
+};
+
+}  // namespace
+
+extern "C" {
+
+helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int nrhs) {
+    if (!h || !in || !out || nrhs < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "apply_precond before factor");
+    const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    helm_status s;
+    const double2* dinp = (const double2*)in;
+    double2* doutp = (double2*)out;
+    if (!din) {
+        if ((s = ws_reserve(h, h->ws_io_in, bytes)) != HELM_OK) return s;
+        CK(h, cudaMemcpyAsync(h->ws_io_in.p, in, bytes, cudaMemcpyHostToDevice, h->stream));
+        dinp = (const double2*)h->ws_io_in.p;
+    }
+    if (!dout || (const void*)doutp == (const void*)dinp) {
+        if ((s = ws_reserve(h, h->ws_io_out, bytes)) != HELM_OK) return s;
+        doutp = (double2*)h->ws_io_out.p;
+    }
+    if ((s = dev_precond(h, dinp, doutp, nrhs)) != HELM_OK) return s;
+    if (!dout) CK(h, cudaMemcpyAsync(out, doutp, bytes, cudaMemcpyDeviceToHost, h->stream));
+    else if ((void*)doutp != (void*)out)
+        CK(h, cudaMemcpyAsync(out, doutp, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return HELM_OK;
+}
+
+helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs) {
+    if (!h || !in || !out || nrhs < 1) return HELM_EINVAL;
+    if (!h->prepared) {
+        helm_status ps = prepare_geom(h);
+        if (ps != HELM_OK) return ps;
+    }
+    const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    helm_status s;
+    const double2* dinp = (const double2*)in;
+    double2* doutp = (double2*)out;
+    if (!din) {
+        if ((s = ws_reserve(h, h->ws_io_in, bytes)) != HELM_OK) return s;
+        CK(h, cudaMemcpyAsync(h->ws_io_in.p, in, bytes, cudaMemcpyHostToDevice, h->stream));
+        dinp = (const double2*)h->ws_io_in.p;
+    }
+    if (!dout) {
+        if ((s = ws_reserve(h, h->ws_io_out, bytes)) != HELM_OK) return s;
+        doutp = (double2*)h->ws_io_out.p;
+    }
+    if ((s = dev_stencil(h, dinp, nullptr, doutp, nrhs)) != HELM_OK) return s;
+    if (!dout) CK(h, cudaMemcpyAsync(out, doutp, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return HELM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Flexible GMRES(m), right preconditioned (Section 2.3, Eq. left_preconditioned;
+// Algorithm 5 in full space), batched over B columns with per-column masks.
+// Classical Gram-Schmidt with reorthogonalisation (CGS2) in FP64 on the device;
+// Hessenberg, Givens rotations and the small triangular solve on the host.
+helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double tol, int m, int maxit,
+                       std::vector<int>& iters, std::vector<double>& relres) {
+    const int64_t NV = nvol(h);
+    const size_t vb = (size_t)B * NV * sizeof(double2);
+    helm_status s;
+    // Krylov storage: V_0..V_m, Z_0..Z_{m-1}, W
+    if ((s = ws_reserve(h, h->ws_kry, (size_t)(2 * m + 2) * vb)) != HELM_OK) return s;
+    const int nblk = 304;
+    const size_t small = (size_t)B * (m + 2) * nblk * sizeof(double2) + (size_t)4 * B * (m + 2) * sizeof(double2);
+    if ((s = ws_reserve(h, h->ws_small, small)) != HELM_OK) return s;
+    double2* V = (double2*)h->ws_kry.p;
+    const int64_t vs = (int64_t)B * NV;   // stride between Krylov vectors (elements)
+    double2* Z = V + (int64_t)(m + 1) * vs;
+    double2* Wv = Z + (int64_t)m * vs;
+    double2* partial = (double2*)h->ws_small.p;
+    double2* dres = partial + (size_t)B * (m + 2) * nblk;
+    double2* dcoef = dres + (size_t)B * (m + 2);
+    double* dscale = (double*)(dcoef + (size_t)B * (m + 2));
+    std::vector<double2> hres(B * (m + 2)), hcoef(B * (m + 2));
+    std::vector<double> hscale(B);
+
+    auto norms = [&](const double2* X, std::vector<double>& nrm) -> helm_status {
+        CK(h, launch_multidot(X, 0, X, 1, B, NV, partial, nblk, dres, h->stream, &h->timer));
+        CK(h, cudaMemcpyAsync(hres.data(), dres, B * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        nrm.resize(B);
+        for (int b = 0; b < B; ++b) nrm[b] = sqrt(std::max(hres[b].x, 0.0));
+        return HELM_OK;
+    };
+
+    std::vector<double> bnorm;
+    if ((s = norms(F, bnorm)) != HELM_OK) return s;
+    for (int b = 0; b < B; ++b)
+        if (!isfinite(bnorm[b])) return fail(h, HELM_ENUMERIC, "non-finite right-hand side");
+    CK(h, cudaMemsetAsync(U, 0, vb, h->stream));
+    iters.assign(B, 0);
+    relres.assign(B, 0.0);
+    std::vector<char> conv(B, 0);
+    std::vector<cd> H((size_t)B * (m + 1) * m), g((size_t)B * (m + 1)), sn((size_t)B * m);
+    std::vector<double> cs((size_t)B * m);
+    std::vector<int> kend(B);
+    std::vector<char> active(B);
+    std::vector<double> beta;
+    int guard = 0;
+    while (true) {
+        // r = f - A x into V_0
+        if ((s = dev_stencil(h, U, F, V, B)) != HELM_OK) return s;
+        if ((s = norms(V, beta)) != HELM_OK) return s;
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            if (!isfinite(beta[b])) return fail(h, HELM_ENUMERIC, "non-finite residual norm");
+            relres[b] = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
+            if (bnorm[b] == 0.0 || beta[b] <= tol * bnorm[b]) conv[b] = 1;
+            active[b] = !conv[b] && iters[b] < maxit;
+            any = any || active[b];
+            hscale[b] = active[b] ? 1.0 / beta[b] : 0.0;
+            kend[b] = 0;
+            for (int i = 0; i <= m; ++i) g[(size_t)b * (m + 1) + i] = 0.0;
+            g[(size_t)b * (m + 1)] = beta[b];
+        }
+        if (!any || ++guard > 100000) break;
+        CK(h, cudaMemcpyAsync(dscale, hscale.data(), B * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, launch_scale(V, V, dscale, B, NV, h->stream));
+        for (int i = 0; i < m; ++i) {
+            double2* Vi = V + (int64_t)i * vs;
+            double2* Zi = Z + (int64_t)i * vs;
+            if ((s = dev_precond(h, Vi, Zi, B)) != HELM_OK) return s;
+            if ((s = dev_stencil(h, Zi, nullptr, Wv, B)) != HELM_OK) return s;
+            // CGS2
+            std::vector<cd> hcol((size_t)B * (i + 1), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(h, launch_multidot(V, vs, Wv, i + 1, B, NV, partial, nblk, dres, h->stream, &h->timer));
+                CK(h, cudaMemcpyAsync(hres.data(), dres, (size_t)B * (i + 1) * sizeof(double2),
+                                      cudaMemcpyDeviceToHost, h->stream));
+                CK(h, cudaStreamSynchronize(h->stream));
+                for (int b = 0; b < B; ++b)
+                    for (int k = 0; k <= i; ++k) {
+                        const double2 v = hres[(size_t)b * (i + 1) + k];
+                        const cd hv = active[b] ? cd(v.x, v.y) : cd(0.0);
+                        hcol[(size_t)b * (i + 1) + k] += hv;
+                        hcoef[(size_t)b * (i + 1) + k] = make_double2(-hv.real(), -hv.imag());
+                    }
+                CK(h, cudaMemcpyAsync(dcoef, hcoef.data(), (size_t)B * (i + 1) * sizeof(double2),
+                                      cudaMemcpyHostToDevice, h->stream));
+                CK(h, launch_multi_axpy(Wv, V, vs, dcoef, i + 1, B, NV, h->stream, &h->timer));
+            }
+            std::vector<double> hn;
+            if ((s = norms(Wv, hn)) != HELM_OK) return s;
+            bool still = false;
+            for (int b = 0; b < B; ++b) {
+                if (!active[b]) { hscale[b] = 0.0; continue; }
+                if (!isfinite(hn[b])) return fail(h, HELM_ENUMERIC, "non-finite Arnoldi norm");
+                cd* Hb = &H[(size_t)b * (m + 1) * m];
+                auto Hc = [&](int r, int c) -> cd& { return Hb[(size_t)c * (m + 1) + r]; };
+                for (int k = 0; k <= i; ++k) Hc(k, i) = hcol[(size_t)b * (i + 1) + k];
+                Hc(i + 1, i) = hn[b];
+                double* csb = &cs[(size_t)b * m];
+                cd* snb = &sn[(size_t)b * m];
+                for (int k = 0; k < i; ++k) {
+                    const cd t = csb[k] * Hc(k, i) + snb[k] * Hc(k + 1, i);
+                    Hc(k + 1, i) = -std::conj(snb[k]) * Hc(k, i) + csb[k] * Hc(k + 1, i);
+                    Hc(k, i) = t;
+                }
+                const cd a = Hc(i, i);
+                const double bb = hn[b];
+                const double rho = hypot(std::abs(a), bb);
+                if (std::abs(a) == 0.0) {
+                    csb[i] = 0.0;
+                    snb[i] = 1.0;
+                    Hc(i, i) = bb;
+                } else {
+                    csb[i] = std::abs(a) / rho;
+                    snb[i] = (a / std::abs(a)) * bb / rho;
+                    Hc(i, i) = (a / std::abs(a)) * rho;
+                }
+                Hc(i + 1, i) = 0.0;
+                cd* gb = &g[(size_t)b * (m + 1)];
+                gb[i + 1] = -std::conj(snb[i]) * gb[i];
+                gb[i] = csb[i] * gb[i];
+                iters[b] += 1;
+                kend[b] = i + 1;
+                const double est = std::abs(gb[i + 1]);
+                if (est <= tol * bnorm[b] || iters[b] >= maxit || hn[b] == 0.0) active[b] = 0;
+                hscale[b] = (active[b] && hn[b] > 0) ? 1.0 / hn[b] : 0.0;
+                still = still || active[b];
+            }
+            if (!still || i == m - 1) break;
+            CK(h, cudaMemcpyAsync(dscale, hscale.data(), B * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            CK(h, launch_scale(V + (int64_t)(i + 1) * vs, Wv, dscale, B, NV, h->stream));
+        }
+        // x += Z y,  H y = g (upper triangular, per column)
+        int kmax = 0;
+        for (int b = 0; b < B; ++b) kmax = std::max(kmax, kend[b]);
+        for (int b = 0; b < B; ++b) {
+            cd* Hb = &H[(size_t)b * (m + 1) * m];
+            auto Hc = [&](int r, int c) -> cd& { return Hb[(size_t)c * (m + 1) + r]; };
+            std::vector<cd> y(kend[b]);
+            for (int k = kend[b] - 1; k >= 0; --k) {
+                cd acc = g[(size_t)b * (m + 1) + k];
+                for (int l = k + 1; l < kend[b]; ++l) acc -= Hc(k, l) * y[l];
+                y[k] = acc / Hc(k, k);
+            }
+            for (int k = 0; k < kmax; ++k) {
+                const cd v = k < kend[b] ? y[k] : cd(0.0);
+                hcoef[(size_t)b * kmax + k] = make_double2(v.real(), v.imag());
+            }
+        }
+        if (kmax > 0) {
+            CK(h, cudaMemcpyAsync(dcoef, hcoef.data(), (size_t)B * kmax * sizeof(double2), cudaMemcpyHostToDevice,
+                                  h->stream));
+            CK(h, launch_multi_axpy(U, Z, vs, dcoef, kmax, B, NV, h->stream, &h->timer));
+        }
+    }
+    // final true residual
+    if ((s = dev_stencil(h, U, F, Wv, B)) != HELM_OK) return s;
+    std::vector<double> rn;
+    if ((s = norms(Wv, rn)) != HELM_OK) return s;
+    bool allconv = true;
+    for (int b = 0; b < B; ++b) {
+        relres[b] = bnorm[b] > 0 ? rn[b] / bnorm[b] : 0.0;
+        if (!(relres[b] <= tol)) allconv = false;
+    }
+    return allconv ? HELM_OK : fail(h, HELM_ENOTCONV, "GMRES reached maxit before the tolerance");
+}
+
+}  // namespace
+
+extern "C" {
+
+helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs, double tol, int restart, int maxit,
+                          helm_rhs_info* info) {
+    if (!h || !rhs || !u || nrhs < 1 || !(tol > 0) || restart < 1 || maxit < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "solve before factor");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
+    const bool din = is_device_ptr(rhs), dout = is_device_ptr(u);
+    helm_status s;
+    const double2* F = (const double2*)rhs;
+    double2* U = (double2*)u;
+    if (!din) {
+        if ((s = ws_reserve(h, h->ws_io_in, bytes)) != HELM_OK) return s;
+        CK(h, cudaMemcpyAsync(h->ws_io_in.p, rhs, bytes, cudaMemcpyHostToDevice, h->stream));
+        F = (const double2*)h->ws_io_in.p;
+    }
+    if (!dout) {
+        if ((s = ws_reserve(h, h->ws_io_out, bytes)) != HELM_OK) return s;
+        U = (double2*)h->ws_io_out.p;
+    }
+    std::vector<int> iters;
+    std::vector<double> relres;
+    helm_status st = dev_fgmres(h, F, U, nrhs, tol, restart, maxit, iters, relres);
+    if (st != HELM_OK && st != HELM_ENOTCONV) return st;
+    if (!dout) CK(h, cudaMemcpyAsync(u, U, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int b = 0; b < nrhs; ++b) info[b] = helm_rhs_info{iters[b], relres[b], ms};
+    return st;
+}
+
+helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc, const int64_t* rec_idx, int nrec,
+                             const double* d, double tol, double* misfit, double* grad_m) {
+    if (!h || !src_idx || !rec_idx || !d || !misfit || !grad_m || nsrc < 1 || nrec < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "gradient before factor");
+    const int64_t NV = nvol(h);
+    for (int i = 0; i < nsrc; ++i)
+        if (src_idx[i] < 0 || src_idx[i] >= NV) return fail(h, HELM_EINVAL, "source index out of range");
+    for (int i = 0; i < nrec; ++i)
+        if (rec_idx[i] < 0 || rec_idx[i] >= NV) return fail(h, HELM_EINVAL, "receiver index out of range");
+    const size_t vb = (size_t)nsrc * NV * sizeof(double2);
+    helm_status s;
+    // ws_grad holds F/Q, U, MU, gpad, gint, receivers, gathered values
+    const int64_t nint = h->n[0] * h->n[1] * h->n[2];
+    const size_t need = 3 * vb + (size_t)NV * sizeof(double) + (size_t)nint * sizeof(double) +
+                        (size_t)nrec * sizeof(int64_t) + (size_t)nsrc * nrec * sizeof(double2) + 256;
+    if ((s = ws_reserve(h, h->ws_grad, need)) != HELM_OK) return s;
+    double2* FQ = (double2*)h->ws_grad.p;
+    double2* U = FQ + (size_t)nsrc * NV;
+    double2* MU = U + (size_t)nsrc * NV;
+    double* gpad = (double*)(MU + (size_t)nsrc * NV);
+    double* gint = gpad + NV;
+    int64_t* drec = (int64_t*)(gint + nint);
+    double2* gath = (double2*)(drec + nrec);
+    // sources: discrete deltas 1/h^dim
+    const double amp = 1.0 / pow(h->h, h->dim);
+    CK(h, cudaMemsetAsync(FQ, 0, vb, h->stream));
+    const double2 a2 = make_double2(amp, 0.0);
+    for (int i = 0; i < nsrc; ++i)
+        CK(h, cudaMemcpyAsync(FQ + (size_t)i * NV + src_idx[i], &a2, sizeof(double2), cudaMemcpyHostToDevice,
+                              h->stream));
+    std::vector<int> iters;
+    std::vector<double> relres;
+    helm_status st = dev_fgmres(h, FQ, U, nsrc, tol, 20, 400, iters, relres);
+    if (st != HELM_OK) return st;
+    // residual at receivers and the misfit
+    CK(h, cudaMemcpyAsync(drec, rec_idx, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_gather(U, NV, drec, nrec, nsrc, gath, h->stream));
+    std::vector<double2> ur((size_t)nsrc * nrec);
+    CK(h, cudaMemcpyAsync(ur.data(), gath, ur.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::vector<double2> dd((size_t)nsrc * nrec);
+    const bool ddev = is_device_ptr(d);
+    if (ddev) CK(h, cudaMemcpy(dd.data(), d, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    else memcpy(dd.data(), d, dd.size() * sizeof(double2));
+    double J = 0.0;
+    // adjoint right-hand side q = S^-1 conj(R^T r), accumulated per index on the host
+    CK(h, cudaMemsetAsync(FQ, 0, vb, h->stream));
+    const int Nx = (int)h->N[0], Ny = (int)h->N[1];
+    for (int sidx = 0; sidx < nsrc; ++sidx) {
+        std::vector<std::pair<int64_t, cd>> acc;
+        for (int r = 0; r < nrec; ++r) {
+            const double2 u0 = ur[(size_t)sidx * nrec + r], d0 = dd[(size_t)sidx * nrec + r];
+            const cd res(u0.x - d0.x, u0.y - d0.y);
+            J += 0.5 * std::norm(res);
+            bool found = false;
+            for (auto& pr : acc)
+                if (pr.first == rec_idx[r]) { pr.second += res; found = true; }
+            if (!found) acc.push_back({rec_idx[r], res});
+        }
+        for (auto& pr : acc) {
+            const int64_t p = pr.first;
+            const int x = (int)(p % Nx), y = (int)((p / Nx) % Ny), z = (int)(p / ((int64_t)Nx * Ny));
+            cd S = (1.0 / h->gx_int[x]) * (1.0 / h->gy_int[y]);
+            if (h->dim == 3) S *= 1.0 / h->gz_int[z];
+            const cd q = std::conj(pr.second) / S;
+            const double2 q2 = make_double2(q.real(), q.imag());
+            CK(h, cudaMemcpyAsync(FQ + (size_t)sidx * NV + p, &q2, sizeof(double2), cudaMemcpyHostToDevice,
+                                  h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    st = dev_fgmres(h, FQ, MU, nsrc, tol, 20, 400, iters, relres);
+    if (st != HELM_OK) return st;
+    CK(h, launch_grad_accum(U, MU, h->geom, nsrc, gpad, h->stream));
+    CK(h, launch_fold(gpad, gint, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->stream));
+    if (is_device_ptr(grad_m))
+        CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    else
+        CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *misfit = J;
+    return HELM_OK;
+}
+
+double helm_dd_precond_factor_bytes(const helm_dd* h) {
+    if (!h) return 0.0;
+    double b = 0.0;
+    for (int j = 0; j < h->J; ++j) {
+        const double blk = (double)h->N[1] * h->strips[j].W * h->strips[j].W * h->esize;
+        b += 2.0 * blk * (j < h->J - 1 ? 2.0 : 1.0);
+    }
+    return b;
+}
+
+void helm_dd_dims(const helm_dd* h, int64_t N[3]) {
+    if (!h || !N) return;
+    for (int a = 0; a < 3; ++a) N[a] = h->N[a];
+}
+
+int helm_dd_strip_widths(const helm_dd* h, int* W, int cap) {
+    if (!h) return 0;
+    for (int j = 0; j < h->J && j < cap && W; ++j) W[j] = h->strips[j].W;
+    return h->J;
+}
+
+int helm_dd_interfaces(const helm_dd* h, int* beta, int cap) {
+    if (!h) return 0;
+    for (int j = 0; j <= h->J && j < cap && beta; ++j) beta[j] = h->beta[j];
+    return h->J + 1;
+}
+
+void helm_dd_destroy(helm_dd* h) {
+    if (!h) return;
+    if (!h->dev_ready && !h->own_stream) { delete h; return; }
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->timer.flush();
+    cudaFree(h->d_c);
+    cudaFree(h->d_k2);
+    cudaFree(h->d_tab);
+    cudaFree(h->d_strips);
+    cudaFree(h->d_ints);
+    cudaFree(h->d_status);
+    for (auto p : h->d_pool) cudaFree(p);
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
+                    &h->ws_small, &h->ws_grad})
+        ws_free(*w);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    cudaGetLastError();
+    delete h;
+}
+
+const char* helm_dd_last_error(const helm_dd* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

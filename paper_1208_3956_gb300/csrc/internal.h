@@ -1,0 +1,141 @@
+// Host-side declarations shared by the helm_dd translation units: the kernel
+// timer and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace helm {
+
+// Brackets launches with CUDA events on the launching stream and accumulates
+// their durations per kernel name (only while enabled).
+struct KernelTimer {
+    bool enabled = false;
+    struct Pending { int id; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<std::string> names;
+    std::vector<int64_t> counts;
+    std::vector<double> total_ms;
+    std::vector<cudaEvent_t> pool;
+
+    int id_of(const char* name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return (int)i;
+        names.emplace_back(name);
+        counts.push_back(0);
+        total_ms.push_back(0.0);
+        return (int)names.size() - 1;
+    }
+    cudaEvent_t get_event() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // Resolve all pending pairs (call after the stream has been synchronised).
+    void flush() {
+        for (auto& p : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                counts[p.id] += 1;
+                total_ms[p.id] += ms;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void reset() { flush(); for (auto& c : counts) c = 0; for (auto& t : total_ms) t = 0; }
+    ~KernelTimer() {
+        for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct TimedLaunch {
+    KernelTimer* t;
+    cudaStream_t s;
+    int id = -1;
+    cudaEvent_t a = nullptr;
+    TimedLaunch(KernelTimer* tm, const char* name, cudaStream_t st) : t(tm), s(st) {
+        if (t && t->enabled) {
+            id = t->id_of(name);
+            a = t->get_event();
+            cudaEventRecord(a, s);
+        }
+    }
+    ~TimedLaunch() {
+        if (t && t->enabled && a) {
+            cudaEvent_t b = t->get_event();
+            cudaEventRecord(b, s);
+            t->pending.push_back({id, a, b});
+        }
+    }
+};
+
+// ---- factor.cu
+size_t factor_smem_bytes(int Wmax, size_t esize);
+template <typename C>
+cudaError_t launch_factor(const Geom& g, int Wmax, void* Sinv, void* GT, void* GB, void* Rinv, void* E,
+                          void* F, int* status, cudaStream_t s, KernelTimer* tm);
+
+// ---- sweep.cu: one strip solve of the sweep.
+// Right-hand side of strip st for row k, column c (padded column gc = lo-lpml+c):
+//   r = [mlo <= gc <= mhi] src(b,k,gc) + [gc == t0 or gc == t0+1] tcoef * tin(b,k)
+// solved for x on the strip grid; then x is scattered to dst on padded columns
+// olo..ohi (dst = x, or dst = base + x when base != null) and the transfer
+// difference tout(b,k) = x(to1) - x(to0) (strip-local columns) is written.
+struct SweepStep {
+    const double2* src;     // [B][Ny][Nx] FP64
+    int mlo, mhi;           // mask of src columns entering the right-hand side
+    const double2* tin;     // [B][Ny] incoming transfer difference, or null
+    int t0;                 // first padded column receiving the transfer
+    double tcoef;           // transfer coefficient (-1/h^2 forward, +1/h^2 backward)
+    double2* dst;           // [B][Ny][Nx] output field
+    const double2* base;    // optional field added to x on output
+    int olo, ohi;           // padded output columns
+    double2* tout;          // [B][Ny] outgoing transfer difference, or null
+    int to0, to1;           // strip-local columns of the outgoing difference
+};
+
+struct SweepWork {
+    void* ybuf;             // [B][Ny][Wmax] working precision
+    int Wmax;
+    int B;
+};
+
+template <typename C>
+cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const SweepStep& step,
+                               const SweepWork& wk, const void* Sinv, const void* GT, const void* GB,
+                               const void* Rinv, const void* E, const void* F, cudaStream_t s,
+                               KernelTimer* tm);
+
+// ---- field.cu: FP64 grid kernels
+cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, int nz, int w, double omega,
+                      cudaStream_t s);
+// out = (f ? f - A u : A u), paper form, B fields
+cudaError_t launch_stencil(const Geom& g, const double2* u, const double2* f, double2* out, int B,
+                           cudaStream_t s, KernelTimer* tm);
+cudaError_t launch_copy_cols(const double2* src, double2* dst, int B, int Nx, int Ny, int Nz, int xlo, int xhi,
+                             cudaStream_t s);
+// partial[b][i][blk] for h[b][i] = sum_n conj(V_i[b][n]) w[b][n]; V_i at V + i*vstride
+cudaError_t launch_multidot(const double2* V, int64_t vstride, const double2* w, int nv, int B, int64_t N,
+                            double2* partial, int nblk, double2* out, cudaStream_t s, KernelTimer* tm);
+// w[b] += sum_i coef[b][i] V_i[b]  (coef device [B][nv])
+cudaError_t launch_multi_axpy(double2* w, const double2* V, int64_t vstride, const double2* coef, int nv,
+                              int B, int64_t N, cudaStream_t s, KernelTimer* tm);
+// dst[b] = src[b] * scale[b] (scale real, device [B])
+cudaError_t launch_scale(double2* dst, const double2* src, const double* scale, int B, int64_t N,
+                         cudaStream_t s);
+cudaError_t launch_grad_accum(const double2* U, const double2* MU, const Geom& g, int nsrc, double* gpad,
+                              cudaStream_t s);
+cudaError_t launch_fold(const double* gpad, double* gint, int dim, int nx, int ny, int nz, int w, cudaStream_t s);
+cudaError_t launch_gather(const double2* U, int64_t ustride, const int64_t* idx, int nidx, int B,
+                          double2* out, cudaStream_t s);
+
+}  // namespace helm

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (from the method's precision, written here):
+  stencil A u ............ 1e-13 relative (FP64, same formula, rounding order only)
+  preconditioner P f ..... 1e-10 relative in FP64; 2e-4 in mixed precision
+                           (complex64 factors: relative error ~ cond x 2^-24)
+  solve .................. true residual <= tol, solution within 1e-4 relative
+                           L2 of the oracle's, iterations within +-1
+  gradient ............... 1e-3 relative
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.helm_oracle import HelmholtzDD, misfit_and_gradient, receiver_data
+from paper_1208_3956_gb300 import helm, media
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+# (n = (n_x, n_y), w_outer, w_sub, J, chunks): ragged sizes, several tiles and chunks
+CASES = [
+    ((37, 29), 5, 4, 3, 3),
+    ((61, 45), 6, 5, 4, 5),
+    ((61, 45), 6, 5, 4, 1),
+    ((40, 33), 4, 3, 1, 4),
+    ((90, 70), 8, 6, 6, 7),
+]
+
+
+def make(n, w_o, w_s, J, chunks, prec, seed=5, c_ref=None):
+    c = media.smooth_medium(n, 3.0, 1.0, 2.0, seed)
+    h = 1.0 / 32
+    omega = media.omega_for(c, h, 8.0)
+    g = helm.HelmDD(c, h, omega, w_o, w_s, J, prec, c_ref=c_ref, chunks=chunks)
+    o = HelmholtzDD(c, h, omega, w_o, w_s, J, c_ref=c_ref)
+    return g, o
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    helm.load()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_matvec_matches_oracle(dim):
+    n = (37, 29) if dim == 2 else (13, 11, 9)
+    c = media.smooth_medium(n, 2.0, 1.0, 2.0, 1)
+    h = 1.0 / 24
+    omega = media.omega_for(c, h, 8.0)
+    g = helm.HelmDD(c, h, omega, 5, 3, 2 if dim == 2 else 1, "fp64")
+    o = HelmholtzDD(c, h, omega, 5, 3, 2 if dim == 2 else 1)
+    u = media.random_rhs((3,) + g.shape, 7)
+    Au = g.matvec(u)
+    ref = np.stack([o.matvec(u[b]) for b in range(3)])
+    assert rel(Au, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_precond_fp64_matches_oracle(case):
+    g, o = make(*case, "fp64")
+    g.factor()
+    o.factor()
+    f = media.random_rhs((2,) + g.shape, 3)
+    Pf = g.apply_precond(f)
+    ref = np.stack([o.apply_precond(f[b]) for b in range(2)])
+    assert rel(Pf, ref) <= 1e-10
+
+
+def test_precond_point_source_fp64_const127():
+    wl = media.WORKLOADS["const127"]
+    c = media.medium("const127")
+    omega = media.omega_for(c, wl.h, wl.ppw)
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "fp64").factor()
+    o = HelmholtzDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J).factor()
+    f = media.point_sources(wl.n, wl.w_outer, wl.h, media.source_positions("const127"))
+    assert rel(g.apply_precond(f), o.apply_precond(f[0])[None]) <= 1e-10
+
+
+@pytest.mark.parametrize("case", CASES[:2])
+def test_precond_mixed_close_to_oracle(case):
+    g, o = make(*case, "mixed")
+    g.factor()
+    o.factor()
+    f = media.random_rhs(g.shape, 4)
+    assert rel(g.apply_precond(f), o.apply_precond(f)) <= 2e-4
+
+
+def test_chunking_does_not_change_the_preconditioner():
+    outs = []
+    for P in (1, 2, 5, 9):
+        g, _ = make((61, 45), 6, 5, 4, P, "fp64")
+        g.factor()
+        outs.append(g.apply_precond(media.random_rhs(g.shape, 8)))
+    for x in outs[1:]:
+        assert rel(x, outs[0]) <= 1e-11
+
+
+def test_one_strip_preconditioner_is_the_inverse():
+    g, o = make((40, 33), 4, 3, 1, 4, "fp64")
+    g.factor()
+    f = media.random_rhs(g.shape, 9)
+    assert rel(g.apply_precond(f), o.direct_solve(f)) <= 1e-10
+
+
+def test_residual_support_invariant_on_gpu_output():
+    """f - A P f vanishes off columns beta_j+1, beta_j+2 (checked with the oracle's A)."""
+    g, o = make((90, 70), 8, 6, 6, 7, "fp64")
+    g.factor()
+    f = media.random_rhs(g.shape, 10)
+    r = f - o.matvec(g.apply_precond(f))
+    b = g.interfaces()
+    cols = sorted({b[j] + 1 for j in range(1, 6)} | {b[j] + 2 for j in range(1, 6)})
+    assert np.linalg.norm(np.delete(r, cols, axis=-1)) <= 1e-11 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_matches_oracle_const127(prec):
+    wl = media.WORKLOADS["const127"]
+    c = media.medium("const127")
+    omega = media.omega_for(c, wl.h, wl.ppw)
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, prec).factor()
+    o = HelmholtzDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J).factor()
+    f = media.point_sources(wl.n, wl.w_outer, wl.h, media.source_positions("const127"))
+    u, info = g.solve(f, tol=1e-6)
+    uo, it_o, rr_o, _ = o.solve(f[0], tol=1e-6)
+    assert info[0]["rel_res"] <= 1e-6
+    assert np.linalg.norm(f[0] - o.matvec(u[0])) / np.linalg.norm(f[0]) <= 1.000001e-6
+    assert abs(info[0]["iters"] - it_o) <= 1
+    assert rel(u[0], uo) <= 1e-4
+    assert rel(u[0], o.direct_solve(f[0])) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_heterogeneous_matches_oracle(prec):
+    g, o = make((90, 70), 8, 6, 6, 7, prec)
+    g.factor()
+    o.factor()
+    f = media.point_sources(g.n, 8, g.h, [(45, 35)])
+    u, info = g.solve(f, tol=1e-6)
+    uo, it_o, _, _ = o.solve(f[0], tol=1e-6)
+    assert info[0]["rel_res"] <= 1e-6
+    assert abs(info[0]["iters"] - it_o) <= 1
+    assert rel(u[0], uo) <= 1e-4
+
+
+def test_batched_solve_equals_single_solves():
+    g, _ = make((61, 45), 6, 5, 4, 5, "mixed")
+    g.factor()
+    pts = [(10, 5), (30, 20), (50, 40)]
+    f = media.point_sources(g.n, 6, g.h, pts)
+    ub, ib = g.solve(f, tol=1e-8)
+    for s in range(3):
+        us, is_ = g.solve(f[s:s + 1], tol=1e-8)
+        assert rel(ub[s], us[0]) <= 1e-6
+        assert ib[s]["iters"] == is_[0]["iters"]
+
+
+def test_device_pointer_path_matches_host_path():
+    torch = pytest.importorskip("torch")
+    g, _ = make((61, 45), 6, 5, 4, 5, "fp64")
+    g.factor()
+    f = media.random_rhs((2,) + g.shape, 12)
+    ph = g.apply_precond(f)
+    fd = torch.as_tensor(f, device="cuda")
+    pd = g.apply_precond(fd)
+    assert rel(pd.cpu().numpy(), ph) <= 1e-14
+    ud, _ = g.solve(fd, tol=1e-8)
+    uh, _ = g.solve(f, tol=1e-8)
+    assert rel(ud.cpu().numpy(), uh) <= 1e-12
+
+
+def test_gradient_matches_oracle():
+    n = (40, 30)
+    w = 5
+    h = 1.0 / 32
+    c0 = media.smooth_medium(n, 3.0, 1.0, 2.0, 3)
+    c = c0 * (1 + 0.1 * media.smooth_medium(n, 3.0, 0.0, 1.0, 4))
+    omega = media.omega_for(c0, h, 8.0)
+    cref = 2.5
+    src = [media.padded_index((x, 0), n, w) for x in (5, 20, 35)]
+    rec = [media.padded_index((x, 0), n, w) for x in range(0, 40, 4)]
+    d = receiver_data(c0, h, omega, w, src, rec, c_ref=cref)
+    Jo, go = misfit_and_gradient(c, h, omega, w, src, rec, d, c_ref=cref)
+    for prec in ("fp64", "mixed"):
+        g = helm.HelmDD(c, h, omega, w, 4, 3, prec, c_ref=cref).factor()
+        Jg, gg = g.gradient(src, rec, d, tol=1e-9)
+        assert abs(Jg - Jo) <= 1e-3 * abs(Jo)
+        assert rel(gg, go) <= 1e-3
+
+
+def test_autograd_misfit():
+    torch = pytest.importorskip("torch")
+    n = (40, 30)
+    w, h = 5, 1.0 / 32
+    c0 = media.smooth_medium(n, 3.0, 1.0, 2.0, 3)
+    omega = media.omega_for(c0, h, 8.0)
+    src = [media.padded_index((x, 0), n, w) for x in (5, 35)]
+    rec = [media.padded_index((x, 0), n, w) for x in range(0, 40, 5)]
+    d = receiver_data(c0, h, omega, w, src, rec, c_ref=2.5)
+    c = c0 * 1.05
+    m = torch.tensor(1.0 / c ** 2, dtype=torch.float64, requires_grad=True)
+    spec = dict(h=h, omega=omega, w_outer=w, w_sub=4, J=3, src=src, rec=rec, d=d, c_ref=2.5,
+                precision="fp64", tol=1e-9)
+    J = helm.misfit(m, spec)
+    J.backward()
+    Jo, go = misfit_and_gradient(c, h, omega, w, src, rec, d, c_ref=2.5)
+    assert abs(J.item() - Jo) <= 1e-6 * Jo
+    assert rel(m.grad.numpy(), go) <= 1e-3
+
+
+def test_state_and_argument_errors():
+    g, _ = make((37, 29), 5, 4, 3, 3, "fp64")
+    f = media.random_rhs(g.shape, 1)
+    with pytest.raises(helm.HelmError) as ei:
+        g.apply_precond(f)
+    assert ei.value.status == -4
+    with pytest.raises(helm.HelmError) as ei:
+        g.solve(f)
+    assert ei.value.status == -4
+    g.factor()
+    with pytest.raises(helm.HelmError) as ei:
+        g.solve(f, tol=1e-6, maxit=1)
+    assert ei.value.status == -5
+    u, info = g.solve(f, tol=1e-6, maxit=1, check=False)
+    assert info[0]["iters"] == 1 and np.all(np.isfinite(u))
+
+
+@pytest.mark.slow
+def test_full_size_smooth1023_mixed_solve_properties():
+    """Bench workload: 1055^2 padded, J=64, one source, mixed precision.
+
+    Properties checked with the oracle's sparse operator (any size): the true
+    residual of the returned solution and the residual-support invariant of P.
+    """
+    wl = media.WORKLOADS["smooth1023"]
+    c = media.medium("smooth1023")
+    omega = media.omega_for(c, wl.h, wl.ppw)
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed").factor()
+    o = HelmholtzDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J)
+    f = media.point_sources(wl.n, wl.w_outer, wl.h, media.source_positions("smooth1023"))
+    u, info = g.solve(f, tol=1e-6)
+    r = np.linalg.norm(f[0] - o.matvec(u[0])) / np.linalg.norm(f[0])
+    assert info[0]["rel_res"] <= 1e-6 and r <= 1.000001e-6
+    assert 2 <= info[0]["iters"] <= 20
+    g64 = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "fp64").factor()
+    x = media.random_rhs(g64.shape, 2)
+    res = x - o.matvec(g64.apply_precond(x))
+    b = g64.interfaces()
+    cols = sorted({b[j] + 1 for j in range(1, wl.J)} | {b[j] + 2 for j in range(1, wl.J)})
+    assert np.linalg.norm(np.delete(res, cols, axis=-1)) <= 1e-9 * np.linalg.norm(x)
