@@ -76,6 +76,7 @@ struct StripDev {
     int64_t fac;   // element offset of this strip's blocks in the factor pools (Ny blocks of BS)
     int64_t red;   // element offset of this strip's reduced-system blocks ((P-1) blocks of BS)
     int64_t bs;    // elements per stored W x W block (column-major, padded to 16 bytes)
+    int64_t ctab;  // offset of this strip's s_x(c) (W entries) in the working-precision table
 };
 
 // Global geometry and tables (device pointers, FP64).
@@ -96,6 +97,14 @@ struct Geom {
     const int* r0;             // chunk p covers rows r0[p] .. r1[p]-1; separator p is row r1[p]
     const int* r1;
     const int* rowmap;         // row k -> chunk p (>= 0) or separator q as -(q+1)
+    // working-precision (complex64 or complex128) tables for the sweep:
+    //   ct[ct_sy + k] = s_y(k) = 1/alpha_y(y_k)          (k < Ny)
+    //   ct[ct_cy + k] = -alpha_y(y_{k-1/2}) / h^2       (k <= Ny)
+    //   ct[strip.ctab + c] = s_x(c) on the strip grid
+    // so that the y-coupling of rows k-1, k is C_k(c) = s_x(c) ct[ct_cy + k]
+    // and the right-hand-side scaling is s_x(c) s_y(k).
+    const void* ct;
+    int64_t ct_sy, ct_cy;
 };
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }

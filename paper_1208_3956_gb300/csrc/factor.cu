@@ -24,6 +24,10 @@
 
 namespace helm {
 
+// Spikes are stored row-major (row c contiguous over columns a) so that the
+// correction step can read only the rows it outputs; e is a column-major index.
+__device__ __forceinline__ int trp(int e, int W) { return (e % W) * W + e / W; }
+
 template <typename C>
 __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT, C* __restrict__ GB,
                                int* __restrict__ status) {
@@ -78,7 +82,7 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
         for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
             const int b = e / W;
             Y[e] = cmul(X[e], dv[b]);
-            GBs[(int64_t)(r1 - 1) * bs + e] = Y[e];
+            GBs[(int64_t)(r1 - 1) * bs + trp(e, W)] = Y[e];
         }
         __syncthreads();
         // X <- Y (current spike block)
@@ -89,7 +93,7 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
             __syncthreads();
             // GB_k = -Sinv_k diag(C_{k+1}) GB_{k+1}
             block_gemm_dscale(Y, M, dv, X, W, false, (typename CT<C>::R)-1);
-            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GBs[(int64_t)k * bs + e] = Y[e];
+            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GBs[(int64_t)k * bs + trp(e, W)] = Y[e];
             __syncthreads();
             block_copy(X, Y, W * W);
         }
@@ -105,7 +109,7 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
         for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
             const int b = e / W;
             X[e] = cmul(M[e], dv[b]);
-            GTs[(int64_t)r0 * bs + e] = X[e];
+            GTs[(int64_t)r0 * bs + trp(e, W)] = X[e];
         }
         __syncthreads();
         for (int k = r0 + 1; k < r1; ++k) {
@@ -113,7 +117,7 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
             for (int c = threadIdx.x; c < W; c += blockDim.x) dv[c] = CT<C>::from(strip_coupling(g, st, k, c));
             __syncthreads();
             block_gemm_dscale(Y, M, dv, X, W, false, (typename CT<C>::R)-1);
-            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GTs[(int64_t)k * bs + e] = Y[e];
+            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GTs[(int64_t)k * bs + trp(e, W)] = Y[e];
             __syncthreads();
             block_copy(X, Y, W * W);
         }
@@ -122,12 +126,12 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
         for (int k = r1 - 2; k >= r0; --k) {
             for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
                 M[e] = SinvS[(int64_t)k * bs + e];
-                Y[e] = GTs[(int64_t)k * bs + e];
+                Y[e] = GTs[(int64_t)k * bs + trp(e, W)];
             }
             for (int c = threadIdx.x; c < W; c += blockDim.x) dv[c] = CT<C>::from(strip_coupling(g, st, k + 1, c));
             __syncthreads();
             block_gemm_dscale(Y, M, dv, X, W, true, (typename CT<C>::R)-1);
-            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GTs[(int64_t)k * bs + e] = Y[e];
+            for (int e = threadIdx.x; e < W * W; e += blockDim.x) GTs[(int64_t)k * bs + trp(e, W)] = Y[e];
             __syncthreads();
             block_copy(X, Y, W * W);
         }
@@ -170,8 +174,8 @@ __global__ void k_factor_reduced(Geom g, const C* __restrict__ GT, const C* __re
         for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
             const int r = e % W;
             C t = M[e];
-            t = csub(t, cmul(d0[r], GBs[(int64_t)last_q * bs + e]));
-            t = csub(t, cmul(d1[r], GTs[(int64_t)first_q1 * bs + e]));
+            t = csub(t, cmul(d0[r], GBs[(int64_t)last_q * bs + trp(e, W)]));
+            t = csub(t, cmul(d1[r], GTs[(int64_t)first_q1 * bs + trp(e, W)]));
             M[e] = t;
         }
         __syncthreads();
@@ -179,7 +183,7 @@ __global__ void k_factor_reduced(Geom g, const C* __restrict__ GT, const C* __re
             // L_q = -diag(C_s) GT_q(last) -> X ; M -= L_q F_{q-1} (F_{q-1} in Y)
             for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
                 const int r = e % W;
-                X[e] = cneg(cmul(d0[r], GTs[(int64_t)last_q * bs + e]));
+                X[e] = cneg(cmul(d0[r], GTs[(int64_t)last_q * bs + trp(e, W)]));
             }
             __syncthreads();
             block_gemm_dscale<C>(M, X, nullptr, Y, W, true, (R)-1);
@@ -201,7 +205,7 @@ __global__ void k_factor_reduced(Geom g, const C* __restrict__ GT, const C* __re
         if (q + 1 < g.P - 1) {
             for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
                 const int r = e % W;
-                X[e] = cneg(cmul(d1[r], GBs[(int64_t)first_q1 * bs + e]));
+                X[e] = cneg(cmul(d1[r], GBs[(int64_t)first_q1 * bs + trp(e, W)]));
             }
             __syncthreads();
             block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)1);

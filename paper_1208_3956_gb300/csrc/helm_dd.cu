@@ -73,6 +73,9 @@ struct helm_dd {
     double* d_c = nullptr;
     double* d_k2 = nullptr;
     double2* d_tab = nullptr;       // global axis tables + per-strip x tables
+    void* d_ct = nullptr;           // working-precision sweep tables
+    int* d_counters = nullptr;      // per-tile arrival counters of the sweep
+    int zrows = 1;
     StripDev* d_strips = nullptr;
     int* d_ints = nullptr;          // r0 | r1 | rowmap
     void* d_pool[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Sinv GT GB Rinv E F
@@ -83,12 +86,14 @@ struct helm_dd {
     bool dev_ready = false;
     // workspaces
     struct Ws { void* p = nullptr; size_t bytes = 0; };
-    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
+    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_parts, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
     KernelTimer timer;
     std::string err;
 };
 
 namespace {
+
+constexpr int kMaxTiles = 4096;   // RHS tiles of one sweep launch (4 RHS per tile)
 
 helm_status fail(helm_dd* h, helm_status s, const std::string& msg) {
     if (h) h->err = msg;
@@ -223,6 +228,9 @@ helm_status ensure_device(helm_dd* h) {
     CK(h, cudaMalloc(&h->d_c, nint * sizeof(double)));
     CK(h, cudaMalloc(&h->d_k2, nvol(h) * sizeof(double)));
     CK(h, cudaMalloc(&h->d_status, sizeof(int)));
+    CK(h, cudaMalloc(&h->d_counters, kMaxTiles * sizeof(int)));
+    CK(h, cudaMemsetAsync(h->d_counters, 0, kMaxTiles * sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     CK(h, cudaMemcpyAsync(h->d_c, h->c.data(), nint * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_k2(h->d_c, h->d_k2, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->omega,
                     h->stream));
@@ -252,6 +260,27 @@ helm_status prepare_geom(helm_dd* h) {
         s.tab = (int64_t)tabs.size() - stab0;
         for (int c = 0; c < s.W; ++c) tabs.push_back(strip_alpha_at(h, s, 2 * c));
         for (int m = 0; m <= s.W; ++m) tabs.push_back(strip_alpha_at(h, s, 2 * m - 1));
+    }
+    // working-precision sweep tables: s_y, y-coupling -alpha_y(k-1/2)/h^2, strip s_x
+    std::vector<cd> ctv;
+    for (int k = 0; k < Ny; ++k) ctv.push_back(1.0 / h->gy_int[k]);
+    const double ih2 = 1.0 / (h->h * h->h);
+    for (int k = 0; k <= Ny; ++k) ctv.push_back(-h->gy_half[k] * ih2);
+    for (auto& s : h->strips) {
+        s.ctab = (int64_t)ctv.size();
+        for (int c = 0; c < s.W; ++c) ctv.push_back(1.0 / tabs[stab0 + s.tab + c]);
+    }
+    if (h->d_ct) cudaFree(h->d_ct);
+    h->d_ct = nullptr;
+    CK(h, cudaMalloc(&h->d_ct, ctv.size() * h->esize));
+    if (h->esize == sizeof(float2)) {
+        std::vector<float2> f(ctv.size());
+        for (size_t i = 0; i < ctv.size(); ++i) f[i] = make_float2((float)ctv[i].real(), (float)ctv[i].imag());
+        CK(h, cudaMemcpy(h->d_ct, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<double2> f(ctv.size());
+        for (size_t i = 0; i < ctv.size(); ++i) f[i] = to_d2h(ctv[i]);
+        CK(h, cudaMemcpy(h->d_ct, f.data(), f.size() * sizeof(double2), cudaMemcpyHostToDevice));
     }
     std::vector<double2> tab2(tabs.size());
     for (size_t i = 0; i < tabs.size(); ++i) tab2[i] = to_d2h(tabs[i]);
@@ -293,6 +322,11 @@ helm_status prepare_geom(helm_dd* h) {
     g.r0 = h->d_ints;
     g.r1 = h->d_ints + h->P;
     g.rowmap = h->d_ints + 2 * h->P;
+    g.ct = h->d_ct;
+    g.ct_sy = 0;
+    g.ct_cy = Ny;
+    h->zrows = h->P - 1;
+    for (int p = 0; p < h->P; ++p) h->zrows = std::max(h->zrows, h->r1[p] - h->r0[p]);
     CK(h, cudaStreamSynchronize(h->stream));
     h->prepared = true;
     return HELM_OK;
@@ -445,6 +479,19 @@ helm_status dev_stencil(helm_dd* h, const double2* u, const double2* f, double2*
     return HELM_OK;
 }
 
+// Device error word: 7 = a bounded wait in a sweep kernel gave up.
+helm_status check_device_status(helm_dd* h) {
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st == 7) {
+        cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+        cudaMemsetAsync(h->d_counters, 0, kMaxTiles * sizeof(int), h->stream);
+        return fail(h, HELM_ETIMEOUT, "a bounded device wait in the sweep gave up");
+    }
+    return HELM_OK;
+}
+
 // P applied to B device fields (Section 2.1): in -> out (distinct buffers).
 helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     const int64_t NV = nvol(h);
@@ -455,11 +502,14 @@ helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     if ((s = ws_reserve(h, h->ws_T0, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_T1, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_Y, (size_t)B * Ny * h->Wmax * h->esize)) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_parts, (size_t)B * std::max(h->P - 1, 1) * 2 * h->Wmax * h->esize)) != HELM_OK)
+        return s;
+    if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
     double2* V = (double2*)h->ws_V.p;
     double2* G = (double2*)h->ws_G.p;
     double2* Tin = (double2*)h->ws_T0.p;
     double2* Tout = (double2*)h->ws_T1.p;
-    SweepWork wk{h->ws_Y.p, h->Wmax, B};
+    SweepWork wk{h->ws_Y.p, h->ws_parts.p, h->d_counters, h->d_status, h->Wmax, B, h->zrows};
     const int J = h->J;
     const auto& beta = h->beta;
     const double ih2 = 1.0 / (h->h * h->h);
@@ -548,6 +598,7 @@ helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int
         doutp = (double2*)h->ws_io_out.p;
     }
     if ((s = dev_precond(h, dinp, doutp, nrhs)) != HELM_OK) return s;
+    if ((s = check_device_status(h)) != HELM_OK) return s;
     if (!dout) CK(h, cudaMemcpyAsync(out, doutp, bytes, cudaMemcpyDeviceToHost, h->stream));
     else if ((void*)doutp != (void*)out)
         CK(h, cudaMemcpyAsync(out, doutp, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -781,6 +832,8 @@ helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs, do
     std::vector<double> relres;
     helm_status st = dev_fgmres(h, F, U, nrhs, tol, restart, maxit, iters, relres);
     if (st != HELM_OK && st != HELM_ENOTCONV) return st;
+    helm_status ds = check_device_status(h);
+    if (ds != HELM_OK) return ds;
     if (!dout) CK(h, cudaMemcpyAsync(u, U, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -912,7 +965,9 @@ void helm_dd_destroy(helm_dd* h) {
     cudaFree(h->d_ints);
     cudaFree(h->d_status);
     for (auto p : h->d_pool) cudaFree(p);
-    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
+    cudaFree(h->d_ct);
+    cudaFree(h->d_counters);
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
                     &h->ws_small, &h->ws_grad})
         ws_free(*w);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);

@@ -105,8 +105,12 @@ struct SweepStep {
 
 struct SweepWork {
     void* ybuf;             // [B][Ny][Wmax] working precision
+    void* parts;            // [B][P-1][2][Wmax] working precision
+    int* counters;          // per RHS tile, zero between launches
+    int* status;            // error word (7 = bounded wait timed out)
     int Wmax;
     int B;
+    int zrows;              // max(rows of the largest chunk, P-1)
 };
 
 template <typename C>
