@@ -24,8 +24,6 @@
 
 namespace helm {
 
-static constexpr int kNW = 4;                 // warps per CTA
-static constexpr int kThreads = 32 * kNW;
 static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -117,7 +115,7 @@ __device__ __forceinline__ C* yrow(const SweepArgs& A, int b, int k) {
 
 // Shared-memory carve-up (bytes), identical on host and device.
 struct SweepSmem {
-    uint32_t slots, zb, tv, red, mbar, flags, total;
+    uint32_t slots, zb, tv, tv2, cx, cy, mbar, flags, total;
 };
 __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, int zrows, int Bt, int W,
                                                 int esz) {
@@ -126,80 +124,36 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     s.slots = o; o += ring * slot_bytes;
     s.zb = o; o += ((uint32_t)zrows * Bt * W * esz + 15u) & ~15u;
     s.tv = o; o += (uint32_t)Bt * 64 * esz;
-    s.red = o; o += (uint32_t)kNW * Bt * 64 * esz;
+    s.tv2 = o; o += (uint32_t)Bt * 64 * esz;
+    s.cx = o; o += 64u * esz;
+    s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
     s.mbar = o; o += kMaxRing * 8;
     s.flags = o; o += 16;
     s.total = o;
     return s;
 }
 
-// Block ring: load number G goes to slot G % ring with parity (G / ring) & 1.
-template <typename C>
-struct Ring {
-    unsigned char* slots;
-    uint64_t* mbar;
-    int ring;
-    uint32_t slot_bytes;
-    __device__ C* slot(int G) const { return reinterpret_cast<C*>(slots + (size_t)(G % ring) * slot_bytes); }
-    __device__ void issue(int G, const C* src) const {   // one thread
-        uint64_t* m = &mbar[G % ring];
-        fence_proxy_async();
-        mbar_expect_tx(m, slot_bytes);
-        bulk_g2s(slots + (size_t)(G % ring) * slot_bytes, src, slot_bytes, m);
-    }
-    __device__ bool wait(int G) const { return mbar_wait(&mbar[G % ring], (uint32_t)((G / ring) & 1)); }
-};
-
-// partial products red[w][b][r] = sum_{a in warp w's range} S(r,a) t[b][a]
-template <typename C>
-__device__ __forceinline__ void warp_partial(const C* __restrict__ S, const C* __restrict__ tv, C* red, int W,
-                                             int nb, int Bt) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int per = (W + kNW - 1) / kNW;
-    const int a0 = w * per, a1 = imin(W, a0 + per);
-    const bool r0ok = l < W, r1ok = l + 32 < W;
-    for (int b = 0; b < nb; ++b) {
-        const C* tb = tv + b * 64;
-        C e0 = CT<C>::zero(), o0 = CT<C>::zero(), e1 = CT<C>::zero(), o1 = CT<C>::zero();
-        int a = a0;
-        for (; a + 1 < a1; a += 2) {
-            const C t0 = tb[a], t1 = tb[a + 1];
-            if (r0ok) { e0 = cfma(S[a * W + l], t0, e0); o0 = cfma(S[(a + 1) * W + l], t1, o0); }
-            if (r1ok) { e1 = cfma(S[a * W + l + 32], t0, e1); o1 = cfma(S[(a + 1) * W + l + 32], t1, o1); }
-        }
-        if (a < a1) {
-            const C t0 = tb[a];
-            if (r0ok) e0 = cfma(S[a * W + l], t0, e0);
-            if (r1ok) e1 = cfma(S[a * W + l + 32], t0, e1);
-        }
-        C* rb = red + (w * Bt + b) * 64;
-        rb[l] = cadd(e0, o0);
-        rb[l + 32] = cadd(e1, o1);
-    }
-}
-
-template <typename C>
-__device__ __forceinline__ C red_sum(const C* red, int b, int c, int Bt) {
-    C s = red[b * 64 + c];
-#pragma unroll
-    for (int w = 1; w < kNW; ++w) s = cadd(s, red[(w * Bt + b) * 64 + c]);
-    return s;
-}
-
-__device__ __forceinline__ bool block_any(bool v) { return __syncthreads_or(v ? 1 : 0) != 0; }
-
 // ------------------------------------------------------------------ chunk + separators
-template <typename C>
-__global__ void __launch_bounds__(kThreads) k_sweep_chunk(SweepArgs A) {
+// Matrix-vector layout of one chain step: the CTA has ceil(W/8) warps; lane l of
+// warp w owns row r = 8w + l/4 and the columns a = l%4 + 4j, j < NJ, of the
+// column-major W x W block in shared memory.  Offsets are precomputed once and
+// clamped into the block (a clamped column meets a zero entry of the vector, a
+// clamped row is computed but never stored), and two xor shuffles complete the
+// row sums.
+template <typename C, int NJ>
+__global__ void __launch_bounds__(256) k_sweep_chunk(SweepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = A.st.W;
     const int esz = (int)sizeof(C);
     const SweepSmem L = sweep_smem(A.ring, A.slot_bytes, A.zrows, A.Bt, W, esz);
-    Ring<C> R{smem + L.slots, reinterpret_cast<uint64_t*>(smem + L.mbar), A.ring, A.slot_bytes};
+    unsigned char* slots = smem + L.slots;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
     C* zb = reinterpret_cast<C*>(smem + L.zb);       // [zrows][Bt][W]
-    C* tv = reinterpret_cast<C*>(smem + L.tv);       // [Bt][64]
-    C* red = reinterpret_cast<C*>(smem + L.red);     // [NW][Bt][64]
-    int* flags = reinterpret_cast<int*>(smem + L.flags);
+    C* tin = reinterpret_cast<C*>(smem + L.tv);      // [Bt][64] vector entering the step
+    C* tout = reinterpret_cast<C*>(smem + L.tv2);    // [Bt][64] vector entering the next step
+    C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
+    C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
+    volatile int* flags = reinterpret_cast<int*>(smem + L.flags);
     const int p = blockIdx.x, tile = blockIdx.y;
     const int b0 = tile * A.Bt;
     const int nb = imin(A.Bt, A.B - b0);
@@ -207,11 +161,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep_chunk(SweepArgs A) {
     const int P = A.g.P, Q = P - 1;
     const int tid = threadIdx.x;
     const int64_t bs = A.st.bs;
+    const int Bt = A.Bt;
+    const int ring = A.ring;
+    const uint32_t sb = A.slot_bytes;
     const C* Sinv = reinterpret_cast<const C*>(A.Sinv) + A.st.fac;
     const C* Rinv = reinterpret_cast<const C*>(A.Rinv) + A.st.red;
-    const bool resident = A.ring >= m + 2;
-    // load schedule of this CTA: forward blocks r0..r1-1, (ring mode) backward
-    // blocks r1-2..r0, then Rinv_p (separator below) and Rinv_{p-1} (above).
+    const bool resident = ring >= m + 2;
+    // load schedule: forward blocks r0..r1-1, (streaming mode) backward blocks
+    // r1-2..r0, then Rinv_p (separator below) and Rinv_{p-1} (separator above).
     const int nfwd = m, nbwd = resident ? 0 : m - 1;
     const bool has_below = p < P - 1, has_above = p > 0;
     const int nload = nfwd + nbwd + (has_below ? 1 : 0) + (has_above ? 1 : 0);
@@ -223,88 +180,128 @@ __global__ void __launch_bounds__(kThreads) k_sweep_chunk(SweepArgs A) {
         if (has_below && G == 0) return Rinv + (int64_t)p * bs;
         return Rinv + (int64_t)(p - 1) * bs;
     };
-    if (tid == 0) {
-        for (int i = 0; i < A.ring; ++i) mbar_init(&R.mbar[i], 1);
-        fence_mbar_init();
-        for (int G = 0; G < imin(A.ring, nload); ++G) R.issue(G, block_of(G));
-    }
-    // right-hand sides of every chunk row (independent of the chain)
-    for (int o = tid; o < m * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
-        zb[(r * A.Bt + b) * W + c] = rhs_entry<C>(A, r0 + r, c, b0 + b);
-    }
-    __syncthreads();
-    for (int o = tid; o < nb * W; o += blockDim.x) {
-        const int c = o % W, b = o / W;
-        tv[b * 64 + c] = zb[b * W + c];
-    }
-    __syncthreads();
-    int G = 0;              // next load to consume
-    int issued = imin(A.ring, nload);   // loads issued so far (thread 0's count)
-    int pending_lo = 0;     // first load not yet consumed (for the drain on time-out)
-    bool bad = false;
-    auto consume = [&](int Gc) -> const C* {
-        pending_lo = Gc;
-        if (!R.wait(Gc)) bad = true;
-        else pending_lo = Gc + 1;
-        return R.slot(Gc);
+    // ---- ring state: loads are numbered G; load G lives in slot G % ring and
+    // completes phase (G / ring) & 1 of that slot's barrier.
+    int issued = 0;                 // thread 0: loads issued
+    int consumed = 0;               // loads consumed (waited for)
+    int cslot = 0;                  // slot of load `consumed`
+    uint32_t cpar = 0;              // its phase parity
+    int last_slot = 0;              // slot of the last consumed load
+    auto issue_into = [&](int slot, const C* src) {   // thread 0 only
+        uint64_t* mb = &mbar[slot];
+        fence_proxy_async();
+        mbar_expect_tx(mb, sb);
+        bulk_g2s(slots + (size_t)slot * sb, src, sb, mb);
+        ++issued;
     };
-    auto issue = [&](int Gi, const C* src) {
-        R.issue(Gi, src);
-        issued = Gi + 1;
+    auto consume = [&]() -> const C* {
+        const C* S = reinterpret_cast<const C*>(slots + (size_t)cslot * sb);
+        if (!mbar_wait(&mbar[cslot], cpar)) flags[1] = 1;
+        last_slot = cslot;
+        ++consumed;
+        if (++cslot == ring) { cslot = 0; cpar ^= 1u; }
+        return S;
     };
-    // bounded wait gave up: record HELM_ETIMEOUT, wait (bounded) for the copies
-    // issued but not consumed, then the caller returns
+    // a bounded wait gave up (flags[1], read after a barrier, so uniform):
+    // record HELM_ETIMEOUT, wait (bounded) for the copies still in flight
     auto drain = [&]() {
         if (tid == 0) {
             atomicExch(A.status, 7);
-            for (int Gd = pending_lo; Gd < issued; ++Gd) R.wait(Gd);
+            for (int Gd = consumed - 1; Gd < issued; ++Gd)
+                if (Gd >= 0) mbar_wait(&mbar[Gd % ring], (uint32_t)((Gd / ring) & 1));
         }
         __syncthreads();
     };
-    // ---- forward elimination
+    if (tid == 0) {
+        flags[1] = 0;
+        for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+        for (int G = 0; G < imin(ring, nload); ++G) issue_into(G, block_of(G));
+    }
+    const C* ct = ctab<C>(A.g);
+    for (int o = tid; o < 2 * Bt * 64; o += blockDim.x) tin[o] = CT<C>::zero();   // tin, tout are adjacent
+    for (int c = tid; c < W; c += blockDim.x) csx[c] = ct[A.st.ctab + c];
+    for (int k = r0 + tid; k <= r1; k += blockDim.x) ccy[k - r0] = ct[A.g.ct_cy + k];
+    __syncthreads();
+    // right-hand sides of every chunk row (independent of the chain)
+    for (int o = tid; o < m * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
+        const C v = rhs_entry<C>(A, r0 + r, c, b0 + b);
+        zb[(r * Bt + b) * W + c] = v;
+        if (r == 0) tin[b * 64 + c] = v;
+    }
+    // per-lane geometry of the products
+    const int w = tid >> 5, l = tid & 31;
+    const int row = w * 8 + (l >> 2);
+    const int g = l & 3;
+    const bool own = g == 0 && row < W;
+    const int rc = imin(row, W - 1);
+    int soff[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) soff[j] = imin(g + 4 * j, W - 1) * W + rc;
+    const C csx_r = csx[rc];
+    __syncthreads();
+    // v_b = sum_a S(row, a) t_b(a) for b < nb; calls fn(b, v) on the owning lane
+    auto step = [&](const C* S, const C* t, auto fn) {
+        C sr[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) sr[j] = S[soff[j]];
+        for (int b = 0; b < nb; ++b) {
+            const C* tb = t + b * 64 + g;
+            C a0 = CT<C>::zero(), a1 = CT<C>::zero();
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {
+                a0 = cfma(sr[j], tb[4 * j], a0);
+                if (j + 1 < NJ) a1 = cfma(sr[j + 1], tb[4 * j + 4], a1);
+            }
+            C v = cadd(a0, a1);
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+            if (own) fn(b, v);
+        }
+    };
+    auto cy = [&](int k) -> C { return ccy[k - r0]; };
+    int G = 0;   // next load number to consume (also drives the refills)
+    // ---- forward elimination z_k = Sinv_k (b_k - C_k z_{k-1})
     for (int s = 0; s < m; ++s) {
         const int k = r0 + s;
-        const C* S = consume(G);
-        if (block_any(bad)) { drain(); return; }
-        warp_partial(S, tv, red, W, nb, A.Bt);
+        const C* S = consume();
+        const C ck = cmul(csx_r, cy(s + 1 < m ? k + 1 : k));
+        step(S, tin, [&](int b, C v) {
+            zb[(s * Bt + b) * W + row] = v;
+            tout[b * 64 + row] = (s + 1 < m) ? csub(zb[((s + 1) * Bt + b) * W + row], cmul(ck, v))
+                                             : cmul(ck, v);   // C_{k+1} x_{k+1} for the back substitution
+        });
         __syncthreads();
-        if (tid == 0 && !resident && G + A.ring < nload) issue(G + A.ring, block_of(G + A.ring));
+        if (flags[1]) { drain(); return; }
+        if (tid == 0 && !resident && G + ring < nload) issue_into(last_slot, block_of(G + ring));
         ++G;
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            const C z = red_sum(red, b, c, A.Bt);
-            zb[(s * A.Bt + b) * W + c] = z;
-            if (s + 1 < m) tv[b * 64 + c] = csub(zb[((s + 1) * A.Bt + b) * W + c], cmul(coupling<C>(A, k + 1, c), z));
-            else tv[b * 64 + c] = cmul(coupling<C>(A, k, c), z);   // C_{k+1} x_{k+1} for the back substitution
-        }
-        __syncthreads();
+        C* t = tin; tin = tout; tout = t;
     }
-    // ---- back substitution
+    // ---- back substitution x_k = z_k - Sinv_k C_{k+1} x_{k+1}
     for (int s = m - 2; s >= 0; --s) {
         const int k = r0 + s;
-        const C* S;
-        if (resident) S = R.slot(s);
-        else S = consume(G);
-        if (block_any(bad)) { drain(); return; }
-        warp_partial(S, tv, red, W, nb, A.Bt);
+        const C* S = resident ? reinterpret_cast<const C*>(slots + (size_t)s * sb) : consume();
+        const C ck = cmul(csx_r, cy(k));
+        step(S, tin, [&](int b, C v) {
+            const C x = csub(zb[(s * Bt + b) * W + row], v);
+            zb[(s * Bt + b) * W + row] = x;
+            tout[b * 64 + row] = cmul(ck, x);
+        });
         __syncthreads();
+        if (flags[1]) { drain(); return; }
         if (!resident) {
-            if (tid == 0 && G + A.ring < nload) issue(G + A.ring, block_of(G + A.ring));
+            if (tid == 0 && G + ring < nload) issue_into(last_slot, block_of(G + ring));
             ++G;
         }
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            const C x = csub(zb[(s * A.Bt + b) * W + c], red_sum(red, b, c, A.Bt));
-            zb[(s * A.Bt + b) * W + c] = x;
-            tv[b * 64 + c] = cmul(coupling<C>(A, k, c), x);
-        }
-        __syncthreads();
+        C* t = tin; tin = tout; tout = t;
     }
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
-        yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * A.Bt + b) * W + c];
+        yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * Bt + b) * W + c];
     }
     // ---- separator right-hand-side parts: A_p = Rinv_p (b_s - C_s y(last)), s = r1
     //      and B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first), s' = r0 - 1
@@ -316,27 +313,23 @@ __global__ void __launch_bounds__(kThreads) k_sweep_chunk(SweepArgs A) {
             for (int o = tid; o < nb * W; o += blockDim.x) {
                 const int c = o % W, b = o / W;
                 C t;
-                if (part == 0) {
-                    const int s = r1;
-                    t = csub(rhs_entry<C>(A, s, c, b0 + b), cmul(coupling<C>(A, s, c), zb[((m - 1) * A.Bt + b) * W + c]));
-                } else {
-                    const int s = r0 - 1;
-                    t = cneg(cmul(coupling<C>(A, s + 1, c), zb[b * W + c]));
-                }
-                tv[b * 64 + c] = t;
+                if (part == 0)
+                    t = csub(rhs_entry<C>(A, r1, c, b0 + b),
+                             cmul(cmul(csx[c], cy(r1)), zb[((m - 1) * Bt + b) * W + c]));
+                else
+                    t = cneg(cmul(cmul(csx[c], cy(r0)), zb[b * W + c]));
+                tin[b * 64 + c] = t;
             }
             __syncthreads();
-            const C* S = consume(G);
-            if (block_any(bad)) { drain(); return; }
-            ++G;
-            warp_partial(S, tv, red, W, nb, A.Bt);
-            __syncthreads();
+            const C* S = consume();
             const int q = part == 0 ? p : p - 1;
-            for (int o = tid; o < nb * W; o += blockDim.x) {
-                const int c = o % W, b = o / W;
-                parts[((((int64_t)(b0 + b) * Q + q) * 2 + part) * A.Wmax) + c] = red_sum(red, b, c, A.Bt);
-            }
+            step(S, tin, [&](int b, C v) {
+                parts[((((int64_t)(b0 + b) * Q + q) * 2 + part) * A.Wmax) + row] = v;
+            });
             __syncthreads();
+            if (flags[1]) { drain(); return; }
+            if (tid == 0 && !resident && G + ring < nload) issue_into(last_slot, block_of(G + ring));
+            ++G;
         }
     }
     if (Q == 0) return;
@@ -352,138 +345,134 @@ __global__ void __launch_bounds__(kThreads) k_sweep_chunk(SweepArgs A) {
         const C* E = reinterpret_cast<const C*>(A.E) + A.st.red;
         const C* F = reinterpret_cast<const C*>(A.F) + A.st.red;
         // loads continue the same ring sequence: E_1..E_{Q-1}, F_{Q-2}..F_0
-        const int G0 = nload;
         const int nred = 2 * (Q - 1);
-        auto rblock = [&](int Gr) -> const C* {
-            const int i = Gr - G0;
+        auto rblock = [&](int i) -> const C* {
             if (i < Q - 1) return E + (int64_t)(1 + i) * bs;
             return F + (int64_t)(Q - 2 - (i - (Q - 1))) * bs;
         };
-        if (tid == 0)
-            for (int Gr = G0; Gr < G0 + imin(A.ring, nred); ++Gr) issue(Gr, rblock(Gr));
-        // a_q = A_q + B_q into zb[q]
+        // every earlier load has been consumed: continue from slot `cslot`
+        if (tid == 0) {
+            int sl = cslot;
+            for (int i = 0; i < imin(ring, nred); ++i) {
+                issue_into(sl, rblock(i));
+                if (++sl == ring) sl = 0;
+            }
+        }
+        // a_q = A_q + B_q
         for (int o = tid; o < Q * nb * W; o += blockDim.x) {
             const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
             const int64_t base = (((int64_t)(b0 + b) * Q + q) * 2) * A.Wmax + c;
-            zb[(q * A.Bt + b) * W + c] = cadd(__ldcg(parts + base), __ldcg(parts + base + A.Wmax));
+            const C v = cadd(__ldcg(parts + base), __ldcg(parts + base + A.Wmax));
+            zb[(q * Bt + b) * W + c] = v;
+            if (q == 0) tin[b * 64 + c] = v;
         }
         __syncthreads();
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            tv[b * 64 + c] = zb[b * W + c];
-        }
-        __syncthreads();
-        int Gr = G0;
+        int i = 0;   // separator-load counter
         // forward: z_q = a_q - E_q z_{q-1}
         for (int q = 1; q < Q; ++q) {
-            const C* S = consume(Gr);
-            if (block_any(bad)) { drain(); return; }
-            warp_partial(S, tv, red, W, nb, A.Bt);
+            const C* S = consume();
+            step(S, tin, [&](int b, C v) {
+                const C z = csub(zb[(q * Bt + b) * W + row], v);
+                zb[(q * Bt + b) * W + row] = z;
+                tout[b * 64 + row] = z;
+            });
             __syncthreads();
-            if (tid == 0 && Gr + A.ring < G0 + nred) issue(Gr + A.ring, rblock(Gr + A.ring));
-            ++Gr;
-            for (int o = tid; o < nb * W; o += blockDim.x) {
-                const int c = o % W, b = o / W;
-                const C z = csub(zb[(q * A.Bt + b) * W + c], red_sum(red, b, c, A.Bt));
-                zb[(q * A.Bt + b) * W + c] = z;
-                tv[b * 64 + c] = z;
-            }
-            __syncthreads();
+            if (flags[1]) { drain(); return; }
+            if (tid == 0 && i + ring < nred) issue_into(last_slot, rblock(i + ring));
+            ++i;
+            C* t = tin; tin = tout; tout = t;
         }
         // backward: x_q = z_q - F_q x_{q+1}
         for (int q = Q - 2; q >= 0; --q) {
-            const C* S = consume(Gr);
-            if (block_any(bad)) { drain(); return; }
-            warp_partial(S, tv, red, W, nb, A.Bt);
+            const C* S = consume();
+            step(S, tin, [&](int b, C v) {
+                const C x = csub(zb[(q * Bt + b) * W + row], v);
+                zb[(q * Bt + b) * W + row] = x;
+                tout[b * 64 + row] = x;
+            });
             __syncthreads();
-            if (tid == 0 && Gr + A.ring < G0 + nred) issue(Gr + A.ring, rblock(Gr + A.ring));
-            ++Gr;
-            for (int o = tid; o < nb * W; o += blockDim.x) {
-                const int c = o % W, b = o / W;
-                const C x = csub(zb[(q * A.Bt + b) * W + c], red_sum(red, b, c, A.Bt));
-                zb[(q * A.Bt + b) * W + c] = x;
-                tv[b * 64 + c] = x;
-            }
-            __syncthreads();
+            if (flags[1]) { drain(); return; }
+            if (tid == 0 && i + ring < nred) issue_into(last_slot, rblock(i + ring));
+            ++i;
+            C* t = tin; tin = tout; tout = t;
         }
         for (int o = tid; o < Q * nb * W; o += blockDim.x) {
             const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
-            yrow<C>(A, b0 + b, A.g.r1[q])[c] = zb[(q * A.Bt + b) * W + c];
+            yrow<C>(A, b0 + b, A.g.r1[q])[c] = zb[(q * Bt + b) * W + c];
         }
         if (tid == 0) A.counters[tile] = 0;
     }
 }
 
 // ------------------------------------------------------------------ correction
+// One CTA per (row, RHS tile); 8 lanes per output column read the spike rows
+// GT_p(k)[c, :], GB_p(k)[c, :] (row-major, coalesced) against the separator
+// values, a three-level butterfly finishes the dot products, and the owning
+// lane scatters x (plus the base field) to the output.
 template <typename C>
-__global__ void __launch_bounds__(kThreads) k_sweep_correct(SweepArgs A, const C* __restrict__ GT,
-                                                            const C* __restrict__ GB) {
+__global__ void __launch_bounds__(256) k_sweep_correct(SweepArgs A, const C* __restrict__ GT,
+                                                       const C* __restrict__ GB) {
     const int k = blockIdx.x;
     const int b0 = blockIdx.y * A.Bt;
     const int nb = imin(A.Bt, A.B - b0);
     const int W = A.st.W;
     const int64_t bs = A.st.bs;
-    __shared__ __align__(16) C xa[4 * 64];
-    __shared__ __align__(16) C xb[4 * 64];
-    __shared__ __align__(16) C xs[4 * 64];
+    __shared__ C xt[8];   // the two transfer columns, per RHS (Bt <= 4)
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     const int pm = A.g.rowmap[k];
-    // output columns (strip-local) plus the transfer columns
     const int off = A.st.lo - A.st.lpml;
     const int olo = imax(A.sp.olo - off, 0), ohi = imin(A.sp.ohi - off, W - 1);
     const int nout = imax(ohi - olo + 1, 0);
-    int extra[2];
-    int nextra = 0;
-    if (A.sp.tout) {
-        if (A.sp.to0 < olo || A.sp.to0 > ohi) extra[nextra++] = A.sp.to0;
-        if (A.sp.to1 < olo || A.sp.to1 > ohi) extra[nextra++] = A.sp.to1;
-    }
-    const int ncol = nout + nextra;
-    auto col = [&](int i) { return i < nout ? olo + i : extra[i - nout]; };
-    if (pm < 0) {
-        for (int o = tid; o < nb * ncol; o += blockDim.x) {
-            const int c = col(o % ncol), b = o / ncol;
-            xs[b * 64 + c] = yrow<C>(A, b0 + b, k)[c];
+    const bool tr = A.sp.tout != nullptr;
+    const bool x0 = tr && (A.sp.to0 < olo || A.sp.to0 > ohi);
+    const bool x1 = tr && (A.sp.to1 < olo || A.sp.to1 > ohi);
+    const int ncol = nout + (x0 ? 1 : 0) + (x1 ? 1 : 0);
+    const bool above = pm > 0, below = pm >= 0 && pm < A.g.P - 1;
+    const int g = l & 7;
+    const int64_t rowoff = (int64_t)k * bs;
+    for (int base = w * 4; base < ncol; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
+        // column i of this 8-lane group; groups past ncol idle but join the shuffles
+        const int i = base + (l >> 3);
+        const bool live = i < ncol;
+        int c = 0;
+        if (live) {
+            if (i < nout) c = olo + i;
+            else if (i == nout && x0) c = A.sp.to0;
+            else c = A.sp.to1;
         }
-    } else {
-        const bool above = pm > 0, below = pm < A.g.P - 1;
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            if (above) xa[b * 64 + c] = yrow<C>(A, b0 + b, A.g.r1[pm - 1])[c];
-            if (below) xb[b * 64 + c] = yrow<C>(A, b0 + b, A.g.r1[pm])[c];
-        }
-        __syncthreads();
-        const C* GTk = GT + A.st.fac + (int64_t)k * bs;
-        const C* GBk = GB + A.st.fac + (int64_t)k * bs;
-        for (int i = w; i < ncol; i += kNW) {
-            const int c = col(i);
-            for (int b = 0; b < nb; ++b) {
-                C s = CT<C>::zero();
-                for (int a = l; a < W; a += 32) {
-                    if (above) s = cfma(GTk[(int64_t)c * W + a], xa[b * 64 + a], s);
-                    if (below) s = cfma(GBk[(int64_t)c * W + a], xb[b * 64 + a], s);
+        for (int b = 0; b < nb; ++b) {
+            C s = CT<C>::zero();
+            if (live && pm >= 0) {
+                const C* xa = yrow<C>(A, b0 + b, above ? A.g.r1[pm - 1] : 0);
+                const C* xb = yrow<C>(A, b0 + b, below ? A.g.r1[pm] : 0);
+                for (int a = g; a < W; a += 8) {
+                    if (above) s = cfma(GT[A.st.fac + rowoff + (int64_t)c * W + a], xa[a], s);
+                    if (below) s = cfma(GB[A.st.fac + rowoff + (int64_t)c * W + a], xb[a], s);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-                    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, 4);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, 4);
+            if (live && g == 0) {
+                const C x = csub(yrow<C>(A, b0 + b, k)[c], s);
+                const int64_t rowi = (int64_t)(b0 + b) * A.g.Ny + k;
+                if (c >= olo && c <= ohi) {
+                    double2 v = to_d2(x);
+                    if (A.sp.base) v = cadd(v, A.sp.base[rowi * A.g.Nx + off + c]);
+                    A.sp.dst[rowi * A.g.Nx + off + c] = v;
                 }
-                if (l == 0) xs[b * 64 + c] = csub(yrow<C>(A, b0 + b, k)[c], s);
+                if (tr && c == A.sp.to0) xt[b * 2] = x;
+                if (tr && c == A.sp.to1) xt[b * 2 + 1] = x;
             }
         }
     }
+    if (!tr) return;
     __syncthreads();
-    for (int o = tid; o < nb * nout; o += blockDim.x) {
-        const int c = olo + o % nout, b = o / nout;
-        const int gc = off + c;
-        const int64_t row = (int64_t)(b0 + b) * A.g.Ny + k;
-        double2 v = to_d2(xs[b * 64 + c]);
-        if (A.sp.base) v = cadd(v, A.sp.base[row * A.g.Nx + gc]);
-        A.sp.dst[row * A.g.Nx + gc] = v;
-    }
-    if (A.sp.tout)
-        for (int b = tid; b < nb; b += blockDim.x)
-            A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + k] =
-                csub(to_d2(xs[b * 64 + A.sp.to1]), to_d2(xs[b * 64 + A.sp.to0]));
+    for (int b = tid; b < nb; b += blockDim.x)
+        A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + k] = csub(to_d2(xt[b * 2 + 1]), to_d2(xt[b * 2]));
 }
 
 // ------------------------------------------------------------------ host
@@ -535,22 +524,30 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     if (!plan<C>(st, wk.zrows, wk.B, Bt, ring, smem)) return cudaErrorInvalidConfiguration;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_chunk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             220 * 1024);
-        if (e != cudaSuccess) return e;
+        for (auto fn : {k_sweep_chunk<C, 8>, k_sweep_chunk<C, 12>, k_sweep_chunk<C, 16>}) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            if (e != cudaSuccess) return e;
+        }
         attr_set = true;
     }
     SweepArgs A = make_args<C>(g, st, step, wk, Sinv, Rinv, E, F, Bt, ring);
     const int ntile = (wk.B + Bt - 1) / Bt;
     {
         TimedLaunch t(tm, "sweep_chunk", s);
-        k_sweep_chunk<C><<<dim3(g.P, ntile), kThreads, smem, s>>>(A);
+        const dim3 grid(g.P, ntile);
+        const int nthr = 32 * ((st.W + 7) / 8);
+        if (st.W <= 32) k_sweep_chunk<C, 8><<<grid, nthr, smem, s>>>(A);
+        else if (st.W <= 48) k_sweep_chunk<C, 12><<<grid, nthr, smem, s>>>(A);
+        else k_sweep_chunk<C, 16><<<grid, nthr, smem, s>>>(A);
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     {
         TimedLaunch t(tm, "sweep_correct", s);
-        k_sweep_correct<C><<<dim3(g.Ny, ntile), kThreads, 0, s>>>(A, (const C*)GT, (const C*)GB);
+        // one warp per output column (the strip's output range plus the transfer columns)
+        const int ncol = (step.ohi - step.olo + 1) + 2;
+        const int nthr = 32 * imin(8, imax(1, (ncol + 3) / 4));
+        k_sweep_correct<C><<<dim3(g.Ny, ntile), nthr, 0, s>>>(A, (const C*)GT, (const C*)GB);
     }
     return cudaGetLastError();
 }
