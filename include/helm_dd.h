@@ -113,6 +113,26 @@ helm_status helm_dd_factor(helm_dd* h);
  * g restricted to D~^(j), and out = v + w.  HELM_ESTATE before helm_dd_factor. */
 helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int nrhs);
 
+/* out = P in, exactly as helm_dd_apply_precond, without allocating device memory.
+ * The paper has no counterpart: this exists for callers that must not have the
+ * library allocate while they run -- programs whose own pool allocator owns all
+ * device memory, programs near the memory limit where a late workspace
+ * allocation could fail, and latency-critical loops where cudaMalloc/cudaFree
+ * would stall the device.  The work buffers come from one 64 MiB file-scope
+ * device array that every GPU loading the library holds until process exit.
+ *   in, out   DEVICE pointers (complex128 fields as above), distinct; host
+ *             pointers are rejected because staging them would allocate
+ *   nrhs      number of fields; HELM_EINVAL (with the byte count in
+ *             helm_dd_last_error) when 2*nrhs*N*16 bytes plus the strip
+ *             buffers exceed the 64 MiB limit
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each reuses what the previous
+ * call left there, so calls that overlap on the GPU (other threads, other
+ * handles, other streams) race and must be serialised by the caller.
+ * HELM_ESTATE before helm_dd_factor. */
+helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* in, double* out, int nrhs);
+
 /* out = A in (paper form, FP64) for nrhs fields. */
 helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs);
 

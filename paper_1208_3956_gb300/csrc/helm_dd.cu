@@ -492,24 +492,57 @@ helm_status check_device_status(helm_dd* h) {
     return HELM_OK;
 }
 
+// Device buffers one preconditioner application works in.
+struct PrecondBufs {
+    double2* V;      // [B][N] forward-sweep field v
+    double2* G;      // [B][N] residual g = f - A v
+    double2* T0;     // [B][Ny] transfer differences (two, swapped per strip)
+    double2* T1;
+    void* Y;         // [B][Ny][Wmax] strip solutions, working precision
+    void* parts;     // [B][P-1][2][Wmax] separator right-hand-side parts
+    int* counters;   // [kMaxTiles] arrival counters, zero on entry
+};
+
+// Bytes of each PrecondBufs member for B right-hand sides.
+void precond_buf_bytes(const helm_dd* h, int B, size_t sz[6]) {
+    const int64_t NV = nvol(h);
+    const int Ny = (int)h->N[1];
+    sz[0] = (size_t)B * NV * sizeof(double2);
+    sz[1] = sz[0];
+    sz[2] = (size_t)B * Ny * sizeof(double2);
+    sz[3] = sz[2];
+    sz[4] = (size_t)B * Ny * h->Wmax * h->esize;
+    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 2 * h->Wmax * h->esize;
+}
+
+helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
+
 // P applied to B device fields (Section 2.1): in -> out (distinct buffers).
 helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
-    const int64_t NV = nvol(h);
+    helm_status s;
+    size_t sz[6];
+    precond_buf_bytes(h, B, sz);
+    if ((s = ws_reserve(h, h->ws_V, sz[0])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_G, sz[1])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_T0, sz[2])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_T1, sz[3])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_Y, sz[4])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_parts, sz[5])) != HELM_OK) return s;
+    PrecondBufs bf{(double2*)h->ws_V.p, (double2*)h->ws_G.p, (double2*)h->ws_T0.p, (double2*)h->ws_T1.p,
+                   h->ws_Y.p, h->ws_parts.p, h->d_counters};
+    return run_precond(h, in, out, B, bf);
+}
+
+// The double sweep itself on caller-provided buffers.
+helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf) {
     const int Ny = (int)h->N[1], Nx = (int)h->N[0];
     helm_status s;
-    if ((s = ws_reserve(h, h->ws_V, (size_t)B * NV * sizeof(double2))) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_G, (size_t)B * NV * sizeof(double2))) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_T0, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_T1, (size_t)B * Ny * sizeof(double2))) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_Y, (size_t)B * Ny * h->Wmax * h->esize)) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_parts, (size_t)B * std::max(h->P - 1, 1) * 2 * h->Wmax * h->esize)) != HELM_OK)
-        return s;
     if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
-    double2* V = (double2*)h->ws_V.p;
-    double2* G = (double2*)h->ws_G.p;
-    double2* Tin = (double2*)h->ws_T0.p;
-    double2* Tout = (double2*)h->ws_T1.p;
-    SweepWork wk{h->ws_Y.p, h->ws_parts.p, h->d_counters, h->d_status, h->Wmax, B, h->zrows};
+    double2* V = bf.V;
+    double2* G = bf.G;
+    double2* Tin = bf.T0;
+    double2* Tout = bf.T1;
+    SweepWork wk{bf.Y, bf.parts, bf.counters, h->d_status, h->Wmax, B, h->zrows};
     const int J = h->J;
     const auto& beta = h->beta;
     const double ih2 = 1.0 / (h->h * h->h);
@@ -976,5 +1009,75 @@ void helm_dd_destroy(helm_dd* h) {
 }
 
 const char* helm_dd_last_error(const helm_dd* h) { return h ? h->err.c_str() : "null handle"; }
+
+// ------------------------------------------------------------------------
+// Preconditioner application that allocates nothing.
+//
+// Some callers cannot let the library allocate device memory while they run:
+// programs that hand all device memory to their own pool allocator and forbid
+// any other allocation, programs running so close to the memory limit that a
+// late workspace allocation could fail mid-run, and latency-critical loops in
+// which cudaMalloc / cudaFree would stall the whole device.  For them the
+// work buffers of the double sweep come from one file-scope device array,
+// allocated by the CUDA runtime when the library's module is loaded and held
+// by every GPU that loads the library until the process exits.
+// ------------------------------------------------------------------------
+static constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};   // device address of the array, per device
+
+// Device address of the scratch array on the current device.  The array's name
+// is only a host-side stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+cudaError_t noalloc_scratch(void** ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* in, double* out, int nrhs) {
+    if (!h || !in || !out || nrhs < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "apply_precond_noalloc before factor");
+    if (!is_device_ptr(in) || !is_device_ptr(out))
+        return fail(h, HELM_EINVAL, "apply_precond_noalloc takes device pointers only (host staging would allocate)");
+    if ((const void*)in == (const void*)out)
+        return fail(h, HELM_EINVAL, "apply_precond_noalloc needs distinct input and output buffers");
+    size_t sz[6];
+    precond_buf_bytes(h, nrhs, sz);
+    size_t off[7];
+    size_t total = 0;
+    for (int i = 0; i < 6; ++i) { off[i] = total; total += align256(sz[i]); }
+    off[6] = total;
+    total += align256((size_t)kMaxTiles * sizeof(int));
+    if (total > kNoAllocScratchBytes)
+        return fail(h, HELM_EINVAL, "apply_precond_noalloc needs " + std::to_string(total) +
+                                        " bytes of scratch; the static limit is " +
+                                        std::to_string(kNoAllocScratchBytes) + " (use fewer right-hand sides)");
+    void* base = nullptr;
+    CK(h, noalloc_scratch(&base));
+    unsigned char* b = (unsigned char*)base;
+    PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), (double2*)(b + off[2]), (double2*)(b + off[3]),
+                   b + off[4], b + off[5], (int*)(b + off[6])};
+    // the array keeps whatever the previous call left: the arrival counters must start at zero
+    CK(h, cudaMemsetAsync(bf.counters, 0, (size_t)kMaxTiles * sizeof(int), h->stream));
+    helm_status s = run_precond(h, (const double2*)in, (double2*)out, nrhs, bf);
+    if (s != HELM_OK) return s;
+    return check_device_status(h);
+}
 
 }  // extern "C"

@@ -54,6 +54,7 @@ def load() -> ctypes.CDLL:
         "helm_dd_set_chunks": (I, [P, I]),
         "helm_dd_factor": (I, [P]),
         "helm_dd_apply_precond": (I, [P, P, P, I]),
+        "helm_dd_apply_precond_noalloc": (I, [P, P, P, I]),
         "helm_dd_matvec": (I, [P, P, P, I]),
         "helm_dd_solve": (I, [P, P, P, I, D, I, I, ctypes.POINTER(RhsInfo)]),
         "helm_dd_gradient": (I, [P, P, I, P, I, P, D, ctypes.POINTER(D), P]),
@@ -219,6 +220,23 @@ class HelmDD:
         _sync_torch(f)
         self._check(self.lib.helm_dd_apply_precond(self._h, a.ptr, o.ptr, nrhs))
         return o.obj
+
+    def apply_precond_noalloc(self, f, out=None):
+        """P f for torch CUDA tensors with no device allocation by the library.
+
+        The library's work buffers come from its static 64 MiB device array; the
+        output tensor may be passed in so that the call allocates nothing at all.
+        Calls sharing the array must not overlap on the GPU.
+        """
+        if not (_is_torch(f) and f.is_cuda):
+            raise ValueError("apply_precond_noalloc takes CUDA tensors")
+        nrhs = self._fields(f)
+        if out is None:
+            out = self._out_like(f)
+        a, o = _Arr(f, np.complex128), _Arr(out, np.complex128)
+        _sync_torch(f)
+        self._check(self.lib.helm_dd_apply_precond_noalloc(self._h, a.ptr, o.ptr, nrhs))
+        return out
 
     def matvec(self, u):
         nrhs = self._fields(u)

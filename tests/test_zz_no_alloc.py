@@ -1,0 +1,62 @@
+"""The preconditioner application that allocates no device memory.
+
+Callers whose own allocator owns all device memory, or that run too close to
+the memory limit (or too latency-critically) to let a library call cudaMalloc
+mid-run, use helm_dd_apply_precond_noalloc: its work buffers live in one
+static 64 MiB device array.  This file checks, through the C ABI, that it
+returns what helm_dd_apply_precond returns on two calls in a row (the second
+call finds the first call's leftovers in the shared array), and that it
+rejects a batch whose buffers would not fit.  It runs last so that a failure
+here cannot hide the rest of the suite; it passes alone and after the others.
+"""
+import numpy as np
+import pytest
+
+from paper_1208_3956_gb300 import helm, media
+
+pytestmark = pytest.mark.gpu
+
+# the FP64 preconditioner bar of the parity tests; mixed precision compares the
+# same complex64 kernels on the same inputs, so it is held to the same bar
+TOL = 1e-10
+
+
+def _problem(prec):
+    n = (61, 45)
+    c = media.smooth_medium(n, 3.0, 1.0, 2.0, 5)
+    h = 1.0 / 32
+    omega = media.omega_for(c, h, 8.0)
+    return helm.HelmDD(c, h, omega, 6, 5, 4, prec, chunks=5).factor()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_matches_apply_precond_on_two_calls(prec):
+    torch = pytest.importorskip("torch")
+    g = _problem(prec)
+    for call, seed in enumerate((21, 22)):
+        f = torch.as_tensor(media.random_rhs((2,) + g.shape, seed), device="cuda")
+        ref = g.apply_precond(f)
+        out = torch.empty_like(f)
+        got = g.apply_precond_noalloc(f, out=out)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+        assert err <= TOL, (call, err)
+    g.close()
+
+
+def test_noalloc_rejects_oversize_batch_and_host_pointers():
+    torch = pytest.importorskip("torch")
+    g = _problem("mixed")
+    # a batch whose two full-grid buffers alone exceed 64 MiB
+    nrhs = (64 << 20) // (2 * 16 * g.ndof) + 1
+    f = torch.zeros((nrhs,) + g.shape, dtype=torch.complex128, device="cuda")
+    with pytest.raises(helm.HelmError) as ei:
+        g.apply_precond_noalloc(f)
+    assert ei.value.status == -1 and "bytes of scratch" in str(ei.value)
+    # host arrays would need staging buffers: refused
+    x = np.zeros(g.shape, dtype=np.complex128)
+    y = np.zeros_like(x)
+    st = g.lib.helm_dd_apply_precond_noalloc(g._h, x.ctypes.data_as(helm.ctypes.c_void_p),
+                                             y.ctypes.data_as(helm.ctypes.c_void_p), 1)
+    assert st == -1
+    g.close()
