@@ -110,6 +110,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def captured_traffic(kernel_src, summary):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()
+        fields = {}
+        for line in open(os.path.join(ROOT, summary)):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256") == sha:
+            return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -262,7 +279,10 @@ def run_ours(args):
                        "factor_ms": t_factor_ms, "iters": iters, "rel_res": rel_res},
             "gpu_launches": int(sum(v[0] for v in stats.values()) / max(1, args.steps)),
             "roofline": {"bound": "hbm", "kernel": "sweep_chunk", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": captured_traffic("paper_1208_3956_gb300/csrc/sweep.cu",
+                                                     "profiles/sweep_chunk_smooth1023.md")
+                         if args.precision == "mixed" and not args.chunks else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
                          "alg_bytes_per_launch": alg_per_launch,
                          "share_of_kernel_time": sc[1] / total_ms if total_ms else None},

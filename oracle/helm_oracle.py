@@ -286,7 +286,7 @@ class HelmholtzDD:
             Aj, Sj = self.strip_operator(j)
             Ahat = sp.diags(Sj.ravel()) @ Aj
             self._strip_mats.append((Aj, Sj))
-            self._strip_lu.append(spla.splu(Ahat.tocsc(), permc_spec="MMD_AT_PLUS_A"))
+            self._strip_lu.append(spla.splu(Ahat.tocsc(), permc_spec="COLAMD"))
         return self
 
     def strip_solve(self, j: int, r: np.ndarray) -> np.ndarray:
@@ -354,7 +354,7 @@ class HelmholtzDD:
     def direct_solve(self, f: np.ndarray) -> np.ndarray:
         if self._full_lu is None:
             Ahat = sp.diags(self.S.ravel()) @ self.A
-            self._full_lu = spla.splu(Ahat.tocsc(), permc_spec="MMD_AT_PLUS_A")
+            self._full_lu = spla.splu(Ahat.tocsc(), permc_spec="COLAMD")
         f = np.asarray(f, dtype=complex)
         return self._full_lu.solve((self.S * f).ravel()).reshape(f.shape)
 

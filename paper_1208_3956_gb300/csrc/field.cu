@@ -96,9 +96,10 @@ __global__ void k_copy_cols(const double2* __restrict__ src, double2* __restrict
 }
 
 cudaError_t launch_copy_cols(const double2* src, double2* dst, int B, int Nx, int Ny, int Nz, int xlo, int xhi,
-                             cudaStream_t s) {
+                             cudaStream_t s, KernelTimer* tm) {
     if (xhi < xlo) return cudaSuccess;
     const int64_t rows = (int64_t)B * Ny * Nz;
+    TimedLaunch t(tm, "compose_copy", s);
     k_copy_cols<<<nblocks(rows * (xhi - xlo + 1), 256), 256, 0, s>>>(src, dst, rows, Nx, xlo, xhi);
     return cudaGetLastError();
 }
@@ -164,6 +165,7 @@ cudaError_t launch_multidot(const double2* V, int64_t vstride, const double2* w,
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int count = nv * B;
+    TimedLaunch t(tm, "krylov_reduce", s);
     k_reduce_partials<<<(count + 7) / 8, 256, 0, s>>>(partial, nblk, count, out);
     return cudaGetLastError();
 }
@@ -195,7 +197,8 @@ __global__ void k_scale(double2* __restrict__ dst, const double2* __restrict__ s
 }
 
 cudaError_t launch_scale(double2* dst, const double2* src, const double* scale, int B, int64_t N,
-                         cudaStream_t s) {
+                         cudaStream_t s, KernelTimer* tm) {
+    TimedLaunch t(tm, "krylov_scale", s);
     k_scale<<<nblocks((int64_t)B * N, 256), 256, 0, s>>>(dst, src, scale, B, N);
     return cudaGetLastError();
 }

@@ -599,7 +599,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         std::swap(Tin, Tout);
     }
     // D~^(J) keeps v (w = 0 there)
-    CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream));
+    CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
     return HELM_OK;
 }
 
@@ -735,7 +735,7 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
         }
         if (!any || ++guard > 100000) break;
         CK(h, cudaMemcpyAsync(dscale, hscale.data(), B * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CK(h, launch_scale(V, V, dscale, B, NV, h->stream));
+        CK(h, launch_scale(V, V, dscale, B, NV, h->stream, &h->timer));
         for (int i = 0; i < m; ++i) {
             double2* Vi = V + (int64_t)i * vs;
             double2* Zi = Z + (int64_t)i * vs;
@@ -801,7 +801,7 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
             }
             if (!still || i == m - 1) break;
             CK(h, cudaMemcpyAsync(dscale, hscale.data(), B * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            CK(h, launch_scale(V + (int64_t)(i + 1) * vs, Wv, dscale, B, NV, h->stream));
+            CK(h, launch_scale(V + (int64_t)(i + 1) * vs, Wv, dscale, B, NV, h->stream, &h->timer));
         }
         // x += Z y,  H y = g (upper triangular, per column)
         int kmax = 0;

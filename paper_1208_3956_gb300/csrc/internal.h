@@ -126,7 +126,7 @@ cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, 
 cudaError_t launch_stencil(const Geom& g, const double2* u, const double2* f, double2* out, int B,
                            cudaStream_t s, KernelTimer* tm);
 cudaError_t launch_copy_cols(const double2* src, double2* dst, int B, int Nx, int Ny, int Nz, int xlo, int xhi,
-                             cudaStream_t s);
+                             cudaStream_t s, KernelTimer* tm);
 // partial[b][i][blk] for h[b][i] = sum_n conj(V_i[b][n]) w[b][n]; V_i at V + i*vstride
 cudaError_t launch_multidot(const double2* V, int64_t vstride, const double2* w, int nv, int B, int64_t N,
                             double2* partial, int nblk, double2* out, cudaStream_t s, KernelTimer* tm);
@@ -135,7 +135,7 @@ cudaError_t launch_multi_axpy(double2* w, const double2* V, int64_t vstride, con
                               int B, int64_t N, cudaStream_t s, KernelTimer* tm);
 // dst[b] = src[b] * scale[b] (scale real, device [B])
 cudaError_t launch_scale(double2* dst, const double2* src, const double* scale, int B, int64_t N,
-                         cudaStream_t s);
+                         cudaStream_t s, KernelTimer* tm);
 cudaError_t launch_grad_accum(const double2* U, const double2* MU, const Geom& g, int nsrc, double* gpad,
                               cudaStream_t s);
 cudaError_t launch_fold(const double* gpad, double* gint, int dim, int nx, int ny, int nz, int w, cudaStream_t s);
