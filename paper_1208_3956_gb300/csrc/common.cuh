@@ -77,7 +77,17 @@ struct StripDev {
     int64_t red;   // element offset of this strip's reduced-system blocks ((P-1) blocks of BS)
     int64_t bs;    // elements per stored W x W block (column-major, padded to 16 bytes)
     int64_t ctab;  // offset of this strip's s_x(c) (W entries) in the working-precision table
+    int nj;        // columns per lane in the sweep products (W <= 4 nj)
+    int ld;        // leading dimension of the sweep-layout blocks (4 nj + 2)
 };
+
+// Sweep layout of the W x W blocks Sinv, Rinv, E, F: row-major with leading
+// dimension ld (>= 4 nj >= W), columns W..ld-1 zero.  Element (r, a) sits at
+// r * ld + a, so a lane owning row r and columns g*nj .. g*nj+nj-1 reads one
+// contiguous run; the +2 padding spreads the rows of a warp over the banks.
+__host__ __device__ __forceinline__ int sweep_nj(int W) {
+    return W <= 32 ? 8 : W <= 40 ? 10 : W <= 48 ? 12 : W <= 56 ? 14 : 16;
+}
 
 // Global geometry and tables (device pointers, FP64).
 struct Geom {

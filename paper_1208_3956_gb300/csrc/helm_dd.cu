@@ -198,7 +198,9 @@ cd strip_alpha_at(const helm_dd* h, const StripDev& s, int x2) {
 
 void chunk_layout(helm_dd* h) {
     const int Ny = (int)h->N[1];
-    int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(sqrt(Ny / 2.0)));
+    // built-in: about sqrt(Ny) chunks balances the chunk chains (~Ny/P steps) against the
+    // separator chain (~P steps)
+    int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(sqrt((double)Ny)));
     P = std::min(P, (Ny + 1) / 2);
     h->P = std::max(P, 1);
     const int rows = Ny - (h->P - 1);
@@ -433,8 +435,9 @@ helm_status helm_dd_factor(helm_dd* h) {
     const int Ny = (int)h->N[1];
     int64_t fac = 0, red = 0;
     for (auto& s : h->strips) {
-        s.bs = (int64_t)s.W * s.W;
-        if (h->esize == sizeof(float2) && (s.bs & 1)) s.bs += 1;   // keep blocks 16-byte aligned
+        s.nj = sweep_nj(s.W);
+        s.ld = 4 * s.nj + 2;
+        s.bs = (int64_t)s.W * s.ld;   // sweep layout; even, so blocks stay 16-byte aligned
         s.fac = fac;
         s.red = red;
         fac += (int64_t)Ny * s.bs;

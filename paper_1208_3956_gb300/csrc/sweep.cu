@@ -115,7 +115,7 @@ __device__ __forceinline__ C* yrow(const SweepArgs& A, int b, int k) {
 
 // Shared-memory carve-up (bytes), identical on host and device.
 struct SweepSmem {
-    uint32_t slots, zb, tv, tv2, cx, cy, mbar, flags, total;
+    uint32_t slots, zb, tv, cx, cy, order, mbar, flags, total;
 };
 __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, int zrows, int Bt, int W,
                                                 int esz) {
@@ -123,10 +123,10 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     uint32_t o = 0;
     s.slots = o; o += ring * slot_bytes;
     s.zb = o; o += ((uint32_t)zrows * Bt * W * esz + 15u) & ~15u;
-    s.tv = o; o += (uint32_t)Bt * 64 * esz;
-    s.tv2 = o; o += (uint32_t)Bt * 64 * esz;
+    s.tv = o; o += 4u * Bt * 64 * esz;                         // in/out vectors of both chains
     s.cx = o; o += 64u * esz;
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
+    s.order = o; o += ((uint32_t)(2 * zrows + 4) * 4 + 15u) & ~15u;   // load order table
     s.mbar = o; o += kMaxRing * 8;
     s.flags = o; o += 16;
     s.total = o;
@@ -134,60 +134,150 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
 }
 
 // ------------------------------------------------------------------ chunk + separators
-// Matrix-vector layout of one chain step: the CTA has ceil(W/8) warps; lane l of
-// warp w owns row r = 8w + l/4 and the columns a = l%4 + 4j, j < NJ, of the
-// column-major W x W block in shared memory.  Offsets are precomputed once and
-// clamped into the block (a clamped column meets a zero entry of the vector, a
-// clamped row is computed but never stored), and two xor shuffles complete the
-// row sums.
+// Products of one chain step.  The CTA has ceil(W/8) warps; lane l of warp w
+// owns row r = 8w + l/4 (clamped to W-1 for the idle rows of the last warp) and
+// the NJ contiguous columns g*NJ .. g*NJ+NJ-1, g = l%4, of a sweep-layout block
+// (row-major, leading dimension 4 NJ + 2, zero beyond column W).  Both the
+// factor row and the vector are read as 16-byte runs; two xor shuffles finish
+// the row sums on all four lanes of the row.
+__device__ __forceinline__ void load_run2(float2* v, const float2* p, int n) {
+    for (int jj = 0; jj < n / 2; ++jj) {
+        const float4 q = reinterpret_cast<const float4*>(p)[jj];
+        v[2 * jj] = make_float2(q.x, q.y);
+        v[2 * jj + 1] = make_float2(q.z, q.w);
+    }
+}
+__device__ __forceinline__ void load_run2(double2* v, const double2* p, int n) {
+    for (int j = 0; j < n; ++j) v[j] = p[j];
+}
 template <typename C, int NJ>
-__global__ void __launch_bounds__(256) k_sweep_chunk(SweepArgs A) {
+__device__ __forceinline__ void load_row(C (&v)[NJ], const C* p) {
+#pragma unroll
+    for (int j = 0; j < NJ; j += 2) load_run2(&v[j], p + j, 2);
+}
+template <typename C, int NJ>
+__device__ __forceinline__ C row_dot(const C (&s)[NJ], const C* t) {
+    C tv[NJ];
+    load_row<C, NJ>(tv, t);
+    C a0 = CT<C>::zero(), a1 = CT<C>::zero();
+#pragma unroll
+    for (int j = 0; j < NJ; j += 2) {
+        a0 = cfma(s[j], tv[j], a0);
+        a1 = cfma(s[j + 1], tv[j + 1], a1);
+    }
+    C v = cadd(a0, a1);
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+    return v;
+}
+
+// Both chains of a step in one instruction stream: vd[b] = Sd-row . td_b and
+// vu[b] = Su-row . tu_b (the row sums complete on all four lanes of a row).
+// D / U select the active chains at compile time.
+template <typename C, int NJ, int BT, bool D, bool U>
+__device__ __forceinline__ void dual_rows(const C* __restrict__ Sd, const C* __restrict__ td,
+                                          const C* __restrict__ Su, const C* __restrict__ tu, int nb,
+                                          C (&vd)[BT], C (&vu)[BT]) {
+    C sd[NJ], su[NJ];
+    if (D) load_row<C, NJ>(sd, Sd);
+    if (U) load_row<C, NJ>(su, Su);
+#pragma unroll
+    for (int b = 0; b < BT; ++b) {
+        if (b < nb) {
+            C xd[NJ], xu[NJ];
+            if (D) load_row<C, NJ>(xd, td + b * 64);
+            if (U) load_row<C, NJ>(xu, tu + b * 64);
+            C d0 = CT<C>::zero(), d1 = CT<C>::zero(), u0 = CT<C>::zero(), u1 = CT<C>::zero();
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {
+                if (D) { d0 = cfma(sd[j], xd[j], d0); d1 = cfma(sd[j + 1], xd[j + 1], d1); }
+                if (U) { u0 = cfma(su[j], xu[j], u0); u1 = cfma(su[j + 1], xu[j + 1], u1); }
+            }
+            C a = cadd(d0, d1), c = cadd(u0, u1);
+#pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                if (D) { a.x += __shfl_xor_sync(0xffffffffu, a.x, o); a.y += __shfl_xor_sync(0xffffffffu, a.y, o); }
+                if (U) { c.x += __shfl_xor_sync(0xffffffffu, c.x, o); c.y += __shfl_xor_sync(0xffffffffu, c.y, o); }
+            }
+            vd[b] = a;
+            vu[b] = c;
+        }
+    }
+}
+template <typename C, int NJ, int BT>
+__device__ __forceinline__ void dual_dispatch(bool dn, bool up, const C* Sd, const C* td, const C* Su,
+                                              const C* tu, int nb, C (&vd)[BT], C (&vu)[BT]) {
+    if (dn && up) dual_rows<C, NJ, BT, true, true>(Sd, td, Su, tu, nb, vd, vu);
+    else if (dn) dual_rows<C, NJ, BT, true, false>(Sd, td, Su, tu, nb, vd, vu);
+    else if (up) dual_rows<C, NJ, BT, false, true>(Sd, td, Su, tu, nb, vd, vu);
+}
+
+// The CTA is ceil(W/8) compute warps plus one producer warp.  The producer's
+// lane 0 owns the TMA ring: it initialises the barriers, issues every bulk
+// copy, and right after each step's barrier refills the slots that step
+// consumed, while the compute warps already run the next step.
+template <typename C, int NJ, int BT>
+__global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int LD = 4 * NJ + 2;
     const int W = A.st.W;
     const int esz = (int)sizeof(C);
-    const SweepSmem L = sweep_smem(A.ring, A.slot_bytes, A.zrows, A.Bt, W, esz);
+    const SweepSmem L = sweep_smem(A.ring, A.slot_bytes, A.zrows, BT, W, esz);
     unsigned char* slots = smem + L.slots;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
-    C* zb = reinterpret_cast<C*>(smem + L.zb);       // [zrows][Bt][W]
-    C* tin = reinterpret_cast<C*>(smem + L.tv);      // [Bt][64] vector entering the step
-    C* tout = reinterpret_cast<C*>(smem + L.tv2);    // [Bt][64] vector entering the next step
+    C* zb = reinterpret_cast<C*>(smem + L.zb);       // [zrows][BT][W]
+    C* v0 = reinterpret_cast<C*>(smem + L.tv);       // four [BT][64] vectors: in/out of both chains
+    C* vin_d = v0;
+    C* vin_u = v0 + BT * 64;
+    C* vout_d = v0 + 2 * BT * 64;
+    C* vout_u = v0 + 3 * BT * 64;
     C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
     C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
+    int* order = reinterpret_cast<int*>(smem + L.order);
     volatile int* flags = reinterpret_cast<int*>(smem + L.flags);
     const int p = blockIdx.x, tile = blockIdx.y;
-    const int b0 = tile * A.Bt;
-    const int nb = imin(A.Bt, A.B - b0);
+    const int b0 = tile * BT;
+    const int nb = imin(BT, A.B - b0);
     const int r0 = A.g.r0[p], r1 = A.g.r1[p], m = r1 - r0;
+    const int t = r0 + (m - 1) / 2;                  // twist row
+    const int nd = t - r0, nu = r1 - 1 - t, nmx = imax(nd, nu);
     const int P = A.g.P, Q = P - 1;
     const int tid = threadIdx.x;
+    const int ptid = blockDim.x - 32;                // the producer thread
+    const bool producer = tid == ptid;
+    const bool compute = tid < ptid;
     const int64_t bs = A.st.bs;
-    const int Bt = A.Bt;
     const int ring = A.ring;
     const uint32_t sb = A.slot_bytes;
     const C* Sinv = reinterpret_cast<const C*>(A.Sinv) + A.st.fac;
     const C* Rinv = reinterpret_cast<const C*>(A.Rinv) + A.st.red;
+    const C* Eb = reinterpret_cast<const C*>(A.E) + A.st.red;
+    const C* Fb = reinterpret_cast<const C*>(A.F) + A.st.red;
     const bool resident = ring >= m + 2;
-    // load schedule: forward blocks r0..r1-1, (streaming mode) backward blocks
-    // r1-2..r0, then Rinv_p (separator below) and Rinv_{p-1} (separator above).
-    const int nfwd = m, nbwd = resident ? 0 : m - 1;
     const bool has_below = p < P - 1, has_above = p > 0;
-    const int nload = nfwd + nbwd + (has_below ? 1 : 0) + (has_above ? 1 : 0);
-    auto block_of = [&](int G) -> const C* {
-        if (G < nfwd) return Sinv + (int64_t)(r0 + G) * bs;
-        G -= nfwd;
-        if (G < nbwd) return Sinv + (int64_t)(r1 - 2 - G) * bs;
-        G -= nbwd;
-        if (has_below && G == 0) return Rinv + (int64_t)p * bs;
-        return Rinv + (int64_t)(p - 1) * bs;
+    // ---- load order of the chunk phase (rows of Sinv; -1 / -2: Rinv below / above)
+    //   forward: s = 0..nmx-1: down row r0+s, up row r1-1-s; then the twist row
+    //   back (streaming only): s = 0..nmx-1: down row t-1-s, up row t+1+s
+    const int nload = m + (resident ? 0 : m - 1) + (has_below ? 1 : 0) + (has_above ? 1 : 0);
+    // ---- ring state: load G lives in slot G % ring and completes phase (G / ring) & 1
+    int issued = 0, consumed = 0;           // issued: the producer's count
+    int cslot = 0;
+    uint32_t cpar = 0;
+    int rf = 0, rfslot = 0;                 // producer: next consumed load whose slot is reused
+    int nseq = nload;                       // loads in the current sequence
+    int seqbase = 0;                        // first load number of the current sequence
+    bool sep_phase = false;
+    auto src_of = [&](int G) -> const C* {
+        const int r = order[G - seqbase];
+        if (!sep_phase) {
+            if (r >= 0) return Sinv + (int64_t)r * bs;
+            return Rinv + (int64_t)(r == -1 ? p : p - 1) * bs;
+        }
+        return r >= 0 ? Eb + (int64_t)r * bs : Fb + (int64_t)(-r - 1) * bs;
     };
-    // ---- ring state: loads are numbered G; load G lives in slot G % ring and
-    // completes phase (G / ring) & 1 of that slot's barrier.
-    int issued = 0;                 // thread 0: loads issued
-    int consumed = 0;               // loads consumed (waited for)
-    int cslot = 0;                  // slot of load `consumed`
-    uint32_t cpar = 0;              // its phase parity
-    int last_slot = 0;              // slot of the last consumed load
-    auto issue_into = [&](int slot, const C* src) {   // thread 0 only
+    auto issue_into = [&](int slot, const C* src) {   // producer only
         uint64_t* mb = &mbar[slot];
         fence_proxy_async();
         mbar_expect_tx(mb, sb);
@@ -196,30 +286,48 @@ __global__ void __launch_bounds__(256) k_sweep_chunk(SweepArgs A) {
     };
     auto consume = [&]() -> const C* {
         const C* S = reinterpret_cast<const C*>(slots + (size_t)cslot * sb);
-        if (!mbar_wait(&mbar[cslot], cpar)) flags[1] = 1;
-        last_slot = cslot;
+        if (compute && !mbar_wait(&mbar[cslot], cpar)) flags[1] = 1;
         ++consumed;
         if (++cslot == ring) { cslot = 0; cpar ^= 1u; }
         return S;
     };
-    // a bounded wait gave up (flags[1], read after a barrier, so uniform):
-    // record HELM_ETIMEOUT, wait (bounded) for the copies still in flight
+    // producer, after a barrier: every consumed slot is free; reuse it
+    auto refill = [&]() {
+        while (rf < consumed) {
+            if (rf + ring < nseq) issue_into(rfslot, src_of(rf + ring));
+            ++rf;
+            if (++rfslot == ring) rfslot = 0;
+        }
+    };
     auto drain = [&]() {
-        if (tid == 0) {
+        if (producer) {
             atomicExch(A.status, 7);
             for (int Gd = consumed - 1; Gd < issued; ++Gd)
                 if (Gd >= 0) mbar_wait(&mbar[Gd % ring], (uint32_t)((Gd / ring) & 1));
         }
         __syncthreads();
     };
-    if (tid == 0) {
+    if (producer) {
+        int G = 0;
+        for (int s = 0; s < nmx; ++s) {
+            if (s < nd) order[G++] = r0 + s;
+            if (s < nu) order[G++] = r1 - 1 - s;
+        }
+        order[G++] = t;
+        if (!resident)
+            for (int s = 0; s < nmx; ++s) {
+                if (s < nd) order[G++] = t - 1 - s;
+                if (s < nu) order[G++] = t + 1 + s;
+            }
+        if (has_below) order[G++] = -1;
+        if (has_above) order[G++] = -2;
         flags[1] = 0;
         for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
-        for (int G = 0; G < imin(ring, nload); ++G) issue_into(G, block_of(G));
+        for (int i = 0; i < imin(ring, nload); ++i) issue_into(i, src_of(i));
     }
     const C* ct = ctab<C>(A.g);
-    for (int o = tid; o < 2 * Bt * 64; o += blockDim.x) tin[o] = CT<C>::zero();   // tin, tout are adjacent
+    for (int o = tid; o < 4 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
     for (int c = tid; c < W; c += blockDim.x) csx[c] = ct[A.st.ctab + c];
     for (int k = r0 + tid; k <= r1; k += blockDim.x) ccy[k - r0] = ct[A.g.ct_cy + k];
     __syncthreads();
@@ -227,110 +335,139 @@ __global__ void __launch_bounds__(256) k_sweep_chunk(SweepArgs A) {
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
         const C v = rhs_entry<C>(A, r0 + r, c, b0 + b);
-        zb[(r * Bt + b) * W + c] = v;
-        if (r == 0) tin[b * 64 + c] = v;
+        zb[(r * BT + b) * W + c] = v;
+        if (r == 0 && nd > 0) vin_d[b * 64 + c] = v;            // down chain starts at r0
+        if (r == m - 1 && nu > 0) vin_u[b * 64 + c] = v;        // up chain starts at r1-1
     }
-    // per-lane geometry of the products
+    // per-lane geometry
     const int w = tid >> 5, l = tid & 31;
     const int row = w * 8 + (l >> 2);
     const int g = l & 3;
-    const bool own = g == 0 && row < W;
+    const bool rowok = compute && row < W;
     const int rc = imin(row, W - 1);
-    int soff[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) soff[j] = imin(g + 4 * j, W - 1) * W + rc;
+    const int lofs = rc * LD + g * NJ;     // this lane's run inside a block
+    const int vofs = g * NJ;               // ... and inside a vector
     const C csx_r = csx[rc];
     __syncthreads();
-    // v_b = sum_a S(row, a) t_b(a) for b < nb; calls fn(b, v) on the owning lane
-    auto step = [&](const C* S, const C* t, auto fn) {
-        C sr[NJ];
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) sr[j] = S[soff[j]];
-        for (int b = 0; b < nb; ++b) {
-            const C* tb = t + b * 64 + g;
-            C a0 = CT<C>::zero(), a1 = CT<C>::zero();
-#pragma unroll
-            for (int j = 0; j < NJ; j += 2) {
-                a0 = cfma(sr[j], tb[4 * j], a0);
-                if (j + 1 < NJ) a1 = cfma(sr[j + 1], tb[4 * j + 4], a1);
-            }
-            C v = cadd(a0, a1);
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
-            if (own) fn(b, v);
-        }
+    auto zr = [&](int k) -> C* { return zb + (k - r0) * BT * W; };   // row k, b = 0
+    auto cpl = [&](int k) -> C { return cmul(csx_r, ccy[k - r0]); }; // C_k at this lane's row
+    auto finish = [&]() -> bool {
+        __syncthreads();
+        if (flags[1]) { drain(); return false; }
+        if (producer && !(resident && !sep_phase)) refill();
+        C* x = vin_d; vin_d = vout_d; vout_d = x;
+        x = vin_u; vin_u = vout_u; vout_u = x;
+        return true;
     };
-    auto cy = [&](int k) -> C { return ccy[k - r0]; };
-    int G = 0;   // next load number to consume (also drives the refills)
-    // ---- forward elimination z_k = Sinv_k (b_k - C_k z_{k-1})
-    for (int s = 0; s < m; ++s) {
-        const int k = r0 + s;
-        const C* S = consume();
-        const C ck = cmul(csx_r, cy(s + 1 < m ? k + 1 : k));
-        step(S, tin, [&](int b, C v) {
-            zb[(s * Bt + b) * W + row] = v;
-            tout[b * 64 + row] = (s + 1 < m) ? csub(zb[((s + 1) * Bt + b) * W + row], cmul(ck, v))
-                                             : cmul(ck, v);   // C_{k+1} x_{k+1} for the back substitution
-        });
-        __syncthreads();
-        if (flags[1]) { drain(); return; }
-        if (tid == 0 && !resident && G + ring < nload) issue_into(last_slot, block_of(G + ring));
-        ++G;
-        C* t = tin; tin = tout; tout = t;
+    C vd[BT], vu[BT];
+    // ---- forward elimination of both halves
+    for (int s = 0; s < nmx; ++s) {
+        const bool dn = s < nd, up = s < nu;
+        const int kd = r0 + s, ku = r1 - 1 - s;
+        const C* Sd = dn ? consume() : nullptr;
+        const C* Su = up ? consume() : nullptr;
+        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        const C cd = cpl(kd + 1), cu = cpl(ku);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                if (dn) {   // z_kd; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
+                    zr(kd)[b * W + row] = vd[b];
+                    if (kd + 1 < t) vout_d[b * 64 + row] = csub(zr(kd + 1)[b * W + row], cmul(cd, vd[b]));
+                }
+                if (up) {   // z_ku; next up input b_{ku-1} - C_ku z_ku (if ku-1 > t)
+                    zr(ku)[b * W + row] = vu[b];
+                    if (ku - 1 > t) vout_u[b * 64 + row] = csub(zr(ku - 1)[b * W + row], cmul(cu, vu[b]));
+                }
+            }
+        if (!finish()) return;
     }
-    // ---- back substitution x_k = z_k - Sinv_k C_{k+1} x_{k+1}
-    for (int s = m - 2; s >= 0; --s) {
-        const int k = r0 + s;
-        const C* S = resident ? reinterpret_cast<const C*>(slots + (size_t)s * sb) : consume();
-        const C ck = cmul(csx_r, cy(k));
-        step(S, tin, [&](int b, C v) {
-            const C x = csub(zb[(s * Bt + b) * W + row], v);
-            zb[(s * Bt + b) * W + row] = x;
-            tout[b * 64 + row] = cmul(ck, x);
-        });
-        __syncthreads();
-        if (flags[1]) { drain(); return; }
-        if (!resident) {
-            if (tid == 0 && G + ring < nload) issue_into(last_slot, block_of(G + ring));
-            ++G;
+    // ---- twist row: y_t = Sinv_t (b_t - C_t z_{t-1} - C_{t+1} z_{t+1})
+    for (int o = tid; o < nb * W; o += blockDim.x) {
+        const int c = o % W, b = o / W;
+        C v = zr(t)[b * W + c];
+        if (nd > 0) v = csub(v, cmul(cmul(csx[c], ccy[t - r0]), zr(t - 1)[b * W + c]));
+        if (nu > 0) v = csub(v, cmul(cmul(csx[c], ccy[t + 1 - r0]), zr(t + 1)[b * W + c]));
+        vin_d[b * 64 + c] = v;
+    }
+    __syncthreads();
+    {
+        const C* St = consume();
+        if (compute) dual_dispatch<C, NJ, BT>(true, false, St + lofs, vin_d + vofs, St, vin_u, nb, vd, vu);
+        const C cd = cpl(t), cu = cpl(t + 1);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                zr(t)[b * W + row] = vd[b];
+                vout_d[b * 64 + row] = cmul(cd, vd[b]);   // C_t y_t for row t-1
+                vout_u[b * 64 + row] = cmul(cu, vd[b]);   // C_{t+1} y_t for row t+1
+            }
+        if (!finish()) return;
+    }
+    // ---- outward back substitution: y_k = z_k - Sinv_k C y_inner
+    for (int s = 0; s < nmx; ++s) {
+        const bool dn = s < nd, up = s < nu;
+        const int kd = t - 1 - s, ku = t + 1 + s;
+        const C* Sd = nullptr;
+        const C* Su = nullptr;
+        if (resident) {
+            // forward position: down row r0+i at i + min(i, nu); up row r1-1-i at min(i+1, nd) + i
+            if (dn) { const int i = kd - r0; Sd = reinterpret_cast<const C*>(slots + (size_t)(i + imin(i, nu)) * sb); }
+            if (up) { const int i = r1 - 1 - ku; Su = reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb); }
+        } else {
+            if (dn) Sd = consume();
+            if (up) Su = consume();
         }
-        C* t = tin; tin = tout; tout = t;
+        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        const C cd = cpl(kd), cu = cpl(ku + 1);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                if (dn) {
+                    C* zp = zr(kd) + b * W + row;
+                    const C y = csub(*zp, vd[b]);
+                    *zp = y;
+                    vout_d[b * 64 + row] = cmul(cd, y);        // C_kd y_kd for row kd-1
+                }
+                if (up) {
+                    C* zp = zr(ku) + b * W + row;
+                    const C y = csub(*zp, vu[b]);
+                    *zp = y;
+                    vout_u[b * 64 + row] = cmul(cu, y);        // C_{ku+1} y_ku for row ku+1
+                }
+            }
+        if (!finish()) return;
     }
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
-        yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * Bt + b) * W + c];
+        yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * BT + b) * W + c];
     }
-    // ---- separator right-hand-side parts: A_p = Rinv_p (b_s - C_s y(last)), s = r1
-    //      and B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first), s' = r0 - 1
+    // ---- separator right-hand-side parts, both in one step:
+    //   down chain: A_p     = Rinv_p     (b_s - C_s y(last)),   s = r1      (separator below)
+    //   up chain:   B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first),     s' = r0 - 1 (separator above)
     if (Q > 0) {
         C* parts = reinterpret_cast<C*>(A.parts);
-        for (int part = 0; part < 2; ++part) {
-            const bool active = part == 0 ? has_below : has_above;
-            if (!active) continue;
-            for (int o = tid; o < nb * W; o += blockDim.x) {
-                const int c = o % W, b = o / W;
-                C t;
-                if (part == 0)
-                    t = csub(rhs_entry<C>(A, r1, c, b0 + b),
-                             cmul(cmul(csx[c], cy(r1)), zb[((m - 1) * Bt + b) * W + c]));
-                else
-                    t = cneg(cmul(cmul(csx[c], cy(r0)), zb[b * W + c]));
-                tin[b * 64 + c] = t;
-            }
-            __syncthreads();
-            const C* S = consume();
-            const int q = part == 0 ? p : p - 1;
-            step(S, tin, [&](int b, C v) {
-                parts[((((int64_t)(b0 + b) * Q + q) * 2 + part) * A.Wmax) + row] = v;
-            });
-            __syncthreads();
-            if (flags[1]) { drain(); return; }
-            if (tid == 0 && !resident && G + ring < nload) issue_into(last_slot, block_of(G + ring));
-            ++G;
+        for (int o = tid; o < nb * W; o += blockDim.x) {
+            const int c = o % W, b = o / W;
+            if (has_below)
+                vin_d[b * 64 + c] = csub(rhs_entry<C>(A, r1, c, b0 + b),
+                                         cmul(cmul(csx[c], ccy[r1 - r0]), zr(r1 - 1)[b * W + c]));
+            if (has_above) vin_u[b * 64 + c] = cneg(cmul(cmul(csx[c], ccy[0]), zr(r0)[b * W + c]));
         }
+        __syncthreads();
+        const C* SA = has_below ? consume() : nullptr;
+        const C* SB = has_above ? consume() : nullptr;
+        if (compute)
+            dual_dispatch<C, NJ, BT>(has_below, has_above, SA + lofs, vin_d + vofs, SB + lofs, vin_u + vofs, nb,
+                                     vd, vu);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                if (has_below) parts[((((int64_t)(b0 + b) * Q + p) * 2 + 0) * A.Wmax) + row] = vd[b];
+                if (has_above) parts[((((int64_t)(b0 + b) * Q + p - 1) * 2 + 1) * A.Wmax) + row] = vu[b];
+            }
+        if (!finish()) return;
     }
     if (Q == 0) return;
     // ---- arrival: the last CTA of this tile solves the separator system
@@ -340,68 +477,113 @@ __global__ void __launch_bounds__(256) k_sweep_chunk(SweepArgs A) {
     __syncthreads();
     if (!flags[0]) return;
     __threadfence();
-    {
-        const C* parts = reinterpret_cast<const C*>(A.parts);
-        const C* E = reinterpret_cast<const C*>(A.E) + A.st.red;
-        const C* F = reinterpret_cast<const C*>(A.F) + A.st.red;
-        // loads continue the same ring sequence: E_1..E_{Q-1}, F_{Q-2}..F_0
-        const int nred = 2 * (Q - 1);
-        auto rblock = [&](int i) -> const C* {
-            if (i < Q - 1) return E + (int64_t)(1 + i) * bs;
-            return F + (int64_t)(Q - 2 - (i - (Q - 1))) * bs;
-        };
-        // every earlier load has been consumed: continue from slot `cslot`
-        if (tid == 0) {
-            int sl = cslot;
-            for (int i = 0; i < imin(ring, nred); ++i) {
-                issue_into(sl, rblock(i));
-                if (++sl == ring) sl = 0;
-            }
+    const C* parts = reinterpret_cast<const C*>(A.parts);
+    const int tq = (Q - 1) / 2;
+    const int fd = imax(tq - 1, 0), fu = imax(Q - 2 - tq, 0), fmx = imax(fd, fu);   // forward steps
+    const int bd = tq, bu = Q - 1 - tq, bmx = imax(bd, bu);                         // back steps
+    // separator load order, encoded q >= 0 -> E_q, q < 0 -> F_{-q-1}; every earlier
+    // load has been consumed, so the ring continues from slot cslot
+    sep_phase = true;
+    if (producer) {
+        int nr = 0;
+        for (int s = 0; s < fmx; ++s) {
+            if (s < fd) order[nr++] = 1 + s;
+            if (s < fu) order[nr++] = Q - 2 - s;
         }
-        // a_q = A_q + B_q
-        for (int o = tid; o < Q * nb * W; o += blockDim.x) {
-            const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
-            const int64_t base = (((int64_t)(b0 + b) * Q + q) * 2) * A.Wmax + c;
-            const C v = cadd(__ldcg(parts + base), __ldcg(parts + base + A.Wmax));
-            zb[(q * Bt + b) * W + c] = v;
-            if (q == 0) tin[b * 64 + c] = v;
+        if (tq >= 1) order[nr++] = tq;
+        if (tq <= Q - 2) order[nr++] = -(tq + 1);
+        for (int s = 0; s < bmx; ++s) {
+            if (s < bd) order[nr++] = -(tq - 1 - s + 1);
+            if (s < bu) order[nr++] = -(tq + 1 + s + 1);
         }
-        __syncthreads();
-        int i = 0;   // separator-load counter
-        // forward: z_q = a_q - E_q z_{q-1}
-        for (int q = 1; q < Q; ++q) {
-            const C* S = consume();
-            step(S, tin, [&](int b, C v) {
-                const C z = csub(zb[(q * Bt + b) * W + row], v);
-                zb[(q * Bt + b) * W + row] = z;
-                tout[b * 64 + row] = z;
-            });
-            __syncthreads();
-            if (flags[1]) { drain(); return; }
-            if (tid == 0 && i + ring < nred) issue_into(last_slot, rblock(i + ring));
-            ++i;
-            C* t = tin; tin = tout; tout = t;
+        seqbase = consumed;
+        nseq = seqbase + nr;
+        rf = seqbase;
+        rfslot = cslot;
+        int sl = cslot;
+        for (int i = 0; i < imin(ring, nr); ++i) {
+            issue_into(sl, src_of(seqbase + i));
+            if (++sl == ring) sl = 0;
         }
-        // backward: x_q = z_q - F_q x_{q+1}
-        for (int q = Q - 2; q >= 0; --q) {
-            const C* S = consume();
-            step(S, tin, [&](int b, C v) {
-                const C x = csub(zb[(q * Bt + b) * W + row], v);
-                zb[(q * Bt + b) * W + row] = x;
-                tout[b * 64 + row] = x;
-            });
-            __syncthreads();
-            if (flags[1]) { drain(); return; }
-            if (tid == 0 && i + ring < nred) issue_into(last_slot, rblock(i + ring));
-            ++i;
-            C* t = tin; tin = tout; tout = t;
-        }
-        for (int o = tid; o < Q * nb * W; o += blockDim.x) {
-            const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
-            yrow<C>(A, b0 + b, A.g.r1[q])[c] = zb[(q * Bt + b) * W + c];
-        }
-        if (tid == 0) A.counters[tile] = 0;
     }
+    // a_q = A_q + B_q
+    for (int o = tid; o < Q * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
+        const int64_t pb = (((int64_t)(b0 + b) * Q + q) * 2) * A.Wmax + c;
+        const C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
+        zb[(q * BT + b) * W + c] = v;
+        if (q == 0) vin_d[b * 64 + c] = v;
+        if (q == Q - 1) vin_u[b * 64 + c] = v;
+    }
+    __syncthreads();
+    auto zq = [&](int q) -> C* { return zb + q * BT * W; };
+    // out_q = z_q - product, stored to z_q and to the chain's next input
+    auto sep_store = [&](bool dn, int qd, bool up, int qu) {
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                if (dn) {
+                    C* zp = zq(qd) + b * W + row;
+                    const C x = csub(*zp, vd[b]);
+                    *zp = x;
+                    vout_d[b * 64 + row] = x;
+                }
+                if (up) {
+                    C* zp = zq(qu) + b * W + row;
+                    const C x = csub(*zp, vu[b]);
+                    *zp = x;
+                    vout_u[b * 64 + row] = x;
+                }
+            }
+    };
+    // forward: z_q = a_q - E_q z_outer, down q = 1..tq-1, up q = Q-2..tq+1
+    for (int s = 0; s < fmx; ++s) {
+        const bool dn = s < fd, up = s < fu;
+        const C* Sd = dn ? consume() : nullptr;
+        const C* Su = up ? consume() : nullptr;
+        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        sep_store(dn, 1 + s, up, Q - 2 - s);
+        if (!finish()) return;
+    }
+    // twist: x_tq = a_tq - E_tq z_{tq-1} - F_tq z_{tq+1}
+    for (int o = tid; o < nb * W; o += blockDim.x) {
+        const int c = o % W, b = o / W;
+        if (tq >= 1) vin_d[b * 64 + c] = zq(tq - 1)[b * W + c];
+        if (tq <= Q - 2) vin_u[b * 64 + c] = zq(tq + 1)[b * W + c];
+    }
+    __syncthreads();
+    {
+        const bool he = tq >= 1, hf = tq <= Q - 2;
+        const C* Se = he ? consume() : nullptr;
+        const C* Sf = hf ? consume() : nullptr;
+        if (compute) dual_dispatch<C, NJ, BT>(he, hf, Se + lofs, vin_d + vofs, Sf + lofs, vin_u + vofs, nb, vd, vu);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                C* zp = zq(tq) + b * W + row;
+                C x = *zp;
+                if (he) x = csub(x, vd[b]);
+                if (hf) x = csub(x, vu[b]);
+                *zp = x;
+                vout_d[b * 64 + row] = x;
+                vout_u[b * 64 + row] = x;
+            }
+        if (!finish()) return;
+    }
+    // back: x_q = z_q - F_q x_inner, down q = tq-1..0, up q = tq+1..Q-1
+    for (int s = 0; s < bmx; ++s) {
+        const bool dn = s < bd, up = s < bu;
+        const C* Sd = dn ? consume() : nullptr;
+        const C* Su = up ? consume() : nullptr;
+        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        sep_store(dn, tq - 1 - s, up, tq + 1 + s);
+        if (!finish()) return;
+    }
+    for (int o = tid; o < Q * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
+        yrow<C>(A, b0 + b, A.g.r1[q])[c] = zb[(q * BT + b) * W + c];
+    }
+    if (tid == 0) A.counters[tile] = 0;
 }
 
 // ------------------------------------------------------------------ correction
@@ -505,8 +687,8 @@ template <typename C>
 static bool plan(const StripDev& st, int zrows, int B, int& Bt, int& ring, size_t& smem) {
     const size_t budget = 220 * 1024;
     const uint32_t slot = (uint32_t)(st.bs * sizeof(C));
-    for (Bt = imin(B, 4); Bt >= 1; --Bt) {
-        for (ring = kMaxRing; ring >= 2; --ring) {
+    for (Bt = (B > 1 ? 4 : 1); Bt >= 1; Bt -= 3) {   // tiles of 4 right-hand sides, or 1
+        for (ring = kMaxRing; ring >= 4; --ring) {
             smem = sweep_smem(ring, slot, zrows, Bt, st.W, (int)sizeof(C)).total;
             if (smem <= budget) return true;
         }
@@ -524,7 +706,10 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     if (!plan<C>(st, wk.zrows, wk.B, Bt, ring, smem)) return cudaErrorInvalidConfiguration;
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto fn : {k_sweep_chunk<C, 8>, k_sweep_chunk<C, 12>, k_sweep_chunk<C, 16>}) {
+        for (auto fn : {k_sweep_chunk<C, 8, 1>, k_sweep_chunk<C, 10, 1>, k_sweep_chunk<C, 12, 1>,
+                        k_sweep_chunk<C, 14, 1>, k_sweep_chunk<C, 16, 1>, k_sweep_chunk<C, 8, 4>,
+                        k_sweep_chunk<C, 10, 4>, k_sweep_chunk<C, 12, 4>, k_sweep_chunk<C, 14, 4>,
+                        k_sweep_chunk<C, 16, 4>}) {
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
             if (e != cudaSuccess) return e;
         }
@@ -535,10 +720,18 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     {
         TimedLaunch t(tm, "sweep_chunk", s);
         const dim3 grid(g.P, ntile);
-        const int nthr = 32 * ((st.W + 7) / 8);
-        if (st.W <= 32) k_sweep_chunk<C, 8><<<grid, nthr, smem, s>>>(A);
-        else if (st.W <= 48) k_sweep_chunk<C, 12><<<grid, nthr, smem, s>>>(A);
-        else k_sweep_chunk<C, 16><<<grid, nthr, smem, s>>>(A);
+        const int nthr = 32 * ((st.W + 7) / 8 + 1);   // compute warps + the producer warp
+#define HELM_LAUNCH_CHUNK(NJ)                                                         \
+    (Bt == 1 ? (k_sweep_chunk<C, NJ, 1><<<grid, nthr, smem, s>>>(A), 0)              \
+             : (k_sweep_chunk<C, NJ, 4><<<grid, nthr, smem, s>>>(A), 0))
+        switch (st.nj) {
+            case 8: HELM_LAUNCH_CHUNK(8); break;
+            case 10: HELM_LAUNCH_CHUNK(10); break;
+            case 12: HELM_LAUNCH_CHUNK(12); break;
+            case 14: HELM_LAUNCH_CHUNK(14); break;
+            default: HELM_LAUNCH_CHUNK(16); break;
+        }
+#undef HELM_LAUNCH_CHUNK
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
