@@ -19,6 +19,8 @@
 //
 // Every mbarrier wait is bounded; on time-out the kernel records
 // HELM_ETIMEOUT in the status word, drains its copies (bounded) and returns.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -360,27 +362,50 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         return true;
     };
     C vd[BT], vu[BT];
-    // ---- forward elimination of both halves
-    for (int s = 0; s < nmx; ++s) {
-        const bool dn = s < nd, up = s < nu;
-        const int kd = r0 + s, ku = r1 - 1 - s;
-        const C* Sd = dn ? consume() : nullptr;
-        const C* Su = up ? consume() : nullptr;
-        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
-        const C cd = cpl(kd + 1), cu = cpl(ku);
+    const bool own1 = rowok && g == 0;                 // BT = 1: the lane that stores a row
+    auto owns = [&](int b) -> bool { return BT == 1 ? own1 : (b < nb && rowok && (b & 3) == g); };
+    C* const zl = zb + row;                            // this lane's entry of z-buffer row r0, b = 0
+    const int zs = BT * W;                             // z-buffer stride between grid rows
+    // ---- forward elimination: both halves while both have rows, then the longer one
+    auto fwd = [&](auto Dc, auto Uc, int s) -> bool {
+        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+        const C* Sd = D ? consume() : nullptr;
+        const C* Su = U ? consume() : nullptr;
+        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        if (D) {   // z_kd, kd = r0+s; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
+            const C ck = cmul(csx_r, ccy[s + 1]);
+            C* zp = zl + s * zs;
+            const bool more = r0 + s + 1 < t;
 #pragma unroll
-        for (int b = 0; b < BT; ++b)
-            if (b < nb && rowok && (b & 3) == g) {
-                if (dn) {   // z_kd; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
-                    zr(kd)[b * W + row] = vd[b];
-                    if (kd + 1 < t) vout_d[b * 64 + row] = csub(zr(kd + 1)[b * W + row], cmul(cd, vd[b]));
+            for (int b = 0; b < BT; ++b)
+                if (owns(b)) {
+                    zp[b * W] = vd[b];
+                    if (more) vout_d[b * 64 + row] = csub(zp[zs + b * W], cmul(ck, vd[b]));
                 }
-                if (up) {   // z_ku; next up input b_{ku-1} - C_ku z_ku (if ku-1 > t)
-                    zr(ku)[b * W + row] = vu[b];
-                    if (ku - 1 > t) vout_u[b * 64 + row] = csub(zr(ku - 1)[b * W + row], cmul(cu, vu[b]));
+        }
+        if (U) {   // z_ku, ku = r1-1-s; next up input b_{ku-1} - C_ku z_ku (if ku-1 > t)
+            const int ui = m - 1 - s;                      // ku - r0
+            const C ck = cmul(csx_r, ccy[ui]);
+            C* zp = zl + ui * zs;
+            const bool more = r1 - 2 - s > t;
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+                if (owns(b)) {
+                    zp[b * W] = vu[b];
+                    if (more) vout_u[b * 64 + row] = csub(zp[-zs + b * W], cmul(ck, vu[b]));
                 }
-            }
-        if (!finish()) return;
+        }
+        return finish();
+    };
+    {
+        int s = 0;
+        const int nboth = imin(nd, nu);
+        for (; s < nboth; ++s)
+            if (!fwd(std::true_type{}, std::true_type{}, s)) return;
+        for (; s < nd; ++s)
+            if (!fwd(std::true_type{}, std::false_type{}, s)) return;
+        for (; s < nu; ++s)
+            if (!fwd(std::false_type{}, std::true_type{}, s)) return;
     }
     // ---- twist row: y_t = Sinv_t (b_t - C_t z_{t-1} - C_{t+1} z_{t+1})
     for (int o = tid; o < nb * W; o += blockDim.x) {
@@ -393,11 +418,11 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     __syncthreads();
     {
         const C* St = consume();
-        if (compute) dual_dispatch<C, NJ, BT>(true, false, St + lofs, vin_d + vofs, St, vin_u, nb, vd, vu);
+        if (compute) dual_rows<C, NJ, BT, true, false>(St + lofs, vin_d + vofs, St, vin_u, nb, vd, vu);
         const C cd = cpl(t), cu = cpl(t + 1);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
-            if (b < nb && rowok && (b & 3) == g) {
+            if (owns(b)) {
                 zr(t)[b * W + row] = vd[b];
                 vout_d[b * 64 + row] = cmul(cd, vd[b]);   // C_t y_t for row t-1
                 vout_u[b * 64 + row] = cmul(cu, vd[b]);   // C_{t+1} y_t for row t+1
@@ -405,38 +430,54 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!finish()) return;
     }
     // ---- outward back substitution: y_k = z_k - Sinv_k C y_inner
-    for (int s = 0; s < nmx; ++s) {
-        const bool dn = s < nd, up = s < nu;
-        const int kd = t - 1 - s, ku = t + 1 + s;
+    auto bwd = [&](auto Dc, auto Uc, int s) -> bool {
+        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+        const int di = nd - 1 - s;              // kd - r0, kd = t-1-s
+        const int ui = nd + 1 + s;              // ku - r0, ku = t+1+s
         const C* Sd = nullptr;
         const C* Su = nullptr;
         if (resident) {
             // forward position: down row r0+i at i + min(i, nu); up row r1-1-i at min(i+1, nd) + i
-            if (dn) { const int i = kd - r0; Sd = reinterpret_cast<const C*>(slots + (size_t)(i + imin(i, nu)) * sb); }
-            if (up) { const int i = r1 - 1 - ku; Su = reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb); }
+            if (D) Sd = reinterpret_cast<const C*>(slots + (size_t)(di + imin(di, nu)) * sb);
+            if (U) { const int i = m - 1 - ui; Su = reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb); }
         } else {
-            if (dn) Sd = consume();
-            if (up) Su = consume();
+            if (D) Sd = consume();
+            if (U) Su = consume();
         }
-        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
-        const C cd = cpl(kd), cu = cpl(ku + 1);
+        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        if (D) {
+            const C ck = cmul(csx_r, ccy[di]);      // C_kd y_kd for row kd-1
+            C* zp = zl + di * zs;
 #pragma unroll
-        for (int b = 0; b < BT; ++b)
-            if (b < nb && rowok && (b & 3) == g) {
-                if (dn) {
-                    C* zp = zr(kd) + b * W + row;
-                    const C y = csub(*zp, vd[b]);
-                    *zp = y;
-                    vout_d[b * 64 + row] = cmul(cd, y);        // C_kd y_kd for row kd-1
+            for (int b = 0; b < BT; ++b)
+                if (owns(b)) {
+                    const C y = csub(zp[b * W], vd[b]);
+                    zp[b * W] = y;
+                    vout_d[b * 64 + row] = cmul(ck, y);
                 }
-                if (up) {
-                    C* zp = zr(ku) + b * W + row;
-                    const C y = csub(*zp, vu[b]);
-                    *zp = y;
-                    vout_u[b * 64 + row] = cmul(cu, y);        // C_{ku+1} y_ku for row ku+1
+        }
+        if (U) {
+            const C ck = cmul(csx_r, ccy[ui + 1]);  // C_{ku+1} y_ku for row ku+1
+            C* zp = zl + ui * zs;
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+                if (owns(b)) {
+                    const C y = csub(zp[b * W], vu[b]);
+                    zp[b * W] = y;
+                    vout_u[b * 64 + row] = cmul(ck, y);
                 }
-            }
-        if (!finish()) return;
+        }
+        return finish();
+    };
+    {
+        int s = 0;
+        const int nboth = imin(nd, nu);
+        for (; s < nboth; ++s)
+            if (!bwd(std::true_type{}, std::true_type{}, s)) return;
+        for (; s < nd; ++s)
+            if (!bwd(std::true_type{}, std::false_type{}, s)) return;
+        for (; s < nu; ++s)
+            if (!bwd(std::false_type{}, std::true_type{}, s)) return;
     }
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
@@ -517,33 +558,40 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     }
     __syncthreads();
     auto zq = [&](int q) -> C* { return zb + q * BT * W; };
-    // out_q = z_q - product, stored to z_q and to the chain's next input
-    auto sep_store = [&](bool dn, int qd, bool up, int qu) {
+    // one separator step: out_q = z_q - product, stored to z_q and to the chain's next input
+    auto sep = [&](auto Dc, auto Uc, int qd, int qu) -> bool {
+        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+        const C* Sd = D ? consume() : nullptr;
+        const C* Su = U ? consume() : nullptr;
+        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
-            if (b < nb && rowok && (b & 3) == g) {
-                if (dn) {
+            if (owns(b)) {
+                if (D) {
                     C* zp = zq(qd) + b * W + row;
                     const C x = csub(*zp, vd[b]);
                     *zp = x;
                     vout_d[b * 64 + row] = x;
                 }
-                if (up) {
+                if (U) {
                     C* zp = zq(qu) + b * W + row;
                     const C x = csub(*zp, vu[b]);
                     *zp = x;
                     vout_u[b * 64 + row] = x;
                 }
             }
+        return finish();
     };
     // forward: z_q = a_q - E_q z_outer, down q = 1..tq-1, up q = Q-2..tq+1
-    for (int s = 0; s < fmx; ++s) {
-        const bool dn = s < fd, up = s < fu;
-        const C* Sd = dn ? consume() : nullptr;
-        const C* Su = up ? consume() : nullptr;
-        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
-        sep_store(dn, 1 + s, up, Q - 2 - s);
-        if (!finish()) return;
+    {
+        int s = 0;
+        const int nboth = imin(fd, fu);
+        for (; s < nboth; ++s)
+            if (!sep(std::true_type{}, std::true_type{}, 1 + s, Q - 2 - s)) return;
+        for (; s < fd; ++s)
+            if (!sep(std::true_type{}, std::false_type{}, 1 + s, 0)) return;
+        for (; s < fu; ++s)
+            if (!sep(std::false_type{}, std::true_type{}, 0, Q - 2 - s)) return;
     }
     // twist: x_tq = a_tq - E_tq z_{tq-1} - F_tq z_{tq+1}
     for (int o = tid; o < nb * W; o += blockDim.x) {
@@ -571,13 +619,15 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!finish()) return;
     }
     // back: x_q = z_q - F_q x_inner, down q = tq-1..0, up q = tq+1..Q-1
-    for (int s = 0; s < bmx; ++s) {
-        const bool dn = s < bd, up = s < bu;
-        const C* Sd = dn ? consume() : nullptr;
-        const C* Su = up ? consume() : nullptr;
-        if (compute) dual_dispatch<C, NJ, BT>(dn, up, Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
-        sep_store(dn, tq - 1 - s, up, tq + 1 + s);
-        if (!finish()) return;
+    {
+        int s = 0;
+        const int nboth = imin(bd, bu);
+        for (; s < nboth; ++s)
+            if (!sep(std::true_type{}, std::true_type{}, tq - 1 - s, tq + 1 + s)) return;
+        for (; s < bd; ++s)
+            if (!sep(std::true_type{}, std::false_type{}, tq - 1 - s, 0)) return;
+        for (; s < bu; ++s)
+            if (!sep(std::false_type{}, std::true_type{}, 0, tq + 1 + s)) return;
     }
     for (int o = tid; o < Q * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
