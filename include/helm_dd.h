@@ -98,6 +98,18 @@ helm_status helm_dd_set_pml_speed(helm_dd* h, double c_ref);
  * built-in choice.  Must be called before helm_dd_factor. */
 helm_status helm_dd_set_chunks(helm_dd* h, int P);
 
+/* Number of groups G the P-1 separator rows of every strip are cut into (a
+ * second level of nested dissection along y): G-1 separators become level-2
+ * separators and the rest form G groups of consecutive separators, each solved
+ * on its own before the small level-2 system couples them.  1 = one separator
+ * chain; 0 selects the built-in choice (about sqrt(P-1)); values above P/2 are
+ * clamped.  Must be called before helm_dd_factor.  The result is the same up to
+ * rounding for every G. */
+helm_status helm_dd_set_sep_groups(helm_dd* h, int G);
+
+/* G in use after helm_dd_factor (0 before). */
+int helm_dd_sep_groups(const helm_dd* h);
+
 /* Algorithm 1 (preparation): assemble every strip operator A^(j) on the grid of
  * Eq. grid_A_j (physical columns beta_{j-1}+1 .. beta_j+1 plus w_sub added PML
  * columns on internal sides, k held constant in x across an added layer) in its

@@ -115,6 +115,14 @@ struct Geom {
     // and the right-hand-side scaling is s_x(c) s_y(k).
     const void* ct;
     int64_t ct_sy, ct_cy;
+    // second level of nested dissection on the separator system: groups
+    // g = 0..G-1 of separators gq0[g] .. gq1[g]-1; level-2 separator r (r < G-1)
+    // is separator gq1[r]; sepmap[q] = group of separator q, or -(r+1) for a
+    // level-2 separator.  G = 1: one group, no level 2.
+    int G;
+    const int* gq0;
+    const int* gq1;
+    const int* sepmap;
 };
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }

@@ -21,7 +21,8 @@
 // separator below) and GT = A_p^{-1} E_first C_{r0} (separator above), so that
 // the chunk solution is x_p = y_p - GT x_sep(p-1) - GB x_sep(p).
 //
-// Separator system (k_factor_reduced, one CTA per strip), q = 0..Q-1, Q = P-1:
+// Separator system (k_factor_sep, one CTA per strip), q = 0..Q-1, Q = P-1, solved
+// in groups (a second level of nested dissection, see k_factor_sep):
 //   T_q = D_s - C_s GB_q(last) - C_{s+1} GT_{q+1}(first),   s = r1[q]
 //   L_q = -C_s GT_q(last),  U_q = -C_{s+1} GB_{q+1}(first)
 // twisted at tq = (Q-1)/2.  Stored per separator: Rinv_q, an "outer" coupling
@@ -213,152 +214,277 @@ __global__ void k_factor_chunk(Geom g, C* __restrict__ Sinv, C* __restrict__ GT,
     }
 }
 
+// Twisted LU of a block-tridiagonal system with dense couplings, elements
+// i = 0..n-1 stored at separator slots sl(i): bT(i) builds the diagonal block
+// into M, bL(i, D) / bU(i, D) build the couplings to i-1 / i+1 into D (they may
+// use Y and Z as scratch but not M).  Stores Rinv, the outer coupling E and the
+// inner coupling F of every element (see the file header).  Shared buffers:
+// M, X, Y, Z (column-major W x W).
+template <typename C, typename SL, typename BT_, typename BL, typename BU>
+__device__ bool twisted_lu(const StripDev& st, int n, SL sl, BT_ bT, BL bL, BU bU, C* Rp, C* Ep, C* Fp, C* M,
+                           C* X, C* Y, int* piv, C* colk, double* red, int* status) {
+    using R = typename CT<C>::R;
+    const int W = st.W;
+    const int64_t bs = st.bs;
+    auto slot = [&](C* pool, int i) { return pool + (int64_t)sl(i) * bs; };
+    auto sub_nb = [&](C* Fpool, int inb) {   // M -= X F_nb
+        load_block(Y, slot(Fpool, inb), W, st.ld);
+        __syncthreads();
+        block_gemm_dscale<C>(M, X, nullptr, Y, W, true, (R)-1);
+    };
+    auto inv_store = [&](int i) -> bool {
+        if (!block_inverse(M, W, piv, colk, red)) {
+            if (threadIdx.x == 0) atomicExch(status, 2);
+            return false;
+        }
+        store_block(slot(Rp, i), M, W, st.ld);
+        __syncthreads();
+        return true;
+    };
+    auto prod_store = [&](C* dst) {   // dst = M X (M = Rinv)
+        block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)1);
+        store_block(dst, Y, W, st.ld);
+        __syncthreads();
+    };
+    auto zero_store = [&](C* dst) {
+        for (int e = threadIdx.x; e < W * st.ld; e += blockDim.x) dst[e] = CT<C>::zero();
+        __syncthreads();
+    };
+    const int tq = (n - 1) / 2;
+    for (int i = 0; i < tq; ++i) {                   // top down
+        bT(i);
+        if (i >= 1) { bL(i, X); sub_nb(Fp, i - 1); }
+        if (!inv_store(i)) return false;
+        if (i >= 1) { bL(i, X); prod_store(slot(Ep, i)); } else zero_store(slot(Ep, i));
+        bU(i, X);
+        prod_store(slot(Fp, i));
+    }
+    for (int i = n - 1; i > tq; --i) {               // bottom up
+        bT(i);
+        if (i <= n - 2) { bU(i, X); sub_nb(Fp, i + 1); }
+        if (!inv_store(i)) return false;
+        if (i <= n - 2) { bU(i, X); prod_store(slot(Ep, i)); } else zero_store(slot(Ep, i));
+        bL(i, X);
+        prod_store(slot(Fp, i));
+    }
+    {                                                // twist
+        const int i = tq;
+        bT(i);
+        if (i >= 1) { bL(i, X); sub_nb(Fp, i - 1); }
+        if (i <= n - 2) { bU(i, X); sub_nb(Fp, i + 1); }
+        if (!inv_store(i)) return false;
+        if (i >= 1) { bL(i, X); prod_store(slot(Ep, i)); } else zero_store(slot(Ep, i));
+        if (i <= n - 2) { bU(i, X); prod_store(slot(Fp, i)); } else zero_store(slot(Fp, i));
+    }
+    return true;
+}
+
 template <typename C>
-__global__ void k_factor_reduced(Geom g, const C* __restrict__ GT, const C* __restrict__ GB,
-                                 C* __restrict__ Rinv, C* __restrict__ E, C* __restrict__ F,
-                                 int* __restrict__ status) {
+struct SepPools {
+    C* Rinv;   // per separator slot, sweep layout
+    C* E;
+    C* F;
+    C* GT2;    // group spikes, row-major W x W
+    C* GB2;
+    C* P2L;    // level-2 right-hand-side products Rinv2 L, Rinv2 U (sweep layout)
+    C* P2U;
+};
+
+// Separator system of every strip (one CTA per strip): twisted LU of each group,
+// the group spikes, and (G > 1) the level-2 system and its products.
+template <typename C>
+__global__ void k_factor_sep(Geom g, const C* __restrict__ GT, const C* __restrict__ GB, SepPools<C> pl,
+                             int* __restrict__ status) {
     const StripDev st = g.strips[blockIdx.x];
     const int W = st.W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* M = reinterpret_cast<C*>(smem_raw);
     C* X = M + W * W;
     C* Y = X + W * W;
-    C* d0 = Y + W * W;          // C_s
-    C* d1 = d0 + W;             // C_{s+1}
-    C* colk = d1 + W;
+    C* Z = g.G > 1 ? Y + W * W : nullptr;   // level-2 scratch, only with groups
+    C* colk = Y + (g.G > 1 ? 2 : 1) * W * W + W;
     int* piv = reinterpret_cast<int*>(colk + W);
     double* red = reinterpret_cast<double*>(piv + ((W + 3) & ~3));
+    using R = typename CT<C>::R;
     const int64_t bs = st.bs;
     const C* GTs = GT + st.fac;
     const C* GBs = GB + st.fac;
-    C* Rs = Rinv + st.red;
-    C* Es = E + st.red;
-    C* Fs = F + st.red;
-    using R = typename CT<C>::R;
-    const int Q = g.P - 1;
-    const int tq = (Q - 1) / 2;
+    SepPools<C> P = pl;
+    P.Rinv += st.red; P.E += st.red; P.F += st.red; P.GT2 += st.red; P.GB2 += st.red; P.P2L += st.red;
+    P.P2U += st.red;
+    const int G = g.G;
 
-    // M <- T_q; leaves C_s in d0 and C_{s+1} in d1
-    auto build_T = [&](int q) {
+    // ---- level-1 blocks of separator q (row s = r1[q])
+    auto build_T1 = [&](int q) {   // M <- T_q = D_s - C_s GB_q(last) - C_{s+1} GT_{q+1}(first)
         const int s = g.r1[q];
-        for (int c = threadIdx.x; c < W; c += blockDim.x) {
-            d0[c] = CT<C>::from(strip_coupling(g, st, s, c));
-            d1[c] = CT<C>::from(strip_coupling(g, st, s + 1, c));
-        }
         build_diag_block(g, st, s, M);
         const int last_q = s - 1, first_q1 = g.r0[q + 1];
         for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
             const int r = e % W;
             C tt = M[e];
-            tt = csub(tt, cmul(d0[r], GBs[(int64_t)last_q * bs + trp(e, W)]));
-            tt = csub(tt, cmul(d1[r], GTs[(int64_t)first_q1 * bs + trp(e, W)]));
+            tt = csub(tt, cmul(CT<C>::from(strip_coupling(g, st, s, r)), GBs[(int64_t)last_q * bs + trp(e, W)]));
+            tt = csub(tt, cmul(CT<C>::from(strip_coupling(g, st, s + 1, r)), GTs[(int64_t)first_q1 * bs + trp(e, W)]));
             M[e] = tt;
         }
         __syncthreads();
     };
-    // X <- L_q = -C_s GT_q(last)   (q >= 1)
-    auto build_L = [&](int q, C* D) {
-        const int last_q = g.r1[q] - 1;
+    auto build_L1 = [&](int q, C* D) {   // L_q = -C_s GT_q(last)
+        const int s = g.r1[q];
         for (int e = threadIdx.x; e < W * W; e += blockDim.x)
-            D[e] = cneg(cmul(d0[e % W], GTs[(int64_t)last_q * bs + trp(e, W)]));
+            D[e] = cneg(cmul(CT<C>::from(strip_coupling(g, st, s, e % W)), GTs[(int64_t)(s - 1) * bs + trp(e, W)]));
         __syncthreads();
     };
-    // D <- U_q = -C_{s+1} GB_{q+1}(first)   (q <= Q-2)
-    auto build_U = [&](int q, C* D) {
+    auto build_U1 = [&](int q, C* D) {   // U_q = -C_{s+1} GB_{q+1}(first)
+        const int s = g.r1[q];
         const int first_q1 = g.r0[q + 1];
         for (int e = threadIdx.x; e < W * W; e += blockDim.x)
-            D[e] = cneg(cmul(d1[e % W], GBs[(int64_t)first_q1 * bs + trp(e, W)]));
+            D[e] = cneg(cmul(CT<C>::from(strip_coupling(g, st, s + 1, e % W)), GBs[(int64_t)first_q1 * bs + trp(e, W)]));
         __syncthreads();
     };
-    auto invert_store = [&](int q) -> bool {
-        if (!block_inverse(M, W, piv, colk, red)) {
-            if (threadIdx.x == 0) atomicExch(status, 2);
-            return false;
+
+    // ---- groups: twisted LU of each group's separators
+    for (int gi = 0; gi < G; ++gi) {
+        const int q0 = g.gq0[gi], n = g.gq1[gi] - q0;
+        auto sl = [&](int i) { return q0 + i; };
+        if (!twisted_lu<C>(st, n, sl, [&](int i) { build_T1(q0 + i); },
+                           [&](int i, C* D) { build_L1(q0 + i, D); }, [&](int i, C* D) { build_U1(q0 + i, D); },
+                           P.Rinv, P.E, P.F, M, X, Y, piv, colk, red, status))
+            return;
+    }
+    if (G == 1) return;
+
+    // ---- group spikes: response of group gi to the level-2 separator above
+    // (right-hand side L_{q0} at its first element) and below (U_{q1-1} at its last)
+    auto rowmajor_store = [&](C* dst, const C* src) {
+        for (int e = threadIdx.x; e < W * W; e += blockDim.x) dst[trp(e, W)] = src[e];
+    };
+    auto rowmajor_load = [&](C* dst, const C* src) {
+        for (int e = threadIdx.x; e < W * W; e += blockDim.x) dst[e] = src[trp(e, W)];
+    };
+    for (int gi = 0; gi < G; ++gi) {
+        const int q0 = g.gq0[gi], q1 = g.gq1[gi], n = q1 - q0, tq = (n - 1) / 2;
+        for (int side = 0; side < 2; ++side) {
+            const bool top = side == 0;
+            if (top && gi == 0) continue;
+            if (!top && gi == G - 1) continue;
+            C* OUT = top ? P.GT2 : P.GB2;
+            auto out = [&](int i) { return OUT + (int64_t)(q0 + i) * bs; };
+            const int rs = top ? 0 : n - 1;
+            // X <- Rinv_rs B, B = L_{q0} (top) or U_{q1-1} (bottom)
+            if (top) build_L1(q0, Z); else build_U1(q1 - 1, Z);
+            load_block(M, P.Rinv + (int64_t)(q0 + rs) * bs, W, st.ld);
+            __syncthreads();
+            block_gemm_dscale<C>(X, M, nullptr, Z, W, false, (R)1);
+            if (rs != tq) {
+                rowmajor_store(out(rs), X);
+                const int dir = rs < tq ? 1 : -1;
+                for (int i = rs + dir; i != tq; i += dir) {   // z_i = -E_i z_prev
+                    load_block(M, P.E + (int64_t)(q0 + i) * bs, W, st.ld);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)-1);
+                    rowmajor_store(out(i), Y);
+                    __syncthreads();
+                    block_copy(X, Y, W * W);
+                }
+                // twist: x_t = -E_t z_{t-1} (from above) or -F_t z_{t+1} (from below)
+                load_block(M, (dir > 0 ? P.E : P.F) + (int64_t)(q0 + tq) * bs, W, st.ld);
+                __syncthreads();
+                block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)-1);
+                block_copy(X, Y, W * W);
+            }
+            rowmajor_store(out(tq), X);
+            __syncthreads();
+            for (int sd = 0; sd < 2; ++sd) {   // outward: x_i = z_i - F_i x_inner
+                const int dir = sd == 0 ? -1 : 1;
+                rowmajor_load(X, out(tq));
+                __syncthreads();
+                for (int i = tq + dir; i >= 0 && i < n; i += dir) {
+                    load_block(M, P.F + (int64_t)(q0 + i) * bs, W, st.ld);
+                    const bool has_z = top ? (dir < 0 && i >= rs) : (dir > 0 && i <= rs);
+                    if (has_z) rowmajor_load(Y, out(i));
+                    else for (int e = threadIdx.x; e < W * W; e += blockDim.x) Y[e] = CT<C>::zero();
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, M, nullptr, X, W, true, (R)-1);
+                    rowmajor_store(out(i), Y);
+                    __syncthreads();
+                    block_copy(X, Y, W * W);
+                }
+            }
         }
-        store_block(Rs + (int64_t)q * bs, M, W, st.ld);
-        __syncthreads();
-        return true;
-    };
-    // out = Rinv_q D  -> global slot
-    auto store_prod = [&](C* slot, const C* D) {
-        block_gemm_dscale<C>(Y, M, nullptr, D, W, false, (R)1);
-        store_block(slot, Y, W, st.ld);
-        __syncthreads();
-    };
-    auto zero_slot = [&](C* slot) {
-        for (int e = threadIdx.x; e < W * st.ld; e += blockDim.x) slot[e] = CT<C>::zero();
-        __syncthreads();
-    };
-    auto inner = [&](int q) -> const C* { return Fs + (int64_t)q * bs; };   // stored F of a neighbour
-    // T -= D * F_nb with D built in X and F_nb read into Y
-    auto sub_coupled = [&](const C* Fnb) {
-        load_block(Y, Fnb, W, st.ld);
-        __syncthreads();
-        block_gemm_dscale<C>(M, X, nullptr, Y, W, true, (R)-1);
-    };
-    // ---- top-down q = 0 .. tq-1
-    for (int q = 0; q < tq; ++q) {
-        build_T(q);
-        if (q >= 1) { build_L(q, X); sub_coupled(inner(q - 1)); }
-        if (!invert_store(q)) return;
-        if (q >= 1) { build_L(q, X); store_prod(Es + (int64_t)q * bs, X); }
-        else zero_slot(Es + (int64_t)q * bs);
-        build_U(q, X);
-        store_prod(Fs + (int64_t)q * bs, X);
     }
-    // ---- bottom-up q = Q-1 .. tq+1
-    for (int q = Q - 1; q > tq; --q) {
-        build_T(q);
-        if (q <= Q - 2) { build_U(q, X); sub_coupled(inner(q + 1)); }
-        if (!invert_store(q)) return;
-        if (q <= Q - 2) { build_U(q, X); store_prod(Es + (int64_t)q * bs, X); }
-        else zero_slot(Es + (int64_t)q * bs);
-        build_L(q, X);
-        store_prod(Fs + (int64_t)q * bs, X);
-    }
-    // ---- twist q = tq (its F slot is written last: the neighbours' F are read first)
-    if (Q >= 1) {
-        const int q = tq;
-        build_T(q);
-        if (q >= 1) { build_L(q, X); sub_coupled(inner(q - 1)); }
-        if (q <= Q - 2) { build_U(q, X); sub_coupled(inner(q + 1)); }
-        if (!invert_store(q)) return;
-        if (q >= 1) { build_L(q, X); store_prod(Es + (int64_t)q * bs, X); }
-        else zero_slot(Es + (int64_t)q * bs);
-        if (q <= Q - 2) { build_U(q, X); store_prod(Fs + (int64_t)q * bs, X); }
-        else zero_slot(Fs + (int64_t)q * bs);
+
+    // ---- level-2 system over r = 0..G-2 (separator sigma_r = gq1[r])
+    auto sig = [&](int r) { return g.gq1[r]; };
+    auto bT2 = [&](int r) {   // T_s - L_s GB2_r(last) - U_s GT2_{r+1}(first)
+        const int q = sig(r);
+        build_T1(q);
+        build_L1(q, Z);
+        rowmajor_load(Y, P.GB2 + (int64_t)(q - 1) * bs);
+        __syncthreads();
+        block_gemm_dscale<C>(M, Z, nullptr, Y, W, true, (R)-1);
+        build_U1(q, Z);
+        rowmajor_load(Y, P.GT2 + (int64_t)g.gq0[r + 1] * bs);
+        __syncthreads();
+        block_gemm_dscale<C>(M, Z, nullptr, Y, W, true, (R)-1);
+    };
+    auto bL2 = [&](int r, C* D) {   // -L_s GT2_r(last)
+        const int q = sig(r);
+        build_L1(q, Z);
+        rowmajor_load(Y, P.GT2 + (int64_t)(q - 1) * bs);
+        __syncthreads();
+        block_gemm_dscale<C>(D, Z, nullptr, Y, W, false, (R)-1);
+    };
+    auto bU2 = [&](int r, C* D) {   // -U_s GB2_{r+1}(first)
+        const int q = sig(r);
+        build_U1(q, Z);
+        rowmajor_load(Y, P.GB2 + (int64_t)g.gq0[r + 1] * bs);
+        __syncthreads();
+        block_gemm_dscale<C>(D, Z, nullptr, Y, W, false, (R)-1);
+    };
+    if (!twisted_lu<C>(st, G - 1, sig, bT2, bL2, bU2, P.Rinv, P.E, P.F, M, X, Y, piv, colk, red, status)) return;
+    // level-2 right-hand-side products: P2L_r = Rinv2_r L_s, P2U_r = Rinv2_r U_s
+    for (int r = 0; r < G - 1; ++r) {
+        const int q = sig(r);
+        load_block(M, P.Rinv + (int64_t)q * bs, W, st.ld);
+        build_L1(q, X);
+        block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)1);
+        store_block(P.P2L + (int64_t)q * bs, Y, W, st.ld);
+        build_U1(q, X);
+        __syncthreads();
+        block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)1);
+        store_block(P.P2U + (int64_t)q * bs, Y, W, st.ld);
+        __syncthreads();
     }
 }
 
-size_t factor_smem_bytes(int Wmax, size_t esize) {
-    return (size_t)3 * Wmax * Wmax * esize + (size_t)3 * Wmax * esize + (size_t)((Wmax + 3) & ~3) * 4 + 16;
+size_t factor_smem_bytes(int Wmax, size_t esize, int nbuf) {
+    return (size_t)nbuf * Wmax * Wmax * esize + (size_t)3 * Wmax * esize + (size_t)((Wmax + 3) & ~3) * 4 + 16;
 }
 
 template <typename C>
-cudaError_t launch_factor(const Geom& g, int Wmax, void* Sinv, void* GT, void* GB, void* Rinv, void* E,
-                          void* F, int* status, cudaStream_t s, KernelTimer* tm) {
-    const size_t smem = factor_smem_bytes(Wmax, sizeof(C));
+cudaError_t launch_factor(const Geom& g, int Wmax, void* const* pool, int* status, cudaStream_t s, KernelTimer* tm) {
+    const size_t smem = factor_smem_bytes(Wmax, sizeof(C), 3);
+    const size_t smem_sep = factor_smem_bytes(Wmax, sizeof(C), g.G > 1 ? 4 : 3);
+    if (smem_sep > kFactorSmemMax) return cudaErrorInvalidConfiguration;
     cudaError_t err = cudaFuncSetAttribute(k_factor_chunk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_factor_reduced<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_factor_sep<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sep);
     if (err != cudaSuccess) return err;
     dim3 grid(g.P, g.J);
     {
         TimedLaunch t(tm, "factor_chunk", s);
-        k_factor_chunk<C><<<grid, 256, smem, s>>>(g, (C*)Sinv, (C*)GT, (C*)GB, status);
+        k_factor_chunk<C><<<grid, 256, smem, s>>>(g, (C*)pool[0], (C*)pool[1], (C*)pool[2], status);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (g.P > 1) {
-        TimedLaunch t(tm, "factor_reduced", s);
-        k_factor_reduced<C><<<g.J, 256, smem, s>>>(g, (const C*)GT, (const C*)GB, (C*)Rinv, (C*)E, (C*)F,
-                                                    status);
+        SepPools<C> pl{(C*)pool[3], (C*)pool[4], (C*)pool[5], (C*)pool[6], (C*)pool[7], (C*)pool[8], (C*)pool[9]};
+        TimedLaunch t(tm, "factor_sep", s);
+        k_factor_sep<C><<<g.J, 256, smem_sep, s>>>(g, (const C*)pool[1], (const C*)pool[2], pl, status);
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_factor<float2>(const Geom&, int, void*, void*, void*, void*, void*, void*, int*,
-                                           cudaStream_t, KernelTimer*);
-template cudaError_t launch_factor<double2>(const Geom&, int, void*, void*, void*, void*, void*, void*, int*,
-                                            cudaStream_t, KernelTimer*);
+template cudaError_t launch_factor<float2>(const Geom&, int, void* const*, int*, cudaStream_t, KernelTimer*);
+template cudaError_t launch_factor<double2>(const Geom&, int, void* const*, int*, cudaStream_t, KernelTimer*);
 
 }  // namespace helm

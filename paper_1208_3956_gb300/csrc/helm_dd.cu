@@ -58,14 +58,15 @@ struct helm_dd {
     int64_t n[3] = {1, 1, 1};
     int64_t N[3] = {1, 1, 1};
     double h = 1.0, omega = 1.0, c_ref = 0.0;
-    int w_outer = 0, w_sub = 0, J = 1, P_req = 0;
+    int w_outer = 0, w_sub = 0, J = 1, P_req = 0, G_req = 0;
     helm_prec prec = HELM_PREC_FP64;
     std::vector<double> c;
     // geometry
     std::vector<int> beta;
     std::vector<StripDev> strips;
-    int P = 1, Wmax = 0;
+    int P = 1, G = 1, Wmax = 0;
     std::vector<int> r0, r1, rowmap;
+    std::vector<int> gq0, gq1, sepmap;   // separator groups (second level of nested dissection)
     std::vector<cd> gx_int, gx_half, gy_int, gy_half, gz_int, gz_half;
     // device
     cudaStream_t stream = nullptr, own_stream = nullptr;
@@ -74,11 +75,13 @@ struct helm_dd {
     double* d_k2 = nullptr;
     double2* d_tab = nullptr;       // global axis tables + per-strip x tables
     void* d_ct = nullptr;           // working-precision sweep tables
-    int* d_counters = nullptr;      // per-tile arrival counters of the sweep
+    int* d_counters = nullptr;      // per-tile arrival counters of the sweep ([kMaxTiles][G+1])
+    size_t counter_bytes = 0;
     int zrows = 1;
     StripDev* d_strips = nullptr;
-    int* d_ints = nullptr;          // r0 | r1 | rowmap
-    void* d_pool[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Sinv GT GB Rinv E F
+    int* d_ints = nullptr;          // r0 | r1 | rowmap | gq0 | gq1 | sepmap
+    // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator)
+    void* d_pool[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int* d_status = nullptr;
     size_t esize = 16;
     bool factored = false;
@@ -198,9 +201,9 @@ cd strip_alpha_at(const helm_dd* h, const StripDev& s, int x2) {
 
 void chunk_layout(helm_dd* h) {
     const int Ny = (int)h->N[1];
-    // built-in: about sqrt(Ny) chunks balances the chunk chains (~Ny/P steps) against the
-    // separator chain (~P steps)
-    int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(sqrt((double)Ny)));
+    // built-in: a strip solve takes about Ny/P (chunk) + P/G (separator group) + G
+    // (level-2 system) dependent steps; G ~ sqrt(P) and P ~ Ny^(2/3) balance them
+    int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(pow((double)Ny, 2.0 / 3.0)));
     P = std::min(P, (Ny + 1) / 2);
     h->P = std::max(P, 1);
     const int rows = Ny - (h->P - 1);
@@ -216,7 +219,32 @@ void chunk_layout(helm_dd* h) {
         k = h->r1[p];
         if (p < h->P - 1) { h->rowmap[k] = -(p + 1); k += 1; }
     }
+    // Separator groups: the Q = P-1 separators are cut by G-1 level-2 separators
+    // into G groups of consecutive separators.  The solve of the separator system
+    // then takes about Q/G + G dependent steps instead of Q; G ~ sqrt(Q) balances
+    // the two.  Every group keeps at least one separator.
+    const int Q = h->P - 1;
+    int G = h->G_req > 0 ? h->G_req : (Q >= 6 ? (int)lround(sqrt((double)Q)) : 1);
+    G = std::max(1, std::min(G, (Q + 1) / 2));
+    // the level-2 factorisation needs a fourth W x W buffer in shared memory
+    if (factor_smem_bytes(h->Wmax, h->esize, 4) > kFactorSmemMax) G = 1;
+    h->G = G;
+    const int nsep = Q - (G - 1);
+    const int gbase = G > 0 ? nsep / G : 0, grem = G > 0 ? nsep % G : 0;
+    h->gq0.assign(G, 0);
+    h->gq1.assign(G, 0);
+    h->sepmap.assign(std::max(Q, 1), 0);
+    int q = 0;
+    for (int gi = 0; gi < G; ++gi) {
+        h->gq0[gi] = q;
+        h->gq1[gi] = q + gbase + (gi < grem ? 1 : 0);
+        for (int i = h->gq0[gi]; i < h->gq1[gi]; ++i) h->sepmap[i] = gi;
+        q = h->gq1[gi];
+        if (gi < G - 1) { h->sepmap[q] = -(gi + 1); q += 1; }
+    }
 }
+
+size_t counter_bytes(const helm_dd* h) { return (size_t)kMaxTiles * (h->G + 1) * sizeof(int); }
 
 double2 to_d2h(cd v) { return make_double2(v.real(), v.imag()); }
 
@@ -230,8 +258,6 @@ helm_status ensure_device(helm_dd* h) {
     CK(h, cudaMalloc(&h->d_c, nint * sizeof(double)));
     CK(h, cudaMalloc(&h->d_k2, nvol(h) * sizeof(double)));
     CK(h, cudaMalloc(&h->d_status, sizeof(int)));
-    CK(h, cudaMalloc(&h->d_counters, kMaxTiles * sizeof(int)));
-    CK(h, cudaMemsetAsync(h->d_counters, 0, kMaxTiles * sizeof(int), h->stream));
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     CK(h, cudaMemcpyAsync(h->d_c, h->c.data(), nint * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_k2(h->d_c, h->d_k2, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->omega,
@@ -292,7 +318,7 @@ helm_status prepare_geom(helm_dd* h) {
     h->d_tab = nullptr; h->d_strips = nullptr; h->d_ints = nullptr;
     CK(h, cudaMalloc(&h->d_tab, tab2.size() * sizeof(double2)));
     CK(h, cudaMalloc(&h->d_strips, h->strips.size() * sizeof(StripDev)));
-    CK(h, cudaMalloc(&h->d_ints, (2 * h->P + Ny) * sizeof(int)));
+    CK(h, cudaMalloc(&h->d_ints, (2 * h->P + Ny + 2 * h->G + h->sepmap.size()) * sizeof(int)));
     CK(h, cudaMemcpyAsync(h->d_tab, tab2.data(), tab2.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
                           cudaMemcpyHostToDevice, h->stream));
@@ -300,6 +326,9 @@ helm_status prepare_geom(helm_dd* h) {
     ints.insert(ints.end(), h->r0.begin(), h->r0.end());
     ints.insert(ints.end(), h->r1.begin(), h->r1.end());
     ints.insert(ints.end(), h->rowmap.begin(), h->rowmap.end());
+    ints.insert(ints.end(), h->gq0.begin(), h->gq0.end());
+    ints.insert(ints.end(), h->gq1.begin(), h->gq1.end());
+    ints.insert(ints.end(), h->sepmap.begin(), h->sepmap.end());
     CK(h, cudaMemcpyAsync(h->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     Geom& g = h->geom;
     g.dim = h->dim;
@@ -324,11 +353,26 @@ helm_status prepare_geom(helm_dd* h) {
     g.r0 = h->d_ints;
     g.r1 = h->d_ints + h->P;
     g.rowmap = h->d_ints + 2 * h->P;
+    g.G = h->G;
+    g.gq0 = g.rowmap + Ny;
+    g.gq1 = g.gq0 + h->G;
+    g.sepmap = g.gq1 + h->G;
+    if (h->counter_bytes != counter_bytes(h)) {
+        if (h->d_counters) cudaFree(h->d_counters);
+        h->d_counters = nullptr;
+        h->counter_bytes = 0;
+        CK(h, cudaMalloc(&h->d_counters, counter_bytes(h)));
+        h->counter_bytes = counter_bytes(h);
+    }
+    CK(h, cudaMemsetAsync(h->d_counters, 0, h->counter_bytes, h->stream));
     g.ct = h->d_ct;
     g.ct_sy = 0;
     g.ct_cy = Ny;
-    h->zrows = h->P - 1;
+    // rows of the sweep's z buffer: the longest chain one CTA runs (a chunk, a
+    // separator group, or the level-2 system)
+    h->zrows = std::max(h->G - 1, 1);
     for (int p = 0; p < h->P; ++p) h->zrows = std::max(h->zrows, h->r1[p] - h->r0[p]);
+    for (int gi = 0; gi < h->G; ++gi) h->zrows = std::max(h->zrows, h->gq1[gi] - h->gq0[gi]);
     CK(h, cudaStreamSynchronize(h->stream));
     h->prepared = true;
     return HELM_OK;
@@ -399,6 +443,16 @@ helm_status helm_dd_set_chunks(helm_dd* h, int P) {
     return HELM_OK;
 }
 
+helm_status helm_dd_set_sep_groups(helm_dd* h, int G) {
+    if (!h || G < 0) return HELM_EINVAL;
+    if (h->factored) return fail(h, HELM_ESTATE, "set_sep_groups after factor");
+    h->G_req = G;
+    h->prepared = false;
+    return HELM_OK;
+}
+
+int helm_dd_sep_groups(const helm_dd* h) { return h && h->prepared ? h->G : 0; }
+
 helm_status helm_dd_set_stream(helm_dd* h, void* stream) {
     if (!h) return HELM_EINVAL;
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;   // null until first device use
@@ -452,17 +506,17 @@ helm_status helm_dd_factor(helm_dd* h) {
     CK(h, cudaMalloc(&h->d_pool[3], redb));
     CK(h, cudaMalloc(&h->d_pool[4], redb));
     CK(h, cudaMalloc(&h->d_pool[5], redb));
+    if (h->G > 1)
+        for (int i = 6; i < 10; ++i) CK(h, cudaMalloc(&h->d_pool[i], redb));
     CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
                           cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     Geom& g = h->geom;
     cudaError_t e;
     if (h->prec == HELM_PREC_MIXED)
-        e = launch_factor<float2>(g, h->Wmax, h->d_pool[0], h->d_pool[1], h->d_pool[2], h->d_pool[3],
-                                  h->d_pool[4], h->d_pool[5], h->d_status, h->stream, &h->timer);
+        e = launch_factor<float2>(g, h->Wmax, h->d_pool, h->d_status, h->stream, &h->timer);
     else
-        e = launch_factor<double2>(g, h->Wmax, h->d_pool[0], h->d_pool[1], h->d_pool[2], h->d_pool[3],
-                                   h->d_pool[4], h->d_pool[5], h->d_status, h->stream, &h->timer);
+        e = launch_factor<double2>(g, h->Wmax, h->d_pool, h->d_status, h->stream, &h->timer);
     if (e != cudaSuccess) return fail_cuda(h, "factor kernels", e);
     int st = 0;
     CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -489,7 +543,7 @@ helm_status check_device_status(helm_dd* h) {
     CK(h, cudaStreamSynchronize(h->stream));
     if (st == 7) {
         cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
-        cudaMemsetAsync(h->d_counters, 0, kMaxTiles * sizeof(int), h->stream);
+        cudaMemsetAsync(h->d_counters, 0, h->counter_bytes, h->stream);
         return fail(h, HELM_ETIMEOUT, "a bounded device wait in the sweep gave up");
     }
     return HELM_OK;
@@ -502,8 +556,8 @@ struct PrecondBufs {
     double2* T0;     // [B][Ny] transfer differences (two, swapped per strip)
     double2* T1;
     void* Y;         // [B][Ny][Wmax] strip solutions, working precision
-    void* parts;     // [B][P-1][2][Wmax] separator right-hand-side parts
-    int* counters;   // [kMaxTiles] arrival counters, zero on entry
+    void* parts;     // [B][P-1][4][Wmax] separator right-hand-side parts
+    int* counters;   // [kMaxTiles][G+1] arrival counters, zero on entry
 };
 
 // Bytes of each PrecondBufs member for B right-hand sides.
@@ -515,7 +569,7 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[6]) {
     sz[2] = (size_t)B * Ny * sizeof(double2);
     sz[3] = sz[2];
     sz[4] = (size_t)B * Ny * h->Wmax * h->esize;
-    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 2 * h->Wmax * h->esize;
+    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 4 * h->Wmax * h->esize;
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
@@ -551,12 +605,8 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     const double ih2 = 1.0 / (h->h * h->h);
     auto strip_solve = [&](int j, const SweepStep& sp) -> cudaError_t {
         if (h->prec == HELM_PREC_MIXED)
-            return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool[0], h->d_pool[1],
-                                              h->d_pool[2], h->d_pool[3], h->d_pool[4], h->d_pool[5],
-                                              h->stream, &h->timer);
-        return launch_strip_solve<double2>(h->geom, j, h->strips[j], sp, wk, h->d_pool[0], h->d_pool[1],
-                                           h->d_pool[2], h->d_pool[3], h->d_pool[4], h->d_pool[5], h->stream,
-                                           &h->timer);
+            return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
+        return launch_strip_solve<double2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
     };
     // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1)
     for (int j = 0; j < J; ++j) {
@@ -1066,7 +1116,7 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
     size_t total = 0;
     for (int i = 0; i < 6; ++i) { off[i] = total; total += align256(sz[i]); }
     off[6] = total;
-    total += align256((size_t)kMaxTiles * sizeof(int));
+    total += align256(h->counter_bytes);
     if (total > kNoAllocScratchBytes)
         return fail(h, HELM_EINVAL, "apply_precond_noalloc needs " + std::to_string(total) +
                                         " bytes of scratch; the static limit is " +
@@ -1077,7 +1127,7 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
     PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), (double2*)(b + off[2]), (double2*)(b + off[3]),
                    b + off[4], b + off[5], (int*)(b + off[6])};
     // the array keeps whatever the previous call left: the arrival counters must start at zero
-    CK(h, cudaMemsetAsync(bf.counters, 0, (size_t)kMaxTiles * sizeof(int), h->stream));
+    CK(h, cudaMemsetAsync(bf.counters, 0, h->counter_bytes, h->stream));
     helm_status s = run_precond(h, (const double2*)in, (double2*)out, nrhs, bf);
     if (s != HELM_OK) return s;
     return check_device_status(h);

@@ -79,10 +79,13 @@ struct TimedLaunch {
 };
 
 // ---- factor.cu
-size_t factor_smem_bytes(int Wmax, size_t esize);
+// shared memory of a factor kernel with nbuf W x W buffers (3, or 4 for the
+// level-2 separator system)
+constexpr size_t kFactorSmemMax = 227 * 1024;
+size_t factor_smem_bytes(int Wmax, size_t esize, int nbuf);
+// pool: Sinv, GT, GB (per grid row), Rinv, E, F, GT2, GB2, P2L, P2U (per separator)
 template <typename C>
-cudaError_t launch_factor(const Geom& g, int Wmax, void* Sinv, void* GT, void* GB, void* Rinv, void* E,
-                          void* F, int* status, cudaStream_t s, KernelTimer* tm);
+cudaError_t launch_factor(const Geom& g, int Wmax, void* const* pool, int* status, cudaStream_t s, KernelTimer* tm);
 
 // ---- sweep.cu: one strip solve of the sweep.
 // Right-hand side of strip st for row k, column c (padded column gc = lo-lpml+c):
@@ -105,7 +108,7 @@ struct SweepStep {
 
 struct SweepWork {
     void* ybuf;             // [B][Ny][Wmax] working precision
-    void* parts;            // [B][P-1][2][Wmax] working precision
+    void* parts;            // [B][P-1][4][Wmax] working precision
     int* counters;          // per RHS tile, zero between launches
     int* status;            // error word (7 = bounded wait timed out)
     int Wmax;
@@ -115,9 +118,7 @@ struct SweepWork {
 
 template <typename C>
 cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const SweepStep& step,
-                               const SweepWork& wk, const void* Sinv, const void* GT, const void* GB,
-                               const void* Rinv, const void* E, const void* F, cudaStream_t s,
-                               KernelTimer* tm);
+                               const SweepWork& wk, void* const* pool, cudaStream_t s, KernelTimer* tm);
 
 // ---- field.cu: FP64 grid kernels
 cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, int nz, int w, double omega,

@@ -11,8 +11,13 @@
 //     with the W x W products split over the warps (lanes own rows);
 //   * adds its two parts of the separator right-hand sides, Rinv_q times
 //     (b_s - C_s y_q(last)) and -Rinv_q C_{s+1} y_{q+1}(first);
-//   * the last CTA of a tile to finish (atomic arrival counter, no waiting)
-//     solves the separator system z_q = a_q - E_q z_{q-1}, x_q = z_q - F_q x_{q+1}.
+//   * the last chunk CTA of a separator group to finish (atomic arrival
+//     counter per group, no waiting) solves the group's separators with the
+//     level-2 separators held at zero (twisted chain z_i = a_i - E_i z_outer,
+//     x_i = z_i - F_i x_inner) and adds the group's parts of the level-2
+//     right-hand sides; the last group to finish solves the level-2 system.
+// k_sweep_sepfix (grid: separators x RHS tiles; only with more than one group)
+//   x_q = y_q - GT2_q x2_above - GB2_q x2_below for the grouped separators.
 // k_sweep_correct (grid: rows x RHS tiles)
 //   x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output columns only, scatter
 //   to the output field (compose) and emit the transfer difference.
@@ -28,6 +33,11 @@ namespace helm {
 
 static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
+static constexpr int kParts = 4;   // separator right-hand-side parts: 2 from chunks, 2 from groups
+
+// load-order table entries: factor pool << 24 | block index in that pool
+enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kP2L = 4, kP2U = 5 };
+__host__ __device__ constexpr int enc(int pool, int idx) { return (pool << 24) | idx; }
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -81,9 +91,11 @@ struct SweepArgs {
     const void* Rinv;
     const void* E;
     const void* F;
+    const void* P2L;         // level-2 products Rinv2 L, Rinv2 U (null with one group)
+    const void* P2U;
     void* ybuf;              // [B][Ny][Wmax] chunk solutions, then separator values
-    void* parts;             // [B][P-1][2][Wmax] separator right-hand-side parts
-    int* counters;           // [ntile] arrival counters, left at zero
+    void* parts;             // [B][P-1][kParts][Wmax] separator right-hand-side parts
+    int* counters;           // [ntile][G+1] arrival counters, left at zero
     int* status;
 };
 
@@ -257,9 +269,11 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     const C* Rinv = reinterpret_cast<const C*>(A.Rinv) + A.st.red;
     const C* Eb = reinterpret_cast<const C*>(A.E) + A.st.red;
     const C* Fb = reinterpret_cast<const C*>(A.F) + A.st.red;
+    const C* P2Lb = A.P2L ? reinterpret_cast<const C*>(A.P2L) + A.st.red : nullptr;
+    const C* P2Ub = A.P2U ? reinterpret_cast<const C*>(A.P2U) + A.st.red : nullptr;
     const bool resident = ring >= m + 2;
     const bool has_below = p < P - 1, has_above = p > 0;
-    // ---- load order of the chunk phase (rows of Sinv; -1 / -2: Rinv below / above)
+    // ---- load order of the chunk phase (rows of Sinv, then Rinv below / above)
     //   forward: s = 0..nmx-1: down row r0+s, up row r1-1-s; then the twist row
     //   back (streaming only): s = 0..nmx-1: down row t-1-s, up row t+1+s
     const int nload = m + (resident ? 0 : m - 1) + (has_below ? 1 : 0) + (has_above ? 1 : 0);
@@ -272,12 +286,16 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     int seqbase = 0;                        // first load number of the current sequence
     bool sep_phase = false;
     auto src_of = [&](int G) -> const C* {
-        const int r = order[G - seqbase];
-        if (!sep_phase) {
-            if (r >= 0) return Sinv + (int64_t)r * bs;
-            return Rinv + (int64_t)(r == -1 ? p : p - 1) * bs;
+        const int e = order[G - seqbase];
+        const int64_t o = (int64_t)(e & 0xffffff) * bs;
+        switch (e >> 24) {
+            case kSinv: return Sinv + o;
+            case kRinv: return Rinv + o;
+            case kEo: return Eb + o;
+            case kFi: return Fb + o;
+            case kP2L: return P2Lb + o;
+            default: return P2Ub + o;
         }
-        return r >= 0 ? Eb + (int64_t)r * bs : Fb + (int64_t)(-r - 1) * bs;
     };
     auto issue_into = [&](int slot, const C* src) {   // producer only
         uint64_t* mb = &mbar[slot];
@@ -312,17 +330,17 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     if (producer) {
         int G = 0;
         for (int s = 0; s < nmx; ++s) {
-            if (s < nd) order[G++] = r0 + s;
-            if (s < nu) order[G++] = r1 - 1 - s;
+            if (s < nd) order[G++] = enc(kSinv, r0 + s);
+            if (s < nu) order[G++] = enc(kSinv, r1 - 1 - s);
         }
-        order[G++] = t;
+        order[G++] = enc(kSinv, t);
         if (!resident)
             for (int s = 0; s < nmx; ++s) {
-                if (s < nd) order[G++] = t - 1 - s;
-                if (s < nu) order[G++] = t + 1 + s;
+                if (s < nd) order[G++] = enc(kSinv, t - 1 - s);
+                if (s < nu) order[G++] = enc(kSinv, t + 1 + s);
             }
-        if (has_below) order[G++] = -1;
-        if (has_above) order[G++] = -2;
+        if (has_below) order[G++] = enc(kRinv, p);
+        if (has_above) order[G++] = enc(kRinv, p - 1);
         flags[1] = 0;
         for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
@@ -505,60 +523,31 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
-                if (has_below) parts[((((int64_t)(b0 + b) * Q + p) * 2 + 0) * A.Wmax) + row] = vd[b];
-                if (has_above) parts[((((int64_t)(b0 + b) * Q + p - 1) * 2 + 1) * A.Wmax) + row] = vu[b];
+                if (has_below) parts[((((int64_t)(b0 + b) * Q + p) * kParts + 0) * A.Wmax) + row] = vd[b];
+                if (has_above) parts[((((int64_t)(b0 + b) * Q + p - 1) * kParts + 1) * A.Wmax) + row] = vu[b];
             }
         if (!finish()) return;
     }
     if (Q == 0) return;
-    // ---- arrival: the last CTA of this tile solves the separator system
+    // ---- arrival: the last chunk CTA of group gi (chunks gq0..gq1) solves its separators
+    const int NG = A.g.G;
+    int* cnt = A.counters + (int64_t)tile * (NG + 1);
+    const int gi = p == Q ? NG - 1 : (A.g.sepmap[p] >= 0 ? A.g.sepmap[p] : -A.g.sepmap[p] - 1);
+    const int q0 = A.g.gq0[gi], q1 = A.g.gq1[gi], n1 = q1 - q0;
     __threadfence();
     __syncthreads();
-    if (tid == 0) flags[0] = (atomicAdd(&A.counters[tile], 1) == P - 1) ? 1 : 0;
+    if (tid == 0) {
+        const bool last = atomicAdd(&cnt[gi], 1) == n1;
+        if (last) cnt[gi] = 0;
+        flags[0] = last ? 1 : 0;
+    }
     __syncthreads();
     if (!flags[0]) return;
     __threadfence();
-    const C* parts = reinterpret_cast<const C*>(A.parts);
-    const int tq = (Q - 1) / 2;
-    const int fd = imax(tq - 1, 0), fu = imax(Q - 2 - tq, 0), fmx = imax(fd, fu);   // forward steps
-    const int bd = tq, bu = Q - 1 - tq, bmx = imax(bd, bu);                         // back steps
-    // separator load order, encoded q >= 0 -> E_q, q < 0 -> F_{-q-1}; every earlier
-    // load has been consumed, so the ring continues from slot cslot
-    sep_phase = true;
-    if (producer) {
-        int nr = 0;
-        for (int s = 0; s < fmx; ++s) {
-            if (s < fd) order[nr++] = 1 + s;
-            if (s < fu) order[nr++] = Q - 2 - s;
-        }
-        if (tq >= 1) order[nr++] = tq;
-        if (tq <= Q - 2) order[nr++] = -(tq + 1);
-        for (int s = 0; s < bmx; ++s) {
-            if (s < bd) order[nr++] = -(tq - 1 - s + 1);
-            if (s < bu) order[nr++] = -(tq + 1 + s + 1);
-        }
-        seqbase = consumed;
-        nseq = seqbase + nr;
-        rf = seqbase;
-        rfslot = cslot;
-        int sl = cslot;
-        for (int i = 0; i < imin(ring, nr); ++i) {
-            issue_into(sl, src_of(seqbase + i));
-            if (++sl == ring) sl = 0;
-        }
-    }
-    // a_q = A_q + B_q
-    for (int o = tid; o < Q * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
-        const int64_t pb = (((int64_t)(b0 + b) * Q + q) * 2) * A.Wmax + c;
-        const C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
-        zb[(q * BT + b) * W + c] = v;
-        if (q == 0) vin_d[b * 64 + c] = v;
-        if (q == Q - 1) vin_u[b * 64 + c] = v;
-    }
-    __syncthreads();
-    auto zq = [&](int q) -> C* { return zb + q * BT * W; };
-    // one separator step: out_q = z_q - product, stored to z_q and to the chain's next input
+    C* parts = reinterpret_cast<C*>(A.parts);
+    auto pidx = [&](int b, int q, int k) -> int64_t { return (((int64_t)(b0 + b) * Q + q) * kParts + k) * A.Wmax; };
+    auto zq = [&](int i) -> C* { return zb + i * BT * W; };
+    // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
     auto sep = [&](auto Dc, auto Uc, int qd, int qu) -> bool {
         constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
         const C* Sd = D ? consume() : nullptr;
@@ -582,65 +571,229 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             }
         return finish();
     };
-    // forward: z_q = a_q - E_q z_outer, down q = 1..tq-1, up q = Q-2..tq+1
-    {
-        int s = 0;
-        const int nboth = imin(fd, fu);
-        for (; s < nboth; ++s)
-            if (!sep(std::true_type{}, std::true_type{}, 1 + s, Q - 2 - s)) return;
-        for (; s < fd; ++s)
-            if (!sep(std::true_type{}, std::false_type{}, 1 + s, 0)) return;
-        for (; s < fu; ++s)
-            if (!sep(std::false_type{}, std::true_type{}, 0, Q - 2 - s)) return;
+    // Twisted solve of n separators whose factors sit at slot(i) (level 1: q0 + i;
+    // level 2: gq1[i]); a_i is in zq(i), a_0 / a_{n-1} in vin_d / vin_u.  xe0 / xe1
+    // (encoded, or -1) are extra loads appended to the sequence.  Every earlier
+    // load has been consumed, so the ring continues from slot cslot.
+    auto chain = [&](int n, int lvl, int xe0, int xe1) -> bool {
+        const int tq = (n - 1) / 2;
+        const int fd = imax(tq - 1, 0), fu = imax(n - 2 - tq, 0), fmx = imax(fd, fu);   // forward steps
+        const int bd = tq, bu = n - 1 - tq, bmx = imax(bd, bu);                         // back steps
+        sep_phase = true;
+        if (producer) {
+            auto slot = [&](int i) { return lvl == 1 ? q0 + i : A.g.gq1[i]; };
+            int nr = 0;
+            for (int s = 0; s < fmx; ++s) {
+                if (s < fd) order[nr++] = enc(kEo, slot(1 + s));
+                if (s < fu) order[nr++] = enc(kEo, slot(n - 2 - s));
+            }
+            if (tq >= 1) order[nr++] = enc(kEo, slot(tq));
+            if (tq <= n - 2) order[nr++] = enc(kFi, slot(tq));
+            for (int s = 0; s < bmx; ++s) {
+                if (s < bd) order[nr++] = enc(kFi, slot(tq - 1 - s));
+                if (s < bu) order[nr++] = enc(kFi, slot(tq + 1 + s));
+            }
+            if (xe0 >= 0) order[nr++] = xe0;
+            if (xe1 >= 0) order[nr++] = xe1;
+            seqbase = consumed;
+            nseq = seqbase + nr;
+            rf = seqbase;
+            rfslot = cslot;
+            int sl = cslot;
+            for (int i = 0; i < imin(ring, nr); ++i) {
+                issue_into(sl, src_of(seqbase + i));
+                if (++sl == ring) sl = 0;
+            }
+        }
+        // forward: z_i = a_i - E_i z_outer, down i = 1..tq-1, up i = n-2..tq+1
+        {
+            int s = 0;
+            const int nboth = imin(fd, fu);
+            for (; s < nboth; ++s)
+                if (!sep(std::true_type{}, std::true_type{}, 1 + s, n - 2 - s)) return false;
+            for (; s < fd; ++s)
+                if (!sep(std::true_type{}, std::false_type{}, 1 + s, 0)) return false;
+            for (; s < fu; ++s)
+                if (!sep(std::false_type{}, std::true_type{}, 0, n - 2 - s)) return false;
+        }
+        // twist: x_tq = a_tq - E_tq z_{tq-1} - F_tq z_{tq+1}
+        for (int o = tid; o < nb * W; o += blockDim.x) {
+            const int c = o % W, b = o / W;
+            if (tq >= 1) vin_d[b * 64 + c] = zq(tq - 1)[b * W + c];
+            if (tq <= n - 2) vin_u[b * 64 + c] = zq(tq + 1)[b * W + c];
+        }
+        __syncthreads();
+        {
+            const bool he = tq >= 1, hf = tq <= n - 2;
+            const C* Se = he ? consume() : nullptr;
+            const C* Sf = hf ? consume() : nullptr;
+            if (compute)
+                dual_dispatch<C, NJ, BT>(he, hf, Se + lofs, vin_d + vofs, Sf + lofs, vin_u + vofs, nb, vd, vu);
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+                if (b < nb && rowok && (b & 3) == g) {
+                    C* zp = zq(tq) + b * W + row;
+                    C x = *zp;
+                    if (he) x = csub(x, vd[b]);
+                    if (hf) x = csub(x, vu[b]);
+                    *zp = x;
+                    vout_d[b * 64 + row] = x;
+                    vout_u[b * 64 + row] = x;
+                }
+            if (!finish()) return false;
+        }
+        // back: x_i = z_i - F_i x_inner, down i = tq-1..0, up i = tq+1..n-1
+        {
+            int s = 0;
+            const int nboth = imin(bd, bu);
+            for (; s < nboth; ++s)
+                if (!sep(std::true_type{}, std::true_type{}, tq - 1 - s, tq + 1 + s)) return false;
+            for (; s < bd; ++s)
+                if (!sep(std::true_type{}, std::false_type{}, tq - 1 - s, 0)) return false;
+            for (; s < bu; ++s)
+                if (!sep(std::false_type{}, std::true_type{}, 0, tq + 1 + s)) return false;
+        }
+        return true;
+    };
+    // ---- level 1: a_q = A_q + B_q for the group's separators q0 .. q1-1
+    const bool up2 = gi > 0, dn2 = gi < NG - 1;   // level-2 separators above / below the group
+    for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+        const int64_t pb = pidx(b, q0 + i, 0) + c;
+        const C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
+        zb[(i * BT + b) * W + c] = v;
+        if (i == 0) vin_d[b * 64 + c] = v;
+        if (i == n1 - 1) vin_u[b * 64 + c] = v;
     }
-    // twist: x_tq = a_tq - E_tq z_{tq-1} - F_tq z_{tq+1}
+    __syncthreads();
+    if (!chain(n1, 1, dn2 ? enc(kP2L, q1) : -1, up2 ? enc(kP2U, q0 - 1) : -1)) return;
+    for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+        yrow<C>(A, b0 + b, A.g.r1[q0 + i])[c] = zb[(i * BT + b) * W + c];
+    }
+    if (NG == 1) return;
+    // ---- the group's parts of the level-2 right-hand sides:
+    //   -P2L_{gi} y(last) to the separator below, -P2U_{gi-1} y(first) to the one above
     for (int o = tid; o < nb * W; o += blockDim.x) {
         const int c = o % W, b = o / W;
-        if (tq >= 1) vin_d[b * 64 + c] = zq(tq - 1)[b * W + c];
-        if (tq <= Q - 2) vin_u[b * 64 + c] = zq(tq + 1)[b * W + c];
+        if (dn2) vin_d[b * 64 + c] = zq(n1 - 1)[b * W + c];
+        if (up2) vin_u[b * 64 + c] = zq(0)[b * W + c];
     }
     __syncthreads();
     {
-        const bool he = tq >= 1, hf = tq <= Q - 2;
-        const C* Se = he ? consume() : nullptr;
-        const C* Sf = hf ? consume() : nullptr;
-        if (compute) dual_dispatch<C, NJ, BT>(he, hf, Se + lofs, vin_d + vofs, Sf + lofs, vin_u + vofs, nb, vd, vu);
+        const C* SL = dn2 ? consume() : nullptr;
+        const C* SU = up2 ? consume() : nullptr;
+        if (compute) dual_dispatch<C, NJ, BT>(dn2, up2, SL + lofs, vin_d + vofs, SU + lofs, vin_u + vofs, nb, vd, vu);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
-                C* zp = zq(tq) + b * W + row;
-                C x = *zp;
-                if (he) x = csub(x, vd[b]);
-                if (hf) x = csub(x, vu[b]);
-                *zp = x;
-                vout_d[b * 64 + row] = x;
-                vout_u[b * 64 + row] = x;
+                if (dn2) parts[pidx(b, q1, 2) + row] = cneg(vd[b]);
+                if (up2) parts[pidx(b, q0 - 1, 3) + row] = cneg(vu[b]);
             }
         if (!finish()) return;
     }
-    // back: x_q = z_q - F_q x_inner, down q = tq-1..0, up q = tq+1..Q-1
-    {
-        int s = 0;
-        const int nboth = imin(bd, bu);
-        for (; s < nboth; ++s)
-            if (!sep(std::true_type{}, std::true_type{}, tq - 1 - s, tq + 1 + s)) return;
-        for (; s < bd; ++s)
-            if (!sep(std::true_type{}, std::false_type{}, tq - 1 - s, 0)) return;
-        for (; s < bu; ++s)
-            if (!sep(std::false_type{}, std::true_type{}, 0, tq + 1 + s)) return;
+    // ---- arrival: the last group to finish solves the level-2 system
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const bool last = atomicAdd(&cnt[NG], 1) == NG - 1;
+        if (last) cnt[NG] = 0;
+        flags[0] = last ? 1 : 0;
     }
-    for (int o = tid; o < Q * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, q = o / (W * nb);
-        yrow<C>(A, b0 + b, A.g.r1[q])[c] = zb[(q * BT + b) * W + c];
+    __syncthreads();
+    if (!flags[0]) return;
+    __threadfence();
+    const int n2 = NG - 1;
+    for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+        const int64_t pb = pidx(b, A.g.gq1[i], 0) + c;
+        C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
+        v = cadd(v, cadd(__ldcg(parts + pb + 2 * A.Wmax), __ldcg(parts + pb + 3 * A.Wmax)));
+        zb[(i * BT + b) * W + c] = v;
+        if (i == 0) vin_d[b * 64 + c] = v;
+        if (i == n2 - 1) vin_u[b * 64 + c] = v;
     }
-    if (tid == 0) A.counters[tile] = 0;
+    __syncthreads();
+    if (!chain(n2, 2, -1, -1)) return;
+    for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+        yrow<C>(A, b0 + b, A.g.r1[A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
+    }
 }
 
-// ------------------------------------------------------------------ correction
-// One CTA per (row, RHS tile); 8 lanes per output column read the spike rows
-// GT_p(k)[c, :], GB_p(k)[c, :] (row-major, coalesced) against the separator
-// values, a three-level butterfly finishes the dot products, and the owning
-// lane scatters x (plus the base field) to the output.
+// ------------------------------------------------------------------ spike corrections
+// Dot products of spike rows with separator values, 8 lanes per output entry:
+// lane g of a group holds the separator entries a = g + 8 i (W <= 64, so i < 8)
+// in registers, loads its spike entries with one unrolled batch of independent
+// loads, and a three-level butterfly finishes the sum on all 8 lanes.
+template <typename C>
+__device__ __forceinline__ void lane_vec(C (&v)[8], const C* x, bool on, int g, int W) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int a = g + 8 * i;
+        v[i] = (on && a < W) ? x[a] : CT<C>::zero();
+    }
+}
+template <typename C>
+__device__ __forceinline__ C spike_dot2(const C* __restrict__ ra, const C (&xa)[8], bool ua,
+                                        const C* __restrict__ rb, const C (&xb)[8], bool ub, int g, int W) {
+    C sa[8], sb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int a = g + 8 * i;
+        sa[i] = (ua && a < W) ? ra[a] : CT<C>::zero();
+        sb[i] = (ub && a < W) ? rb[a] : CT<C>::zero();
+    }
+    C s0 = CT<C>::zero(), s1 = CT<C>::zero();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        s0 = cfma(sa[i], xa[i], s0);
+        s1 = cfma(sb[i], xb[i], s1);
+    }
+    C s = cadd(s0, s1);
+#pragma unroll
+    for (int o = 1; o <= 4; o <<= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    return s;
+}
+
+// One CTA per (separator, RHS tile): the grouped separator q of group gi gets
+// x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi} (row-major spikes); level-2
+// separators are already final.
+template <typename C>
+__global__ void __launch_bounds__(512) k_sweep_sepfix(SweepArgs A, const C* __restrict__ GT2,
+                                                      const C* __restrict__ GB2) {
+    const int q = blockIdx.x;
+    const int gi = A.g.sepmap[q];
+    if (gi < 0) return;
+    const int b0 = blockIdx.y * A.Bt;
+    const int nb = imin(A.Bt, A.B - b0);
+    const int W = A.st.W;
+    const int64_t off = A.st.red + (int64_t)q * A.st.bs;
+    const bool up = gi > 0, dn = gi < A.g.G - 1;
+    const int ra = up ? A.g.r1[A.g.gq0[gi] - 1] : 0;
+    const int rb = dn ? A.g.r1[A.g.gq1[gi]] : 0;
+    const int tid = threadIdx.x, g = tid & 7;
+    const int c = tid >> 3;                       // the block has 8 lanes per column, W <= 64
+    const bool live = c < W;
+    const int cc = imin(c, W - 1);
+    for (int b = 0; b < nb; ++b) {
+        C xa[8], xb[8];
+        lane_vec(xa, yrow<C>(A, b0 + b, ra), up, g, W);
+        lane_vec(xb, yrow<C>(A, b0 + b, rb), dn, g, W);
+        const C s = spike_dot2(GT2 + off + (int64_t)cc * W, xa, up, GB2 + off + (int64_t)cc * W, xb, dn, g, W);
+        if (live && g == 0) {
+            C* y = yrow<C>(A, b0 + b, A.g.r1[q]);
+            y[c] = csub(y[c], s);
+        }
+    }
+}
+
+// One CTA per (row, RHS tile): x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the
+// output columns and the two transfer columns; the owning lane scatters x
+// (plus the base field) to the output, and the transfer difference is emitted.
 template <typename C>
 __global__ void __launch_bounds__(256) k_sweep_correct(SweepArgs A, const C* __restrict__ GT,
                                                        const C* __restrict__ GB) {
@@ -661,33 +814,24 @@ __global__ void __launch_bounds__(256) k_sweep_correct(SweepArgs A, const C* __r
     const int ncol = nout + (x0 ? 1 : 0) + (x1 ? 1 : 0);
     const bool above = pm > 0, below = pm >= 0 && pm < A.g.P - 1;
     const int g = l & 7;
-    const int64_t rowoff = (int64_t)k * bs;
-    for (int base = w * 4; base < ncol; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
-        // column i of this 8-lane group; groups past ncol idle but join the shuffles
-        const int i = base + (l >> 3);
-        const bool live = i < ncol;
-        int c = 0;
-        if (live) {
-            if (i < nout) c = olo + i;
-            else if (i == nout && x0) c = A.sp.to0;
-            else c = A.sp.to1;
-        }
-        for (int b = 0; b < nb; ++b) {
-            C s = CT<C>::zero();
-            if (live && pm >= 0) {
-                const C* xa = yrow<C>(A, b0 + b, above ? A.g.r1[pm - 1] : 0);
-                const C* xb = yrow<C>(A, b0 + b, below ? A.g.r1[pm] : 0);
-                for (int a = g; a < W; a += 8) {
-                    if (above) s = cfma(GT[A.st.fac + rowoff + (int64_t)c * W + a], xa[a], s);
-                    if (below) s = cfma(GB[A.st.fac + rowoff + (int64_t)c * W + a], xb[a], s);
-                }
+    const int64_t rowoff = A.st.fac + (int64_t)k * bs;
+    for (int b = 0; b < nb; ++b) {
+        C xa[8], xb[8];
+        lane_vec(xa, yrow<C>(A, b0 + b, above ? A.g.r1[pm - 1] : 0), above, g, W);
+        lane_vec(xb, yrow<C>(A, b0 + b, below ? A.g.r1[pm] : 0), below, g, W);
+        for (int base = w * 4; base < ncol; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
+            // column i of this 8-lane group; groups past ncol idle but join the shuffles
+            const int i = base + (l >> 3);
+            const bool live = i < ncol;
+            int c = olo;
+            if (live) {
+                if (i < nout) c = olo + i;
+                else if (i == nout && x0) c = A.sp.to0;
+                else c = A.sp.to1;
             }
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, 4);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, 4);
+            const int cs = imin(imax(c, 0), W - 1);
+            const C s = spike_dot2(GT + rowoff + (int64_t)cs * W, xa, above, GB + rowoff + (int64_t)cs * W, xb,
+                                   below, g, W);
             if (live && g == 0) {
                 const C x = csub(yrow<C>(A, b0 + b, k)[c], s);
                 const int64_t rowi = (int64_t)(b0 + b) * A.g.Ny + k;
@@ -710,7 +854,7 @@ __global__ void __launch_bounds__(256) k_sweep_correct(SweepArgs A, const C* __r
 // ------------------------------------------------------------------ host
 template <typename C>
 static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& step, const SweepWork& wk,
-                           const void* Sinv, const void* Rinv, const void* E, const void* F, int Bt, int ring) {
+                           void* const* pool, int Bt, int ring) {
     SweepArgs A;
     A.g = g;
     A.st = st;
@@ -721,10 +865,12 @@ static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& s
     A.ring = ring;
     A.zrows = wk.zrows;
     A.slot_bytes = (uint32_t)(st.bs * sizeof(C));
-    A.Sinv = Sinv;
-    A.Rinv = Rinv;
-    A.E = E;
-    A.F = F;
+    A.Sinv = pool[0];
+    A.Rinv = pool[3];
+    A.E = pool[4];
+    A.F = pool[5];
+    A.P2L = g.G > 1 ? pool[8] : nullptr;
+    A.P2U = g.G > 1 ? pool[9] : nullptr;
     A.ybuf = wk.ybuf;
     A.parts = wk.parts;
     A.counters = wk.counters;
@@ -748,9 +894,7 @@ static bool plan(const StripDev& st, int zrows, int B, int& Bt, int& ring, size_
 
 template <typename C>
 cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const SweepStep& step,
-                               const SweepWork& wk, const void* Sinv, const void* GT, const void* GB,
-                               const void* Rinv, const void* E, const void* F, cudaStream_t s,
-                               KernelTimer* tm) {
+                               const SweepWork& wk, void* const* pool, cudaStream_t s, KernelTimer* tm) {
     int Bt, ring;
     size_t smem;
     if (!plan<C>(st, wk.zrows, wk.B, Bt, ring, smem)) return cudaErrorInvalidConfiguration;
@@ -765,7 +909,7 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
         }
         attr_set = true;
     }
-    SweepArgs A = make_args<C>(g, st, step, wk, Sinv, Rinv, E, F, Bt, ring);
+    SweepArgs A = make_args<C>(g, st, step, wk, pool, Bt, ring);
     const int ntile = (wk.B + Bt - 1) / Bt;
     {
         TimedLaunch t(tm, "sweep_chunk", s);
@@ -785,23 +929,25 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    if (g.G > 1) {
+        TimedLaunch t(tm, "sweep_sepfix", s);
+        k_sweep_sepfix<C><<<dim3(g.P - 1, ntile), 8 * ((st.W + 3) & ~3), 0, s>>>(A, (const C*)pool[6],
+                                                                                (const C*)pool[7]);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     {
         TimedLaunch t(tm, "sweep_correct", s);
         // one warp per output column (the strip's output range plus the transfer columns)
         const int ncol = (step.ohi - step.olo + 1) + 2;
         const int nthr = 32 * imin(8, imax(1, (ncol + 3) / 4));
-        k_sweep_correct<C><<<dim3(g.Ny, ntile), nthr, 0, s>>>(A, (const C*)GT, (const C*)GB);
+        k_sweep_correct<C><<<dim3(g.Ny, ntile), nthr, 0, s>>>(A, (const C*)pool[1], (const C*)pool[2]);
     }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_strip_solve<float2>(const Geom&, int, const StripDev&, const SweepStep&,
-                                                const SweepWork&, const void*, const void*, const void*,
-                                                const void*, const void*, const void*, cudaStream_t,
-                                                KernelTimer*);
+                                                const SweepWork&, void* const*, cudaStream_t, KernelTimer*);
 template cudaError_t launch_strip_solve<double2>(const Geom&, int, const StripDev&, const SweepStep&,
-                                                 const SweepWork&, const void*, const void*, const void*,
-                                                 const void*, const void*, const void*, cudaStream_t,
-                                                 KernelTimer*);
+                                                 const SweepWork&, void* const*, cudaStream_t, KernelTimer*);
 
 }  // namespace helm

@@ -52,6 +52,8 @@ def load() -> ctypes.CDLL:
         "helm_dd_create": (I, [ctypes.POINTER(_Grid), P, D, I, I, I, I, ctypes.POINTER(P)]),
         "helm_dd_set_pml_speed": (I, [P, D]),
         "helm_dd_set_chunks": (I, [P, I]),
+        "helm_dd_set_sep_groups": (I, [P, I]),
+        "helm_dd_sep_groups": (I, [P]),
         "helm_dd_factor": (I, [P]),
         "helm_dd_apply_precond": (I, [P, P, P, I]),
         "helm_dd_apply_precond_noalloc": (I, [P, P, P, I]),
@@ -112,10 +114,12 @@ class HelmDD:
     c: interior speed, shape (n_y, n_x) or (n_z, n_y, n_x) (x fastest); h: spacing;
     omega: angular frequency; w_outer / w_sub: outer and added PML widths;
     J: strips along x; precision: "fp64" or "mixed"; c_ref: speed fixing the
-    PML strength (default max c); chunks: y-partition count (0 = built-in).
+    PML strength (default max c); chunks: y-partition count (0 = built-in);
+    sep_groups: groups of the separator system (0 = built-in, 1 = one chain).
     """
 
-    def __init__(self, c, h, omega, w_outer, w_sub, J, precision="mixed", c_ref=None, chunks=0):
+    def __init__(self, c, h, omega, w_outer, w_sub, J, precision="mixed", c_ref=None, chunks=0,
+                 sep_groups=0):
         self.lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.dim = c.ndim
@@ -139,6 +143,8 @@ class HelmDD:
             self._check(self.lib.helm_dd_set_pml_speed(self._h, float(c_ref)))
         if chunks:
             self._check(self.lib.helm_dd_set_chunks(self._h, int(chunks)))
+        if sep_groups:
+            self._check(self.lib.helm_dd_set_sep_groups(self._h, int(sep_groups)))
         N = (ctypes.c_int64 * 3)()
         self.lib.helm_dd_dims(self._h, N)
         self.N = tuple(int(N[a]) for a in range(self.dim))
@@ -175,6 +181,9 @@ class HelmDD:
         buf = (ctypes.c_int * self.J)()
         self.lib.helm_dd_strip_widths(self._h, buf, self.J)
         return list(buf)
+
+    def sep_groups(self) -> int:
+        return int(self.lib.helm_dd_sep_groups(self._h))
 
     def precond_factor_bytes(self) -> float:
         return float(self.lib.helm_dd_precond_factor_bytes(self._h))

@@ -101,6 +101,26 @@ def test_chunking_does_not_change_the_preconditioner():
         assert rel(x, outs[0]) <= 1e-11
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_separator_groups_match_oracle(prec, tol):
+    """The two-level separator solve (groups plus a level-2 system) for several
+    group counts, including groups of one separator, single and batched RHS."""
+    n = (61, 90)
+    c = media.smooth_medium(n, 3.0, 1.0, 2.0, 6)
+    h = 1.0 / 32
+    omega = media.omega_for(c, h, 8.0)
+    o = HelmholtzDD(c, h, omega, 6, 5, 3).factor()
+    f = media.random_rhs((3,) + tuple(reversed(o.N)), 12)
+    ref = np.stack([o.apply_precond(f[b]) for b in range(3)])
+    for P, G, G_used in ((13, 1, 1), (13, 2, 2), (13, 3, 3), (13, 5, 5), (13, 9, 6), (4, 2, 2), (3, 2, 1),
+                         (13, 0, 3)):
+        g = helm.HelmDD(c, h, omega, 6, 5, 3, prec, chunks=P, sep_groups=G).factor()
+        assert g.sep_groups() == G_used
+        assert rel(g.apply_precond(f), ref) <= tol, (P, G)
+        assert rel(g.apply_precond(f[1]), ref[1]) <= tol, (P, G)
+        g.close()
+
+
 def test_one_strip_preconditioner_is_the_inverse():
     g, o = make((40, 33), 4, 3, 1, 4, "fp64")
     g.factor()

@@ -21,18 +21,19 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-def _problem(prec):
+def _problem(prec, chunks=5):
     n = (61, 45)
     c = media.smooth_medium(n, 3.0, 1.0, 2.0, 5)
     h = 1.0 / 32
     omega = media.omega_for(c, h, 8.0)
-    return helm.HelmDD(c, h, omega, 6, 5, 4, prec, chunks=5).factor()
+    return helm.HelmDD(c, h, omega, 6, 5, 4, prec, chunks=chunks).factor()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_noalloc_matches_apply_precond_on_two_calls(prec):
+# chunks 9 gives three separator groups (per-group arrival counters in the array)
+@pytest.mark.parametrize("prec,chunks", [("fp64", 5), ("mixed", 5), ("mixed", 9)])
+def test_noalloc_matches_apply_precond_on_two_calls(prec, chunks):
     torch = pytest.importorskip("torch")
-    g = _problem(prec)
+    g = _problem(prec, chunks)
     for call, seed in enumerate((21, 22)):
         f = torch.as_tensor(media.random_rhs((2,) + g.shape, seed), device="cuda")
         ref = g.apply_precond(f)
