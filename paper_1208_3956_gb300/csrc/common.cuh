@@ -89,6 +89,10 @@ __host__ __device__ __forceinline__ int sweep_nj(int W) {
     return W <= 32 ? 8 : W <= 40 ? 10 : W <= 48 ? 12 : W <= 56 ? 14 : 16;
 }
 
+// Spikes GT / GB (and GT2 / GB2) are stored row-major, W rows of spld(W)
+// entries: an even row length keeps every row 16-byte aligned for bulk copies.
+__host__ __device__ __forceinline__ int spld(int W) { return (W + 1) & ~1; }
+
 // Global geometry and tables (device pointers, FP64).
 struct Geom {
     int dim;
@@ -123,6 +127,10 @@ struct Geom {
     const int* gq0;
     const int* gq1;
     const int* sepmap;
+    // per chunk p, two int4: {r0, r1, gA, gB}, {raA, rbA, raB, rbB}: gA / gB is the
+    // group of the separator above / below the chunk (-1: none, level 2, or G = 1),
+    // ra / rb the rows of the level-2 separators above and below that group
+    const int4* cmeta;
 };
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }

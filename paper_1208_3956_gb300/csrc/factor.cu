@@ -39,9 +39,10 @@
 
 namespace helm {
 
-// Spikes are stored row-major (row c contiguous over columns a) so that the
-// correction step can read only the rows it outputs; e is a column-major index.
-__device__ __forceinline__ int trp(int e, int W) { return (e % W) * W + e / W; }
+// Spikes are stored row-major (row c contiguous over columns a, row length
+// spld(W)) so that the correction step can stage only the rows it outputs; e is
+// a column-major index.
+__device__ __forceinline__ int trp(int e, int W) { return (e % W) * spld(W) + e / W; }
 
 // shared (column-major W x W) <-> global sweep layout (row-major, ld, zero pad)
 template <typename C>

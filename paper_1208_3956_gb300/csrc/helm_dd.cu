@@ -79,7 +79,7 @@ struct helm_dd {
     size_t counter_bytes = 0;
     int zrows = 1;
     StripDev* d_strips = nullptr;
-    int* d_ints = nullptr;          // r0 | r1 | rowmap | gq0 | gq1 | sepmap
+    int* d_ints = nullptr;          // cmeta (8 per chunk) | r0 | r1 | rowmap | gq0 | gq1 | sepmap
     // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator)
     void* d_pool[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int* d_status = nullptr;
@@ -244,6 +244,10 @@ void chunk_layout(helm_dd* h) {
     }
 }
 
+// Row stride of the strip-solution and parts buffers: even, so that every row
+// starts 16-byte aligned for bulk copies.
+int work_stride(const helm_dd* h) { return (h->Wmax + 1) & ~1; }
+
 size_t counter_bytes(const helm_dd* h) { return (size_t)kMaxTiles * (h->G + 1) * sizeof(int); }
 
 double2 to_d2h(cd v) { return make_double2(v.real(), v.imag()); }
@@ -318,11 +322,24 @@ helm_status prepare_geom(helm_dd* h) {
     h->d_tab = nullptr; h->d_strips = nullptr; h->d_ints = nullptr;
     CK(h, cudaMalloc(&h->d_tab, tab2.size() * sizeof(double2)));
     CK(h, cudaMalloc(&h->d_strips, h->strips.size() * sizeof(StripDev)));
-    CK(h, cudaMalloc(&h->d_ints, (2 * h->P + Ny + 2 * h->G + h->sepmap.size()) * sizeof(int)));
+    CK(h, cudaMalloc(&h->d_ints, (8 * h->P + 2 * h->P + Ny + 2 * h->G + h->sepmap.size()) * sizeof(int)));
     CK(h, cudaMemcpyAsync(h->d_tab, tab2.data(), tab2.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
                           cudaMemcpyHostToDevice, h->stream));
     std::vector<int> ints;
+    for (int p = 0; p < h->P; ++p) {   // chunk metadata of the finishing kernel
+        int gs[2] = {-1, -1}, ra[2] = {0, 0}, rb[2] = {0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const int q = side == 0 ? p - 1 : p;
+            if (q < 0 || q >= h->P - 1 || h->G == 1 || h->sepmap[q] < 0) continue;
+            const int gi = h->sepmap[q];
+            gs[side] = gi;
+            if (gi > 0) ra[side] = h->r1[h->gq0[gi] - 1];
+            if (gi < h->G - 1) rb[side] = h->r1[h->gq1[gi]];
+        }
+        const int meta[8] = {h->r0[p], h->r1[p], gs[0], gs[1], ra[0], rb[0], ra[1], rb[1]};
+        ints.insert(ints.end(), meta, meta + 8);
+    }
     ints.insert(ints.end(), h->r0.begin(), h->r0.end());
     ints.insert(ints.end(), h->r1.begin(), h->r1.end());
     ints.insert(ints.end(), h->rowmap.begin(), h->rowmap.end());
@@ -350,9 +367,10 @@ helm_status prepare_geom(helm_dd* h) {
     g.gz_half = h->d_tab + o; o += h->gz_half.size();
     g.stab = h->d_tab + stab0;
     g.strips = h->d_strips;
-    g.r0 = h->d_ints;
-    g.r1 = h->d_ints + h->P;
-    g.rowmap = h->d_ints + 2 * h->P;
+    g.cmeta = reinterpret_cast<const int4*>(h->d_ints);
+    g.r0 = h->d_ints + 8 * h->P;
+    g.r1 = g.r0 + h->P;
+    g.rowmap = g.r1 + h->P;
     g.G = h->G;
     g.gq0 = g.rowmap + Ny;
     g.gq1 = g.gq0 + h->G;
@@ -555,8 +573,8 @@ struct PrecondBufs {
     double2* G;      // [B][N] residual g = f - A v
     double2* T0;     // [B][Ny] transfer differences (two, swapped per strip)
     double2* T1;
-    void* Y;         // [B][Ny][Wmax] strip solutions, working precision
-    void* parts;     // [B][P-1][4][Wmax] separator right-hand-side parts
+    void* Y;         // [B][Ny][ws] strip solutions, working precision (ws = work_stride)
+    void* parts;     // [B][P-1][4][ws] separator right-hand-side parts
     int* counters;   // [kMaxTiles][G+1] arrival counters, zero on entry
 };
 
@@ -568,8 +586,8 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[6]) {
     sz[1] = sz[0];
     sz[2] = (size_t)B * Ny * sizeof(double2);
     sz[3] = sz[2];
-    sz[4] = (size_t)B * Ny * h->Wmax * h->esize;
-    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 4 * h->Wmax * h->esize;
+    sz[4] = (size_t)B * Ny * work_stride(h) * h->esize;
+    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
@@ -599,7 +617,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     double2* G = bf.G;
     double2* Tin = bf.T0;
     double2* Tout = bf.T1;
-    SweepWork wk{bf.Y, bf.parts, bf.counters, h->d_status, h->Wmax, B, h->zrows};
+    SweepWork wk{bf.Y, bf.parts, bf.counters, h->d_status, work_stride(h), B, h->zrows};
     const int J = h->J;
     const auto& beta = h->beta;
     const double ih2 = 1.0 / (h->h * h->h);

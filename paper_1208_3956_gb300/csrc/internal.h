@@ -109,11 +109,11 @@ struct SweepStep {
 struct SweepWork {
     void* ybuf;             // [B][Ny][Wmax] working precision
     void* parts;            // [B][P-1][4][Wmax] working precision
-    int* counters;          // per RHS tile, zero between launches
+    int* counters;          // [RHS tile][G+1], zero between launches
     int* status;            // error word (7 = bounded wait timed out)
-    int Wmax;
+    int Wmax;               // row stride of ybuf and parts: even, >= every strip width
     int B;
-    int zrows;              // max(rows of the largest chunk, P-1)
+    int zrows;              // longest chain of one CTA (chunk rows, group size, G-1)
 };
 
 template <typename C>

@@ -16,9 +16,9 @@
 //     level-2 separators held at zero (twisted chain z_i = a_i - E_i z_outer,
 //     x_i = z_i - F_i x_inner) and adds the group's parts of the level-2
 //     right-hand sides; the last group to finish solves the level-2 system.
-// k_sweep_sepfix (grid: separators x RHS tiles; only with more than one group)
-//   x_q = y_q - GT2_q x2_above - GB2_q x2_below for the grouped separators.
-// k_sweep_correct (grid: rows x RHS tiles)
+// k_sweep_finish (grid: chunks x RHS tiles)
+//   final separator values (grouped separators: x_q = y_q - GT2_q x2_above -
+//   GB2_q x2_below), then
 //   x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output columns only, scatter
 //   to the output field (compose) and emit the transfer difference.
 //
@@ -34,6 +34,8 @@ namespace helm {
 static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
 static constexpr int kParts = 4;   // separator right-hand-side parts: 2 from chunks, 2 from groups
+static constexpr int kAhead = 6;   // block loads in flight ahead of the chain (three dual steps)
+static constexpr uint32_t kFinishBudget = 216 * 1024;  // k_sweep_finish: shared-memory budget
 
 // load-order table entries: factor pool << 24 | block index in that pool
 enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kP2L = 4, kP2U = 5 };
@@ -62,6 +64,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(m))
         : "memory");
+}
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
     uint32_t ok;
@@ -107,21 +112,6 @@ __device__ __forceinline__ C coupling(const SweepArgs& A, int k, int c) {
     return cmul(ctab<C>(A.g)[A.st.ctab + c], ctab<C>(A.g)[A.g.ct_cy + k]);
 }
 
-// S^(j) r at strip-local column c, row k, RHS b (working precision)
-template <typename C>
-__device__ __forceinline__ C rhs_entry(const SweepArgs& A, int k, int c, int b) {
-    const int gc = A.st.lo - A.st.lpml + c;
-    double2 v = make_double2(0.0, 0.0);
-    const int64_t row = (int64_t)b * A.g.Ny + k;
-    if (gc >= A.sp.mlo && gc <= A.sp.mhi) v = A.sp.src[row * A.g.Nx + gc];
-    if (A.sp.tin && (gc == A.sp.t0 || gc == A.sp.t0 + 1)) {
-        const double2 t = A.sp.tin[row];
-        v.x = fma(A.sp.tcoef, t.x, v.x);
-        v.y = fma(A.sp.tcoef, t.y, v.y);
-    }
-    return cmul(CT<C>::from(v), cmul(ctab<C>(A.g)[A.st.ctab + c], ctab<C>(A.g)[A.g.ct_sy + k]));
-}
-
 template <typename C>
 __device__ __forceinline__ C* yrow(const SweepArgs& A, int b, int k) {
     return reinterpret_cast<C*>(A.ybuf) + ((int64_t)b * A.g.Ny + k) * A.Wmax;
@@ -137,14 +127,37 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     uint32_t o = 0;
     s.slots = o; o += ring * slot_bytes;
     s.zb = o; o += ((uint32_t)zrows * Bt * W * esz + 15u) & ~15u;
-    s.tv = o; o += 4u * Bt * 64 * esz;                         // in/out vectors of both chains
+    s.tv = o; o += 5u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs
     s.cx = o; o += 64u * esz;
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
-    s.order = o; o += ((uint32_t)(2 * zrows + 4) * 4 + 15u) & ~15u;   // load order table
+    s.order = o; o += ((uint32_t)(6 * zrows + 8) * 4 + 15u) & ~15u;   // load order table
     s.mbar = o; o += kMaxRing * 8;
     s.flags = o; o += 16;
     s.total = o;
     return s;
+}
+
+// Load order of a twisted separator chain over n elements (consumed in the
+// same order by `chain` in k_sweep_chunk): the forward E loads of both halves
+// interleaved, E and F of the twist, then the back F loads.  slot(i) is the
+// factor slot of element i.
+template <typename SL>
+__device__ int chain_order(int* ord, int n, SL slot) {
+    const int tq = (n - 1) / 2;
+    const int fd = imax(tq - 1, 0), fu = imax(n - 2 - tq, 0), fmx = imax(fd, fu);
+    const int bd = tq, bu = n - 1 - tq, bmx = imax(bd, bu);
+    int nr = 0;
+    for (int s = 0; s < fmx; ++s) {
+        if (s < fd) ord[nr++] = enc(kEo, slot(1 + s));
+        if (s < fu) ord[nr++] = enc(kEo, slot(n - 2 - s));
+    }
+    if (tq >= 1) ord[nr++] = enc(kEo, slot(tq));
+    if (tq <= n - 2) ord[nr++] = enc(kFi, slot(tq));
+    for (int s = 0; s < bmx; ++s) {
+        if (s < bd) ord[nr++] = enc(kFi, slot(tq - 1 - s));
+        if (s < bu) ord[nr++] = enc(kFi, slot(tq + 1 + s));
+    }
+    return nr;
 }
 
 // ------------------------------------------------------------------ chunk + separators
@@ -231,7 +244,13 @@ __device__ __forceinline__ void dual_dispatch(bool dn, bool up, const C* Sd, con
 // The CTA is ceil(W/8) compute warps plus one producer warp.  The producer's
 // lane 0 owns the TMA ring: it initialises the barriers, issues every bulk
 // copy, and right after each step's barrier refills the slots that step
-// consumed, while the compute warps already run the next step.
+// consumed, while the compute warps already run the next step.  All factor
+// blocks the CTA may need form one load sequence: the chunk's Sinv rows and
+// the two Rinv blocks, then the chain of the chunk's separator group and the
+// level-2 chain.  Every CTA streams the start of the separator chains into
+// its free slots while it finishes the chunk; the CTA that arrives last at
+// its group solves the group with those blocks already resident, the others
+// wait for their copies to land and exit.
 template <typename C, int NJ, int BT>
 __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -242,11 +261,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     unsigned char* slots = smem + L.slots;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
     C* zb = reinterpret_cast<C*>(smem + L.zb);       // [zrows][BT][W]
-    C* v0 = reinterpret_cast<C*>(smem + L.tv);       // four [BT][64] vectors: in/out of both chains
+    C* v0 = reinterpret_cast<C*>(smem + L.tv);       // [BT][64] vectors: in/out of both chains, separator rhs
     C* vin_d = v0;
     C* vin_u = v0 + BT * 64;
     C* vout_d = v0 + 2 * BT * 64;
     C* vout_u = v0 + 3 * BT * 64;
+    C* rsep = v0 + 4 * BT * 64;                      // S r on the separator row below the chunk
     C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
     C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
     int* order = reinterpret_cast<int*>(smem + L.order);
@@ -259,8 +279,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     const int nd = t - r0, nu = r1 - 1 - t, nmx = imax(nd, nu);
     const int P = A.g.P, Q = P - 1;
     const int tid = threadIdx.x;
-    const int ptid = blockDim.x - 32;                // the producer thread
-    const bool producer = tid == ptid;
+    const int ptid = blockDim.x - 32;                // the producer warp starts here; threads below compute
+    const bool producer = tid == ptid;               // its lane 0: barriers, order table, status
+    const bool pwarp = tid >= ptid;                  // all its lanes issue copies, one each
+    const int plane = tid - ptid;
     const bool compute = tid < ptid;
     const int64_t bs = A.st.bs;
     const int ring = A.ring;
@@ -273,20 +295,22 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     const C* P2Ub = A.P2U ? reinterpret_cast<const C*>(A.P2U) + A.st.red : nullptr;
     const bool resident = ring >= m + 2;
     const bool has_below = p < P - 1, has_above = p > 0;
-    // ---- load order of the chunk phase (rows of Sinv, then Rinv below / above)
-    //   forward: s = 0..nmx-1: down row r0+s, up row r1-1-s; then the twist row
-    //   back (streaming only): s = 0..nmx-1: down row t-1-s, up row t+1+s
-    const int nload = m + (resident ? 0 : m - 1) + (has_below ? 1 : 0) + (has_above ? 1 : 0);
+    // separator group of this chunk: group gi owns separators gq0..gq1-1 and chunks gq0..gq1
+    const int NG = A.g.G;
+    const int gi = Q == 0 ? 0 : (p == Q ? NG - 1 : (A.g.sepmap[p] >= 0 ? A.g.sepmap[p] : -A.g.sepmap[p] - 1));
+    const int q0 = Q == 0 ? 0 : A.g.gq0[gi], q1 = Q == 0 ? 0 : A.g.gq1[gi], n1 = q1 - q0;
+    const bool up2 = gi > 0, dn2 = gi < NG - 1;   // level-2 separators above / below the group
+    const int n2 = NG - 1;
     // ---- ring state: load G lives in slot G % ring and completes phase (G / ring) & 1
-    int issued = 0, consumed = 0;           // issued: the producer's count
+    int nload = 0;                          // producer warp: length of the load sequence
+    int cap = 0;                            // producer warp: loads from cap on wait for the next arrival
+    int issued = 0, consumed = 0;
     int cslot = 0;
     uint32_t cpar = 0;
-    int rf = 0, rfslot = 0;                 // producer: next consumed load whose slot is reused
-    int nseq = nload;                       // loads in the current sequence
-    int seqbase = 0;                        // first load number of the current sequence
-    bool sep_phase = false;
+    bool hold = resident;                   // a resident chunk's slots are read again by the back pass
+    int nchunk = 0, ngroup = 0;             // producer warp: loads of the chunk and of the group chain
     auto src_of = [&](int G) -> const C* {
-        const int e = order[G - seqbase];
+        const int e = order[G];
         const int64_t o = (int64_t)(e & 0xffffff) * bs;
         switch (e >> 24) {
             case kSinv: return Sinv + o;
@@ -297,12 +321,18 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             default: return P2Ub + o;
         }
     };
-    auto issue_into = [&](int slot, const C* src) {   // producer only
-        uint64_t* mb = &mbar[slot];
-        fence_proxy_async();
-        mbar_expect_tx(mb, sb);
-        bulk_g2s(slots + (size_t)slot * sb, src, sb, mb);
-        ++issued;
+    // producer warp: issue loads issued .. lim-1 (at most one ring, one per lane) together
+    auto issue_upto = [&](int lim) {
+        const int n = lim - issued;
+        if (n <= 0) return;
+        if (plane < n) {
+            const int G = issued + plane, slot = G % ring;
+            uint64_t* mb = &mbar[slot];
+            fence_proxy_async();
+            mbar_expect_tx(mb, sb);
+            bulk_g2s(slots + (size_t)slot * sb, src_of(G), sb, mb);
+        }
+        issued = lim;
     };
     auto consume = [&]() -> const C* {
         const C* S = reinterpret_cast<const C*>(slots + (size_t)cslot * sb);
@@ -311,23 +341,33 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (++cslot == ring) { cslot = 0; cpar ^= 1u; }
         return S;
     };
-    // producer, after a barrier: every consumed slot is free; reuse it
+    // producer warp, after a barrier: keep kAhead loads in flight, each into a
+    // slot whose previous load has been consumed (and is no longer held)
     auto refill = [&]() {
-        while (rf < consumed) {
-            if (rf + ring < nseq) issue_into(rfslot, src_of(rf + ring));
-            ++rf;
-            if (++rfslot == ring) rfslot = 0;
-        }
+        const int room = hold ? ring : consumed + ring;
+        issue_upto(imin(imin(cap, nload), imin(room, consumed + kAhead)));
     };
-    auto drain = [&]() {
-        if (producer) {
-            atomicExch(A.status, 7);
-            for (int Gd = consumed - 1; Gd < issued; ++Gd)
-                if (Gd >= 0) mbar_wait(&mbar[Gd % ring], (uint32_t)((Gd / ring) & 1));
-        }
+    // producer: wait (bounded) for the copies still in flight from load `from` on
+    auto land = [&](int from) {
+        if (producer)
+            for (int Gd = imax(from, 0); Gd < issued; ++Gd) mbar_wait(&mbar[Gd % ring], (uint32_t)((Gd / ring) & 1));
+    };
+    auto abort_wait = [&]() {   // a bounded wait gave up: report, let the copies land, leave
+        if (producer) atomicExch(A.status, 7);
+        land(consumed - 1);
         __syncthreads();
     };
     if (producer) {
+        flags[1] = 0;
+        for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+    }
+    for (int o = tid; o < 5 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
+    __syncthreads();   // barriers initialised, vectors zeroed
+    const C* ct = ctab<C>(A.g);
+    if (producer) {
+        // load order: the chunk's blocks, then the group's separator chain (with the
+        // level-2 products) and the level-2 chain, whose slots come from global memory
         int G = 0;
         for (int s = 0; s < nmx; ++s) {
             if (s < nd) order[G++] = enc(kSinv, r0 + s);
@@ -341,24 +381,80 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             }
         if (has_below) order[G++] = enc(kRinv, p);
         if (has_above) order[G++] = enc(kRinv, p - 1);
-        flags[1] = 0;
-        for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
-        fence_mbar_init();
-        for (int i = 0; i < imin(ring, nload); ++i) issue_into(i, src_of(i));
+        nchunk = G;
+        if (Q > 0) {
+            G += chain_order(order + G, n1, [&](int i) { return q0 + i; });
+            if (dn2) order[G++] = enc(kP2L, q1);
+            if (up2) order[G++] = enc(kP2U, q0 - 1);
+            ngroup = G - nchunk;
+            if (NG > 1) {
+                int sl[64];   // level-2 slots, loads in flight together
+                for (int i = 0; i < imin(n2, 64); ++i) sl[i] = A.g.gq1[i];
+                G += chain_order(order + G, n2, [&](int i) { return i < 64 ? sl[i] : A.g.gq1[i]; });
+            }
+        }
+        nload = G;
     }
-    const C* ct = ctab<C>(A.g);
-    for (int o = tid; o < 4 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
-    for (int c = tid; c < W; c += blockDim.x) csx[c] = ct[A.st.ctab + c];
-    for (int k = r0 + tid; k <= r1; k += blockDim.x) ccy[k - r0] = ct[A.g.ct_cy + k];
+    if (pwarp) {
+        __syncwarp();
+        nload = __shfl_sync(0xffffffffu, nload, 0);
+        nchunk = __shfl_sync(0xffffffffu, nchunk, 0);
+        ngroup = __shfl_sync(0xffffffffu, ngroup, 0);
+        // the chunk's blocks and the first two steps of the group's separator chain:
+        // only the CTA that solves the group uses those, the others let them land
+        cap = nchunk + imin(4, ngroup);
+        refill();
+        // the group's first chunk stages the group's separator chain in L2, chunk 0
+        // the level-2 chain, for whichever CTA ends up solving them
+        auto stage_l2 = [&](int from, int to) {
+            for (int G = from + plane; G < to; G += 32) bulk_prefetch_l2(src_of(G), sb);
+        };
+        if (Q > 0 && p == q0) stage_l2(nchunk, nchunk + ngroup);
+        if (NG > 1 && p == 0) stage_l2(nchunk + ngroup, nload);
+    } else {
+        // tables and the right-hand sides of the chunk rows (and of the separator
+        // row below), four entries per thread with all their loads in flight together
+        for (int c = tid; c < W; c += ptid) csx[c] = ct[A.st.ctab + c];
+        for (int k = r0 + tid; k <= r1; k += ptid) ccy[k - r0] = ct[A.g.ct_cy + k];
+        const int tot = (m + (has_below ? 1 : 0)) * nb * W;
+        const int cofs = A.st.lo - A.st.lpml;
+        for (int o0 = tid; o0 < tot; o0 += 4 * ptid) {
+            double2 sv[4], tv2[4];
+            C sx[4], sy[4];
+            int cc[4], bb[4], rr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {   // loads only (clamped indices, no branches)
+                const int o = imin(o0 + u * ptid, tot - 1);
+                cc[u] = o % W;
+                bb[u] = (o / W) % nb;
+                rr[u] = o / (W * nb);
+                const int64_t rowi = (int64_t)(b0 + bb[u]) * A.g.Ny + r0 + rr[u];
+                sv[u] = __ldg(A.sp.src + rowi * A.g.Nx + imin(imax(cofs + cc[u], 0), A.g.Nx - 1));
+                tv2[u] = A.sp.tin ? __ldg(A.sp.tin + rowi) : make_double2(0.0, 0.0);
+                sx[u] = ct[A.st.ctab + cc[u]];
+                sy[u] = ct[A.g.ct_sy + r0 + rr[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (o0 + u * ptid >= tot) continue;
+                const int c = cc[u], b = bb[u], r = rr[u], gc = cofs + c;
+                double2 f = (gc >= A.sp.mlo && gc <= A.sp.mhi) ? sv[u] : make_double2(0.0, 0.0);
+                if (A.sp.tin && (gc == A.sp.t0 || gc == A.sp.t0 + 1)) {
+                    f.x = fma(A.sp.tcoef, tv2[u].x, f.x);
+                    f.y = fma(A.sp.tcoef, tv2[u].y, f.y);
+                }
+                const C v = cmul(CT<C>::from(f), cmul(sx[u], sy[u]));   // S^(j) r
+                if (r < m) {
+                    zb[(r * BT + b) * W + c] = v;
+                    if (r == 0 && nd > 0) vin_d[b * 64 + c] = v;       // down chain starts at r0
+                    if (r == m - 1 && nu > 0) vin_u[b * 64 + c] = v;   // up chain starts at r1-1
+                } else {
+                    rsep[b * 64 + c] = v;
+                }
+            }
+        }
+    }
     __syncthreads();
-    // right-hand sides of every chunk row (independent of the chain)
-    for (int o = tid; o < m * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
-        const C v = rhs_entry<C>(A, r0 + r, c, b0 + b);
-        zb[(r * BT + b) * W + c] = v;
-        if (r == 0 && nd > 0) vin_d[b * 64 + c] = v;            // down chain starts at r0
-        if (r == m - 1 && nu > 0) vin_u[b * 64 + c] = v;        // up chain starts at r1-1
-    }
     // per-lane geometry
     const int w = tid >> 5, l = tid & 31;
     const int row = w * 8 + (l >> 2);
@@ -367,14 +463,13 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     const int rc = imin(row, W - 1);
     const int lofs = rc * LD + g * NJ;     // this lane's run inside a block
     const int vofs = g * NJ;               // ... and inside a vector
-    const C csx_r = csx[rc];
-    __syncthreads();
+    const C csx_r = compute ? csx[rc] : CT<C>::zero();
     auto zr = [&](int k) -> C* { return zb + (k - r0) * BT * W; };   // row k, b = 0
     auto cpl = [&](int k) -> C { return cmul(csx_r, ccy[k - r0]); }; // C_k at this lane's row
     auto finish = [&]() -> bool {
         __syncthreads();
-        if (flags[1]) { drain(); return false; }
-        if (producer && !(resident && !sep_phase)) refill();
+        if (flags[1]) { abort_wait(); return false; }
+        if (pwarp) refill();
         C* x = vin_d; vin_d = vout_d; vout_d = x;
         x = vin_u; vin_u = vout_u; vout_u = x;
         return true;
@@ -497,24 +592,26 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         for (; s < nu; ++s)
             if (!bwd(std::false_type{}, std::true_type{}, s)) return;
     }
+    hold = false;   // the chunk's slots are free from here on: the next refill streams the separator chains
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, r = o / (W * nb);
         yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * BT + b) * W + c];
     }
+    if (Q == 0) return;   // every load of the sequence has been consumed
+    C* parts = reinterpret_cast<C*>(A.parts);
+    auto pidx = [&](int b, int q, int k) -> int64_t { return (((int64_t)(b0 + b) * Q + q) * kParts + k) * A.Wmax; };
     // ---- separator right-hand-side parts, both in one step:
     //   down chain: A_p     = Rinv_p     (b_s - C_s y(last)),   s = r1      (separator below)
     //   up chain:   B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first),     s' = r0 - 1 (separator above)
-    if (Q > 0) {
-        C* parts = reinterpret_cast<C*>(A.parts);
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            if (has_below)
-                vin_d[b * 64 + c] = csub(rhs_entry<C>(A, r1, c, b0 + b),
-                                         cmul(cmul(csx[c], ccy[r1 - r0]), zr(r1 - 1)[b * W + c]));
-            if (has_above) vin_u[b * 64 + c] = cneg(cmul(cmul(csx[c], ccy[0]), zr(r0)[b * W + c]));
-        }
-        __syncthreads();
+    for (int o = tid; o < nb * W; o += blockDim.x) {
+        const int c = o % W, b = o / W;
+        if (has_below)
+            vin_d[b * 64 + c] = csub(rsep[b * 64 + c], cmul(cmul(csx[c], ccy[r1 - r0]), zr(r1 - 1)[b * W + c]));
+        if (has_above) vin_u[b * 64 + c] = cneg(cmul(cmul(csx[c], ccy[0]), zr(r0)[b * W + c]));
+    }
+    __syncthreads();
+    {
         const C* SA = has_below ? consume() : nullptr;
         const C* SB = has_above ? consume() : nullptr;
         if (compute)
@@ -523,29 +620,33 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
-                if (has_below) parts[((((int64_t)(b0 + b) * Q + p) * kParts + 0) * A.Wmax) + row] = vd[b];
-                if (has_above) parts[((((int64_t)(b0 + b) * Q + p - 1) * kParts + 1) * A.Wmax) + row] = vu[b];
+                if (has_below) parts[pidx(b, p, 0) + row] = vd[b];
+                if (has_above) parts[pidx(b, p - 1, 1) + row] = vu[b];
             }
         if (!finish()) return;
     }
-    if (Q == 0) return;
     // ---- arrival: the last chunk CTA of group gi (chunks gq0..gq1) solves its separators
-    const int NG = A.g.G;
     int* cnt = A.counters + (int64_t)tile * (NG + 1);
-    const int gi = p == Q ? NG - 1 : (A.g.sepmap[p] >= 0 ? A.g.sepmap[p] : -A.g.sepmap[p] - 1);
-    const int q0 = A.g.gq0[gi], q1 = A.g.gq1[gi], n1 = q1 - q0;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const bool last = atomicAdd(&cnt[gi], 1) == n1;
-        if (last) cnt[gi] = 0;
-        flags[0] = last ? 1 : 0;
+    auto arrive = [&](int* ctr, int expect) -> bool {   // after a barrier; true on the last arrival
+        if (tid == 0) {
+            __threadfence();
+            const bool last = atomicAdd(ctr, 1) == expect;
+            if (last) {
+                *ctr = 0;
+                __threadfence();
+            }
+            flags[0] = last ? 1 : 0;
+        }
+        __syncthreads();
+        if (flags[0]) return true;
+        land(consumed);   // not the last: let the copies already issued land before leaving
+        return false;
+    };
+    if (!arrive(&cnt[gi], n1)) return;
+    if (pwarp) {   // the rest of the group chain, then the level-2 chain, stream in
+        cap = nload;
+        refill();
     }
-    __syncthreads();
-    if (!flags[0]) return;
-    __threadfence();
-    C* parts = reinterpret_cast<C*>(A.parts);
-    auto pidx = [&](int b, int q, int k) -> int64_t { return (((int64_t)(b0 + b) * Q + q) * kParts + k) * A.Wmax; };
     auto zq = [&](int i) -> C* { return zb + i * BT * W; };
     // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
     auto sep = [&](auto Dc, auto Uc, int qd, int qu) -> bool {
@@ -571,40 +672,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             }
         return finish();
     };
-    // Twisted solve of n separators whose factors sit at slot(i) (level 1: q0 + i;
-    // level 2: gq1[i]); a_i is in zq(i), a_0 / a_{n-1} in vin_d / vin_u.  xe0 / xe1
-    // (encoded, or -1) are extra loads appended to the sequence.  Every earlier
-    // load has been consumed, so the ring continues from slot cslot.
-    auto chain = [&](int n, int lvl, int xe0, int xe1) -> bool {
+    // Twisted solve of n separators in the load order of chain_order; a_i is in
+    // zq(i), a_0 / a_{n-1} in vin_d / vin_u.
+    auto chain = [&](int n) -> bool {
         const int tq = (n - 1) / 2;
-        const int fd = imax(tq - 1, 0), fu = imax(n - 2 - tq, 0), fmx = imax(fd, fu);   // forward steps
-        const int bd = tq, bu = n - 1 - tq, bmx = imax(bd, bu);                         // back steps
-        sep_phase = true;
-        if (producer) {
-            auto slot = [&](int i) { return lvl == 1 ? q0 + i : A.g.gq1[i]; };
-            int nr = 0;
-            for (int s = 0; s < fmx; ++s) {
-                if (s < fd) order[nr++] = enc(kEo, slot(1 + s));
-                if (s < fu) order[nr++] = enc(kEo, slot(n - 2 - s));
-            }
-            if (tq >= 1) order[nr++] = enc(kEo, slot(tq));
-            if (tq <= n - 2) order[nr++] = enc(kFi, slot(tq));
-            for (int s = 0; s < bmx; ++s) {
-                if (s < bd) order[nr++] = enc(kFi, slot(tq - 1 - s));
-                if (s < bu) order[nr++] = enc(kFi, slot(tq + 1 + s));
-            }
-            if (xe0 >= 0) order[nr++] = xe0;
-            if (xe1 >= 0) order[nr++] = xe1;
-            seqbase = consumed;
-            nseq = seqbase + nr;
-            rf = seqbase;
-            rfslot = cslot;
-            int sl = cslot;
-            for (int i = 0; i < imin(ring, nr); ++i) {
-                issue_into(sl, src_of(seqbase + i));
-                if (++sl == ring) sl = 0;
-            }
-        }
+        const int fd = imax(tq - 1, 0), fu = imax(n - 2 - tq, 0);   // forward steps
+        const int bd = tq, bu = n - 1 - tq;                          // back steps
         // forward: z_i = a_i - E_i z_outer, down i = 1..tq-1, up i = n-2..tq+1
         {
             int s = 0;
@@ -655,18 +728,39 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         return true;
     };
-    // ---- level 1: a_q = A_q + B_q for the group's separators q0 .. q1-1
-    const bool up2 = gi > 0, dn2 = gi < NG - 1;   // level-2 separators above / below the group
-    for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-        const int64_t pb = pidx(b, q0 + i, 0) + c;
-        const C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
-        zb[(i * BT + b) * W + c] = v;
-        if (i == 0) vin_d[b * 64 + c] = v;
-        if (i == n1 - 1) vin_u[b * 64 + c] = v;
-    }
-    __syncthreads();
-    if (!chain(n1, 1, dn2 ? enc(kP2L, q1) : -1, up2 ? enc(kP2U, q0 - 1) : -1)) return;
+    // right-hand sides a_i = sum of the parts of separator slot(i), two entries
+    // per thread with their loads in flight together
+    auto load_a = [&](int n, int lvl) {
+        const int tot = n * nb * W;
+        for (int o0 = tid; o0 < tot; o0 += 2 * blockDim.x) {
+            C v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = o0 + u * blockDim.x;
+                if (o < tot) {
+                    const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+                    const int64_t pb = pidx(b, lvl == 1 ? q0 + i : A.g.gq1[i], 0) + c;
+                    v[u] = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
+                    if (lvl == 2)
+                        v[u] = cadd(v[u], cadd(__ldcg(parts + pb + 2 * A.Wmax), __ldcg(parts + pb + 3 * A.Wmax)));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = o0 + u * blockDim.x;
+                if (o < tot) {
+                    const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+                    zb[(i * BT + b) * W + c] = v[u];
+                    if (i == 0) vin_d[b * 64 + c] = v[u];
+                    if (i == n - 1) vin_u[b * 64 + c] = v[u];
+                }
+            }
+        }
+        __syncthreads();
+    };
+    // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at zero
+    load_a(n1, 1);
+    if (!chain(n1)) return;
     for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
         yrow<C>(A, b0 + b, A.g.r1[q0 + i])[c] = zb[(i * BT + b) * W + c];
@@ -693,28 +787,9 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!finish()) return;
     }
     // ---- arrival: the last group to finish solves the level-2 system
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const bool last = atomicAdd(&cnt[NG], 1) == NG - 1;
-        if (last) cnt[NG] = 0;
-        flags[0] = last ? 1 : 0;
-    }
-    __syncthreads();
-    if (!flags[0]) return;
-    __threadfence();
-    const int n2 = NG - 1;
-    for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-        const int64_t pb = pidx(b, A.g.gq1[i], 0) + c;
-        C v = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
-        v = cadd(v, cadd(__ldcg(parts + pb + 2 * A.Wmax), __ldcg(parts + pb + 3 * A.Wmax)));
-        zb[(i * BT + b) * W + c] = v;
-        if (i == 0) vin_d[b * 64 + c] = v;
-        if (i == n2 - 1) vin_u[b * 64 + c] = v;
-    }
-    __syncthreads();
-    if (!chain(n2, 2, -1, -1)) return;
+    if (!arrive(&cnt[NG], NG - 1)) return;
+    load_a(n2, 2);
+    if (!chain(n2)) return;
     for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
         const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
         yrow<C>(A, b0 + b, A.g.r1[A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
@@ -759,96 +834,309 @@ __device__ __forceinline__ C spike_dot2(const C* __restrict__ ra, const C (&xa)[
     return s;
 }
 
-// One CTA per (separator, RHS tile): the grouped separator q of group gi gets
-// x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi} (row-major spikes); level-2
-// separators are already final.
-template <typename C>
-__global__ void __launch_bounds__(512) k_sweep_sepfix(SweepArgs A, const C* __restrict__ GT2,
-                                                      const C* __restrict__ GB2) {
-    const int q = blockIdx.x;
-    const int gi = A.g.sepmap[q];
-    if (gi < 0) return;
-    const int b0 = blockIdx.y * A.Bt;
-    const int nb = imin(A.Bt, A.B - b0);
-    const int W = A.st.W;
-    const int64_t off = A.st.red + (int64_t)q * A.st.bs;
-    const bool up = gi > 0, dn = gi < A.g.G - 1;
-    const int ra = up ? A.g.r1[A.g.gq0[gi] - 1] : 0;
-    const int rb = dn ? A.g.r1[A.g.gq1[gi]] : 0;
-    const int tid = threadIdx.x, g = tid & 7;
-    const int c = tid >> 3;                       // the block has 8 lanes per column, W <= 64
-    const bool live = c < W;
-    const int cc = imin(c, W - 1);
-    for (int b = 0; b < nb; ++b) {
-        C xa[8], xb[8];
-        lane_vec(xa, yrow<C>(A, b0 + b, ra), up, g, W);
-        lane_vec(xb, yrow<C>(A, b0 + b, rb), dn, g, W);
-        const C s = spike_dot2(GT2 + off + (int64_t)cc * W, xa, up, GB2 + off + (int64_t)cc * W, xb, dn, g, W);
-        if (live && g == 0) {
-            C* y = yrow<C>(A, b0 + b, A.g.r1[q]);
-            y[c] = csub(y[c], s);
-        }
+// Staging plan of k_sweep_finish, identical on host and device.
+//  Step 1 (the chunk's two separators): per side the level-2 spike blocks GT2_q,
+//  GB2_q (W rows of spld(W)) and, per RHS, three rows of we = even(W) entries:
+//  y_q and the level-2 values above and below the group.
+//  Step 2 (chunk rows): strip-local columns cmin..cmax cover the output and
+//  transfer columns; each row stages those rows of its two spikes (ncs rows of
+//  spld(W)), per RHS the even-aligned run y0..y0+ny-1 of its chain solution
+//  and, with a base field, the base values of the output columns.
+struct FinishPlan {
+    int cmin, cmax, ncs, y0, ny, we;
+    int rb;                  // chunk rows per batch
+    int nbuf;                // 1: every chunk in one batch; 2: two batches in flight
+    bool stage1;             // step 1 staged (else read from global memory)
+    uint32_t blk_bytes;      // one level-2 spike block
+    uint32_t vrow_bytes;     // one step-1 row
+    uint32_t spike_bytes;    // one spike segment of a chunk row
+    uint32_t y_bytes;        // one solution run
+    uint32_t base_bytes;     // base values of one row
+    uint32_t row_bytes;      // all segments of one chunk row: 2 spikes + Bt runs + Bt base runs
+    uint32_t xs, p1, buf, mbar, xt, total;   // shared-memory offsets
+};
+__host__ __device__ inline FinishPlan finish_plan(int W, int olo, int ohi, bool tr, int to0, int to1, bool base,
+                                                  bool grouped, int Bt, int esz, int maxrows, uint32_t budget) {
+    FinishPlan f;
+    const int nout = imax(ohi - olo + 1, 0);
+    f.cmin = olo;
+    f.cmax = ohi;
+    if (tr) {
+        f.cmin = imin(f.cmin, imin(to0, to1));
+        f.cmax = imax(f.cmax, imax(to0, to1));
     }
+    if (f.cmax < f.cmin) { f.cmin = 0; f.cmax = 0; }
+    f.ncs = f.cmax - f.cmin + 1;
+    f.y0 = f.cmin & ~1;
+    f.ny = ((f.cmax + 2) & ~1) - f.y0;
+    f.we = (W + 1) & ~1;
+    f.blk_bytes = (uint32_t)(W * spld(W) * esz);
+    f.vrow_bytes = (uint32_t)(f.we * esz);
+    f.spike_bytes = (uint32_t)(f.ncs * spld(W) * esz);
+    f.y_bytes = (uint32_t)(f.ny * esz);
+    f.base_bytes = base ? (uint32_t)(nout * 16) : 0u;
+    f.row_bytes = 2 * f.spike_bytes + (uint32_t)Bt * (f.y_bytes + f.base_bytes);
+    const uint32_t p1 = (grouped ? 4 * f.blk_bytes : 0u) + 2u * Bt * 3 * f.vrow_bytes;
+    const uint32_t xsb = (uint32_t)(2 * Bt * 64 * esz);
+    const uint32_t per1 = f.row_bytes + (uint32_t)(Bt * 2 * esz);       // one buffer, per row
+    const uint32_t per2 = 2 * f.row_bytes + (uint32_t)(Bt * 2 * esz);   // two buffers, per row
+    // stage step 1 when batches of two rows still fit beside it
+    f.stage1 = xsb + 32 + p1 + 2 * per2 <= budget;
+    const uint32_t left = budget - xsb - 32 - (f.stage1 ? p1 : 0u);
+    if ((uint32_t)maxrows * per1 <= left) {
+        f.nbuf = 1;
+        f.rb = imax(maxrows, 1);
+    } else {
+        f.nbuf = 2;
+        f.rb = imax(1, (int)(left / per2));
+    }
+    f.xs = 0;
+    f.p1 = xsb;
+    f.buf = f.p1 + (f.stage1 ? p1 : 0u);
+    f.mbar = f.buf + (uint32_t)f.nbuf * f.rb * f.row_bytes;
+    f.xt = f.mbar + 32;                                   // three barriers; then [rb][Bt][2] transfer columns
+    f.total = f.xt + (uint32_t)(f.rb * Bt * 2 * esz);
+    return f;
 }
 
-// One CTA per (row, RHS tile): x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the
-// output columns and the two transfer columns; the owning lane scatters x
-// (plus the base field) to the output, and the transfer difference is emitted.
+// One CTA per (chunk, RHS tile), after the chain kernel:
+//  1. the final values of the separators above and below the chunk: the chain
+//     kernel's values, for grouped separators corrected by the level-2 spikes,
+//     x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi}  (8 lanes per entry);
+//  2. x_k = y_k - GT_p(k) x_above - GB_p(k) x_below on the output and transfer
+//     columns of every chunk row (the separator row below is x_below itself),
+//     scattered (plus the base field) to the output, and the transfer
+//     difference x_k(to1) - x_k(to0) emitted.
+// Everything both steps read streams into shared memory with TMA bulk copies:
+// step 1's blocks first, then the chunk rows in batches, two in flight, while
+// the CTA works on step 1 and on the batch before.  Bounded waits as in
+// k_sweep_chunk.
 template <typename C>
-__global__ void __launch_bounds__(256) k_sweep_correct(SweepArgs A, const C* __restrict__ GT,
-                                                       const C* __restrict__ GB) {
-    const int k = blockIdx.x;
+__global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __restrict__ GT,
+                                                      const C* __restrict__ GB, const C* __restrict__ GT2,
+                                                      const C* __restrict__ GB2) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int p = blockIdx.x;
     const int b0 = blockIdx.y * A.Bt;
     const int nb = imin(A.Bt, A.B - b0);
-    const int W = A.st.W;
-    const int64_t bs = A.st.bs;
-    __shared__ C xt[8];   // the two transfer columns, per RHS (Bt <= 4)
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
-    const int pm = A.g.rowmap[k];
+    const int W = A.st.W, SL = spld(W);
+    const int esz = (int)sizeof(C);
+    const int P = A.g.P, NG = A.g.G;
+    const int4 m0 = A.g.cmeta[2 * p], m1 = A.g.cmeta[2 * p + 1];
+    const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
     const int off = A.st.lo - A.st.lpml;
     const int olo = imax(A.sp.olo - off, 0), ohi = imin(A.sp.ohi - off, W - 1);
     const int nout = imax(ohi - olo + 1, 0);
     const bool tr = A.sp.tout != nullptr;
-    const bool x0 = tr && (A.sp.to0 < olo || A.sp.to0 > ohi);
-    const bool x1 = tr && (A.sp.to1 < olo || A.sp.to1 > ohi);
-    const int ncol = nout + (x0 ? 1 : 0) + (x1 ? 1 : 0);
-    const bool above = pm > 0, below = pm >= 0 && pm < A.g.P - 1;
-    const int g = l & 7;
-    const int64_t rowoff = A.st.fac + (int64_t)k * bs;
-    for (int b = 0; b < nb; ++b) {
-        C xa[8], xb[8];
-        lane_vec(xa, yrow<C>(A, b0 + b, above ? A.g.r1[pm - 1] : 0), above, g, W);
-        lane_vec(xb, yrow<C>(A, b0 + b, below ? A.g.r1[pm] : 0), below, g, W);
-        for (int base = w * 4; base < ncol; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
-            // column i of this 8-lane group; groups past ncol idle but join the shuffles
-            const int i = base + (l >> 3);
-            const bool live = i < ncol;
-            int c = olo;
-            if (live) {
-                if (i < nout) c = olo + i;
-                else if (i == nout && x0) c = A.sp.to0;
-                else c = A.sp.to1;
-            }
-            const int cs = imin(imax(c, 0), W - 1);
-            const C s = spike_dot2(GT + rowoff + (int64_t)cs * W, xa, above, GB + rowoff + (int64_t)cs * W, xb,
-                                   below, g, W);
-            if (live && g == 0) {
-                const C x = csub(yrow<C>(A, b0 + b, k)[c], s);
-                const int64_t rowi = (int64_t)(b0 + b) * A.g.Ny + k;
-                if (c >= olo && c <= ohi) {
-                    double2 v = to_d2(x);
-                    if (A.sp.base) v = cadd(v, A.sp.base[rowi * A.g.Nx + off + c]);
-                    A.sp.dst[rowi * A.g.Nx + off + c] = v;
-                }
-                if (tr && c == A.sp.to0) xt[b * 2] = x;
-                if (tr && c == A.sp.to1) xt[b * 2 + 1] = x;
+    const bool hasb = A.sp.base != nullptr;
+    const FinishPlan F = finish_plan(W, olo, ohi, tr, A.sp.to0, A.sp.to1, hasb, NG > 1, A.Bt, esz, A.zrows,
+                                     kFinishBudget);
+    C* xs = reinterpret_cast<C*>(smem + F.xs);       // [2][Bt][64]: separator above, below
+    unsigned char* p1 = smem + F.p1;                 // step-1 staging
+    unsigned char* buf = smem + F.buf;               // [2][rb] rows of staged segments
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + F.mbar);   // [0], [1]: batches, [2]: step 1
+    C* xt = reinterpret_cast<C*>(smem + F.xt);
+    __shared__ int fail;
+    const bool above = p > 0, below = p < P - 1;
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = l & 7;
+    const int grp = tid >> 3, ngrp = blockDim.x >> 3;
+    const int nbatch = (m + F.rb - 1) / F.rb;
+    const int64_t bs = A.st.bs;
+    // step-1 geometry per side: separator q and its row, its group (>= 0: corrected
+    // by level-2 spikes) and the rows of the level-2 separators around that group
+    const int sq[2] = {p - 1, p}, srow[2] = {r0 - 1, r1};
+    const int sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
+    auto p1blk = [&](int side, int k) { return p1 + (size_t)(side * 2 + k) * F.blk_bytes; };   // k: GT2, GB2
+    auto p1row = [&](int side, int b, int k) {   // k: y_q, x2 above, x2 below
+        return p1 + 4 * (size_t)F.blk_bytes * (NG > 1) + ((size_t)(side * A.Bt + b) * 3 + k) * F.vrow_bytes;
+    };
+    // base values of the separator row below, prefetched into registers (nb * nout <= 256)
+    double2 sep_base = make_double2(0.0, 0.0);
+    if (below && hasb && tid < nb * nout) {
+        const int b = tid / nout, c = olo + tid % nout;
+        sep_base = A.sp.base[((int64_t)(b0 + b) * A.g.Ny + r1) * A.g.Nx + off + c];
+    }
+    if (tid == 0) {
+        fail = 0;
+        for (int i = 0; i < 3; ++i) mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // warp 0, step 1's blocks
+    if (F.stage1 && w == 0) {
+        uint32_t total = 0;
+        for (int side = 0; side < 2; ++side) {
+            if (side == 0 ? !above : !below) continue;
+            total += (uint32_t)nb * F.vrow_bytes * (1 + (sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
+            total += F.blk_bytes * ((sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
+        }
+        if (l == 0) mbar_expect_tx(&mbar[2], total);
+        __syncwarp();
+        for (int ci = l; ci < 2 * (2 + 3 * nb); ci += 32) {
+            const int side = ci / (2 + 3 * nb), k = ci % (2 + 3 * nb);
+            if (side == 0 ? !above : !below) continue;
+            const int gi = sg[side];
+            const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
+            const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
+            if (k == 0 && up) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[2]);
+            else if (k == 1 && dn) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[2]);
+            else if (k >= 2) {
+                const int b = (k - 2) / 3, kind = (k - 2) % 3;
+                if (kind == 0)
+                    bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[2]);
+                else if (kind == 1 && up)
+                    bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[2]);
+                else if (kind == 2 && dn)
+                    bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[2]);
             }
         }
     }
-    if (!tr) return;
+    int nissued = 0;
+    // warp 0: batch i into buffer i % 2 (called by every thread)
+    auto issue = [&](int i) {
+        ++nissued;
+        if (w != 0) return;
+        const int k0 = r0 + i * F.rb, nr = imin(F.rb, r1 - k0);
+        const uint32_t total = (uint32_t)nr * ((above ? F.spike_bytes : 0u) + (below ? F.spike_bytes : 0u) +
+                                               (uint32_t)nb * (F.y_bytes + F.base_bytes));
+        uint64_t* mb = &mbar[i & 1];
+        if (l == 0) mbar_expect_tx(mb, total);
+        __syncwarp();
+        unsigned char* bb = buf + (size_t)(i & 1) * F.rb * F.row_bytes;
+        const int per = 2 + 2 * nb;
+        for (int ci = l; ci < nr * per; ci += 32) {
+            const int kk = ci / per, kind = ci % per, k = k0 + kk;
+            unsigned char* dst = bb + (size_t)kk * F.row_bytes;
+            if (kind == 0 && above)
+                bulk_g2s(dst, GT + A.st.fac + (int64_t)k * bs + (int64_t)F.cmin * SL, F.spike_bytes, mb);
+            else if (kind == 1 && below)
+                bulk_g2s(dst + F.spike_bytes, GB + A.st.fac + (int64_t)k * bs + (int64_t)F.cmin * SL, F.spike_bytes,
+                         mb);
+            else if (kind >= 2 && kind < 2 + nb)
+                bulk_g2s(dst + 2 * F.spike_bytes + (size_t)(kind - 2) * F.y_bytes,
+                         yrow<C>(A, b0 + kind - 2, k) + F.y0, F.y_bytes, mb);
+            else if (kind >= 2 + nb && F.base_bytes > 0) {
+                const int b = kind - 2 - nb;
+                bulk_g2s(dst + 2 * F.spike_bytes + (size_t)A.Bt * F.y_bytes + (size_t)b * F.base_bytes,
+                         A.sp.base + ((int64_t)(b0 + b) * A.g.Ny + k) * A.g.Nx + off + olo, F.base_bytes, mb);
+            }
+        }
+    };
+    // batch i has landed (false, the same on every thread, if a bounded wait gave up)
+    auto wait = [&](int i) -> bool {
+        if (!mbar_wait(&mbar[i & 1], (uint32_t)((i >> 1) & 1))) fail = 1;
+        __syncthreads();
+        return fail == 0;
+    };
+    if (nbatch > 0) issue(0);
+    if (nbatch > 1) issue(1);
+    // ---- 1. separator values
+    if (F.stage1 && (above || below)) {
+        if (!mbar_wait(&mbar[2], 0u)) fail = 1;
+    }
     __syncthreads();
-    for (int b = tid; b < nb; b += blockDim.x)
-        A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + k] = csub(to_d2(xt[b * 2 + 1]), to_d2(xt[b * 2]));
+    if (fail) {   // a bounded wait gave up: let the issued copies land (bounded), leave
+        if (tid == 0) {
+            atomicExch(A.status, 7);
+            mbar_wait(&mbar[2], 0u);
+            for (int j = 0; j < nissued; ++j) mbar_wait(&mbar[j & 1], 0u);
+        }
+        __syncthreads();
+        return;
+    }
+    for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !above : !below) continue;
+        const int gi = sg[side];
+        const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
+        const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
+        const C* T2 = F.stage1 ? reinterpret_cast<const C*>(p1blk(side, 0)) : GT2 + o2;
+        const C* B2 = F.stage1 ? reinterpret_cast<const C*>(p1blk(side, 1)) : GB2 + o2;
+        for (int b = 0; b < nb; ++b) {
+            const C* y = F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 0))
+                                  : yrow<C>(A, b0 + b, srow[side]);
+            C* xo = xs + (side * A.Bt + b) * 64;
+            if (gi < 0) {
+                for (int c = tid; c < W; c += blockDim.x) xo[c] = y[c];
+                continue;
+            }
+            C xa[8], xb[8];
+            lane_vec(xa, F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 1)) : yrow<C>(A, b0 + b, sra[side]),
+                     up, g, W);
+            lane_vec(xb, F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 2)) : yrow<C>(A, b0 + b, srb[side]),
+                     dn, g, W);
+            for (int base = w * 4; base < W; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
+                const int c = base + (l >> 3);
+                const int cc = imin(c, W - 1);
+                const C sum = spike_dot2(T2 + (int64_t)cc * SL, xa, up, B2 + (int64_t)cc * SL, xb, dn, g, W);
+                if (c < W && g == 0) xo[c] = csub(y[c], sum);
+            }
+        }
+    }
+    __syncthreads();
+    auto emit = [&](int b, int k, int c, const C& x, const double2& bv) {   // output column c of row k
+        double2 v = to_d2(x);
+        if (hasb) v = cadd(v, bv);
+        A.sp.dst[((int64_t)(b0 + b) * A.g.Ny + k) * A.g.Nx + off + c] = v;
+    };
+    // the separator row below the chunk is final: x_below
+    if (below) {
+        if (tid < nb * nout) {
+            const int b = tid / nout, c = olo + tid % nout;
+            emit(b, r1, c, xs[(A.Bt + b) * 64 + c], sep_base);
+        }
+        if (tr && tid < nb) {
+            const C* xb = xs + (A.Bt + tid) * 64;
+            A.sp.tout[(int64_t)(b0 + tid) * A.g.Ny + r1] = csub(to_d2(xb[A.sp.to1]), to_d2(xb[A.sp.to0]));
+        }
+    }
+    // ---- 2. chunk rows, one batch at a time; tasks: output columns, then the two
+    //      transfer columns (one column per 8-lane group, all lanes shuffle)
+    const int ntask = nout + (tr ? 2 : 0);
+    int i = 0;
+    for (; i < nbatch; ++i) {
+        if (!wait(i)) break;
+        const int k0 = r0 + i * F.rb, nr = imin(F.rb, r1 - k0);
+        const unsigned char* bb = buf + (size_t)(i & 1) * F.rb * F.row_bytes;
+        for (int b = 0; b < nb; ++b) {
+            C xa[8], xb[8];
+            lane_vec(xa, xs + b * 64, above, g, W);
+            lane_vec(xb, xs + (A.Bt + b) * 64, below, g, W);
+            for (int t0 = 0; t0 < nr * ntask; t0 += ngrp) {   // uniform trip count
+                const bool live = t0 + grp < nr * ntask;
+                const int task = imin(t0 + grp, nr * ntask - 1);
+                const int kk = task / ntask, j = task % ntask;
+                const unsigned char* rowp = bb + (size_t)kk * F.row_bytes;
+                const C* sT = reinterpret_cast<const C*>(rowp);
+                const C* sB = reinterpret_cast<const C*>(rowp + F.spike_bytes);
+                const C* ys = reinterpret_cast<const C*>(rowp + 2 * F.spike_bytes + (size_t)b * F.y_bytes);
+                const double2* bsv = reinterpret_cast<const double2*>(rowp + 2 * F.spike_bytes +
+                                                                      (size_t)A.Bt * F.y_bytes +
+                                                                      (size_t)b * F.base_bytes);
+                const int c = j < nout ? olo + j : (j == nout ? A.sp.to0 : A.sp.to1);
+                const C sum = spike_dot2(sT + (c - F.cmin) * SL, xa, above, sB + (c - F.cmin) * SL, xb, below, g, W);
+                if (live && g == 0) {
+                    const C x = csub(ys[c - F.y0], sum);
+                    if (j < nout) emit(b, k0 + kk, c, x, hasb ? bsv[j] : make_double2(0.0, 0.0));
+                    else xt[(kk * A.Bt + b) * 2 + (j - nout)] = x;
+                }
+            }
+        }
+        __syncthreads();   // buffer i % 2 is free again; transfer columns complete
+        if (tr)
+            for (int o = tid; o < nr * nb; o += blockDim.x) {
+                const int kk = o / nb, b = o % nb;
+                A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + k0 + kk] =
+                    csub(to_d2(xt[(kk * A.Bt + b) * 2 + 1]), to_d2(xt[(kk * A.Bt + b) * 2]));
+            }
+        if (i + 2 < nbatch) issue(i + 2);
+    }
+    if (i < nbatch) {   // a bounded wait gave up: report, let the issued copies land (bounded), leave
+        if (tid == 0) {
+            atomicExch(A.status, 7);
+            for (int j = i; j < nissued; ++j) mbar_wait(&mbar[j & 1], (uint32_t)((j >> 1) & 1));
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ host
@@ -929,18 +1217,24 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    if (g.G > 1) {
-        TimedLaunch t(tm, "sweep_sepfix", s);
-        k_sweep_sepfix<C><<<dim3(g.P - 1, ntile), 8 * ((st.W + 3) & ~3), 0, s>>>(A, (const C*)pool[6],
-                                                                                (const C*)pool[7]);
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
     {
-        TimedLaunch t(tm, "sweep_correct", s);
-        // one warp per output column (the strip's output range plus the transfer columns)
-        const int ncol = (step.ohi - step.olo + 1) + 2;
-        const int nthr = 32 * imin(8, imax(1, (ncol + 3) / 4));
-        k_sweep_correct<C><<<dim3(g.Ny, ntile), nthr, 0, s>>>(A, (const C*)pool[1], (const C*)pool[2]);
+        // the plan the kernel derives, for the longest chunk (zrows bounds its rows):
+        // every chunk's own plan fits in this allocation
+        const int off = st.lo - st.lpml;
+        const int olo = imax(step.olo - off, 0), ohi = imin(step.ohi - off, st.W - 1);
+        const FinishPlan F = finish_plan(st.W, olo, ohi, step.tout != nullptr, step.to0, step.to1,
+                                         step.base != nullptr, g.G > 1, Bt, (int)sizeof(C), wk.zrows, kFinishBudget);
+        static bool fattr = false;
+        if (!fattr) {
+            err = cudaFuncSetAttribute(k_sweep_finish<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kFinishBudget);
+            if (err != cudaSuccess) return err;
+            fattr = true;
+        }
+        if (F.total > kFinishBudget) return cudaErrorInvalidConfiguration;
+        TimedLaunch t(tm, "sweep_finish", s);
+        k_sweep_finish<C><<<dim3(g.P, ntile), 512, F.total, s>>>(A, (const C*)pool[1], (const C*)pool[2],
+                                                                 (const C*)pool[6], (const C*)pool[7]);
     }
     return cudaGetLastError();
 }
