@@ -79,6 +79,7 @@ struct StripDev {
     int64_t ctab;  // offset of this strip's s_x(c) (W entries) in the working-precision table
     int nj;        // columns per lane in the sweep products (W <= 4 nj)
     int ld;        // leading dimension of the sweep-layout blocks (4 nj + 2)
+    int olo[2], ohi[2];   // padded output columns of the forward (0) and backward (1) sweeps
 };
 
 // Sweep layout of the W x W blocks Sinv, Rinv, E, F: row-major with leading

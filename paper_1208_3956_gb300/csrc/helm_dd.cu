@@ -89,7 +89,7 @@ struct helm_dd {
     bool dev_ready = false;
     // workspaces
     struct Ws { void* p = nullptr; size_t bytes = 0; };
-    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_parts, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
+    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_parts, ws_xsep, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
     KernelTimer timer;
     std::string err;
 };
@@ -506,7 +506,14 @@ helm_status helm_dd_factor(helm_dd* h) {
     if (h->dim != 2) return fail(h, HELM_EINVAL, "strip factorisation is implemented for 2-D grids");
     const int Ny = (int)h->N[1];
     int64_t fac = 0, red = 0;
-    for (auto& s : h->strips) {
+    for (size_t jj = 0; jj < h->strips.size(); ++jj) {
+        auto& s = h->strips[jj];
+        const int j = (int)jj;
+        // output columns: the forward sweep keeps v^(j) on D^(j), the backward w^(j) on D~^(j)
+        s.olo[0] = h->beta[j] + 1;
+        s.ohi[0] = h->beta[j + 1];
+        s.olo[1] = j > 0 ? h->beta[j] + 2 : 0;
+        s.ohi[1] = h->beta[j + 1] + 1;
         s.nj = sweep_nj(s.W);
         s.ld = 4 * s.nj + 2;
         s.bs = (int64_t)s.W * s.ld;   // sweep layout; even, so blocks stay 16-byte aligned
@@ -573,21 +580,24 @@ struct PrecondBufs {
     double2* G;      // [B][N] residual g = f - A v
     double2* T0;     // [B][Ny] transfer differences (two, swapped per strip)
     double2* T1;
-    void* Y;         // [B][Ny][ws] strip solutions, working precision (ws = work_stride)
+    void* Y;         // [J][B][Ny][ws] chain solutions of every strip, working precision (ws = work_stride)
     void* parts;     // [B][P-1][4][ws] separator right-hand-side parts
+    void* xsep;      // [J][B][max(P-1,1)][ws] final separator values of every strip
     int* counters;   // [kMaxTiles][G+1] arrival counters, zero on entry
 };
+constexpr int kPrecondBufs = 7;
 
-// Bytes of each PrecondBufs member for B right-hand sides.
-void precond_buf_bytes(const helm_dd* h, int B, size_t sz[6]) {
+// Bytes of each PrecondBufs member (V, G, T0, T1, Y, parts, xsep) for B right-hand sides.
+void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
     const int64_t NV = nvol(h);
     const int Ny = (int)h->N[1];
     sz[0] = (size_t)B * NV * sizeof(double2);
     sz[1] = sz[0];
     sz[2] = (size_t)B * Ny * sizeof(double2);
     sz[3] = sz[2];
-    sz[4] = (size_t)B * Ny * work_stride(h) * h->esize;
+    sz[4] = (size_t)h->J * B * Ny * work_stride(h) * h->esize;
     sz[5] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
+    sz[6] = (size_t)h->J * B * std::max(h->P - 1, 1) * work_stride(h) * h->esize;
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
@@ -595,7 +605,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
 // P applied to B device fields (Section 2.1): in -> out (distinct buffers).
 helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     helm_status s;
-    size_t sz[6];
+    size_t sz[kPrecondBufs];
     precond_buf_bytes(h, B, sz);
     if ((s = ws_reserve(h, h->ws_V, sz[0])) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_G, sz[1])) != HELM_OK) return s;
@@ -603,8 +613,9 @@ helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     if ((s = ws_reserve(h, h->ws_T1, sz[3])) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_Y, sz[4])) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_parts, sz[5])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_xsep, sz[6])) != HELM_OK) return s;
     PrecondBufs bf{(double2*)h->ws_V.p, (double2*)h->ws_G.p, (double2*)h->ws_T0.p, (double2*)h->ws_T1.p,
-                   h->ws_Y.p, h->ws_parts.p, h->d_counters};
+                   h->ws_Y.p, h->ws_parts.p, h->ws_xsep.p, h->d_counters};
     return run_precond(h, in, out, B, bf);
 }
 
@@ -617,14 +628,24 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     double2* G = bf.G;
     double2* Tin = bf.T0;
     double2* Tout = bf.T1;
-    SweepWork wk{bf.Y, bf.parts, bf.counters, h->d_status, work_stride(h), B, h->zrows};
+    const int ws = work_stride(h);
+    const int64_t ystride = (int64_t)B * Ny * ws, xstride = (int64_t)B * std::max(h->P - 1, 1) * ws;
     const int J = h->J;
     const auto& beta = h->beta;
     const double ih2 = 1.0 / (h->h * h->h);
+    const bool mixed = h->prec == HELM_PREC_MIXED;
+    // strip j: chain solution and final separator values in its own slices, so that
+    // the output columns of a whole sweep are written afterwards in one launch
     auto strip_solve = [&](int j, const SweepStep& sp) -> cudaError_t {
-        if (h->prec == HELM_PREC_MIXED)
-            return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
+        SweepWork wk{(char*)bf.Y + j * ystride * (int64_t)h->esize, bf.parts, bf.counters, h->d_status, ws, B,
+                     h->zrows, (char*)bf.xsep + j * xstride * (int64_t)h->esize};
+        if (mixed) return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
         return launch_strip_solve<double2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
+    };
+    auto outputs = [&](int dir, int nstrip, double2* dst, const double2* base) -> cudaError_t {
+        OutArgs O{h->geom, dir, 0, nstrip, bf.Y, ystride, bf.xsep, xstride, ws, B, B > 1 ? 4 : 1, dst, base};
+        if (mixed) return launch_outputs<float2>(O, h->d_pool, h->stream, &h->timer);
+        return launch_outputs<double2>(O, h->d_pool, h->stream, &h->timer);
     };
     // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1)
     for (int j = 0; j < J; ++j) {
@@ -646,6 +667,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         CK(h, strip_solve(j, sp));
         std::swap(Tin, Tout);
     }
+    CK(h, outputs(0, J, (J == 1) ? out : V, nullptr));
     if (J == 1) return HELM_OK;
     // residual g = f - A v
     if ((s = dev_stencil(h, V, in, G, B)) != HELM_OK) return s;
@@ -669,6 +691,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         CK(h, strip_solve(j, sp));
         std::swap(Tin, Tout);
     }
+    CK(h, outputs(1, J - 1, out, V));
     // D~^(J) keeps v (w = 0 there)
     CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
     return HELM_OK;
@@ -1071,7 +1094,7 @@ void helm_dd_destroy(helm_dd* h) {
     for (auto p : h->d_pool) cudaFree(p);
     cudaFree(h->d_ct);
     cudaFree(h->d_counters);
-    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_parts, &h->ws_xsep, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
                     &h->ws_small, &h->ws_grad})
         ws_free(*w);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -1128,12 +1151,12 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
         return fail(h, HELM_EINVAL, "apply_precond_noalloc takes device pointers only (host staging would allocate)");
     if ((const void*)in == (const void*)out)
         return fail(h, HELM_EINVAL, "apply_precond_noalloc needs distinct input and output buffers");
-    size_t sz[6];
+    size_t sz[kPrecondBufs];
     precond_buf_bytes(h, nrhs, sz);
-    size_t off[7];
+    size_t off[kPrecondBufs + 1];
     size_t total = 0;
-    for (int i = 0; i < 6; ++i) { off[i] = total; total += align256(sz[i]); }
-    off[6] = total;
+    for (int i = 0; i < kPrecondBufs; ++i) { off[i] = total; total += align256(sz[i]); }
+    off[kPrecondBufs] = total;
     total += align256(h->counter_bytes);
     if (total > kNoAllocScratchBytes)
         return fail(h, HELM_EINVAL, "apply_precond_noalloc needs " + std::to_string(total) +
@@ -1143,7 +1166,7 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
     CK(h, noalloc_scratch(&base));
     unsigned char* b = (unsigned char*)base;
     PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), (double2*)(b + off[2]), (double2*)(b + off[3]),
-                   b + off[4], b + off[5], (int*)(b + off[6])};
+                   b + off[4], b + off[5], b + off[6], (int*)(b + off[7])};
     // the array keeps whatever the previous call left: the arrival counters must start at zero
     CK(h, cudaMemsetAsync(bf.counters, 0, h->counter_bytes, h->stream));
     helm_status s = run_precond(h, (const double2*)in, (double2*)out, nrhs, bf);

@@ -107,14 +107,33 @@ struct SweepStep {
 };
 
 struct SweepWork {
-    void* ybuf;             // [B][Ny][Wmax] working precision
+    void* ybuf;             // [B][Ny][Wmax] working precision (this strip's chain solution)
     void* parts;            // [B][P-1][4][Wmax] working precision
     int* counters;          // [RHS tile][G+1], zero between launches
     int* status;            // error word (7 = bounded wait timed out)
-    int Wmax;               // row stride of ybuf and parts: even, >= every strip width
+    int Wmax;               // row stride of ybuf, parts and xsep: even, >= every strip width
     int B;
     int zrows;              // longest chain of one CTA (chunk rows, group size, G-1)
+    void* xsep;             // [B][max(P-1,1)][Wmax] this strip's final separator values
 };
+
+// Output pass of a sweep (k_sweep_output) over strips jlo .. jlo+nstrip-1,
+// after their strip solves: strip j's chain solution sits at ybuf + j*ystride
+// and its final separator values at xsep + j*xstride (elements).
+struct OutArgs {
+    Geom g;
+    int dir;                // output ranges of the forward (0) or backward (1) sweep
+    int jlo, nstrip;
+    const void* ybuf;
+    int64_t ystride;
+    const void* xsep;
+    int64_t xstride;
+    int Wmax, B, Bt;
+    double2* dst;           // [B][Ny][Nx] output field
+    const double2* base;    // optional field added on output
+};
+template <typename C>
+cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm);
 
 template <typename C>
 cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const SweepStep& step,

@@ -16,11 +16,13 @@
 //     level-2 separators held at zero (twisted chain z_i = a_i - E_i z_outer,
 //     x_i = z_i - F_i x_inner) and adds the group's parts of the level-2
 //     right-hand sides; the last group to finish solves the level-2 system.
-// k_sweep_finish (grid: chunks x RHS tiles)
+// k_sweep_transfer (grid: chunks x RHS tiles)
 //   final separator values (grouped separators: x_q = y_q - GT2_q x2_above -
-//   GB2_q x2_below), then
-//   x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output columns only, scatter
-//   to the output field (compose) and emit the transfer difference.
+//   GB2_q x2_below) and the transfer difference of every row, which is all the
+//   next strip solve waits for;
+// k_sweep_output (grid: chunks x strips x RHS tiles, once per sweep)
+//   x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output columns of every
+//   strip, scattered (plus the base field) to the output field.
 //
 // Every mbarrier wait is bounded; on time-out the kernel records
 // HELM_ETIMEOUT in the status word, drains its copies (bounded) and returns.
@@ -35,7 +37,7 @@ static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
 static constexpr int kParts = 4;   // separator right-hand-side parts: 2 from chunks, 2 from groups
 static constexpr int kAhead = 6;   // block loads in flight ahead of the chain (three dual steps)
-static constexpr uint32_t kFinishBudget = 216 * 1024;  // k_sweep_finish: shared-memory budget
+static constexpr uint32_t kXferBudget = 216 * 1024;   // k_sweep_transfer: shared-memory budget
 
 // load-order table entries: factor pool << 24 | block index in that pool
 enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kP2L = 4, kP2U = 5 };
@@ -100,6 +102,7 @@ struct SweepArgs {
     const void* P2U;
     void* ybuf;              // [B][Ny][Wmax] chunk solutions, then separator values
     void* parts;             // [B][P-1][kParts][Wmax] separator right-hand-side parts
+    void* xsep;              // [B][max(P-1,1)][Wmax] final separator values (for the output kernel)
     int* counters;           // [ntile][G+1] arrival counters, left at zero
     int* status;
 };
@@ -834,87 +837,45 @@ __device__ __forceinline__ C spike_dot2(const C* __restrict__ ra, const C (&xa)[
     return s;
 }
 
-// Staging plan of k_sweep_finish, identical on host and device.
-//  Step 1 (the chunk's two separators): per side the level-2 spike blocks GT2_q,
-//  GB2_q (W rows of spld(W)) and, per RHS, three rows of we = even(W) entries:
-//  y_q and the level-2 values above and below the group.
-//  Step 2 (chunk rows): strip-local columns cmin..cmax cover the output and
-//  transfer columns; each row stages those rows of its two spikes (ncs rows of
-//  spld(W)), per RHS the even-aligned run y0..y0+ny-1 of its chain solution
-//  and, with a base field, the base values of the output columns.
-struct FinishPlan {
-    int cmin, cmax, ncs, y0, ny, we;
-    int rb;                  // chunk rows per batch
-    int nbuf;                // 1: every chunk in one batch; 2: two batches in flight
-    bool stage1;             // step 1 staged (else read from global memory)
-    uint32_t blk_bytes;      // one level-2 spike block
-    uint32_t vrow_bytes;     // one step-1 row
-    uint32_t spike_bytes;    // one spike segment of a chunk row
-    uint32_t y_bytes;        // one solution run
-    uint32_t base_bytes;     // base values of one row
-    uint32_t row_bytes;      // all segments of one chunk row: 2 spikes + Bt runs + Bt base runs
-    uint32_t xs, p1, buf, mbar, xt, total;   // shared-memory offsets
+// Shared memory of k_sweep_transfer (bytes), identical on host and device: the
+// separator values xs [2][Bt][64], then, when it fits, the staged level-2
+// spike blocks GT2_q, GB2_q of both sides (W rows of spld(W)) and per side and
+// RHS three rows of we = even(W) entries (y_q and the level-2 values above and
+// below the group), then three barriers and the transfer columns [rows][Bt][2].
+struct XferPlan {
+    bool stage;
+    uint32_t blk_bytes, vrow_bytes, xs, p1, mbar, xt, total;
 };
-__host__ __device__ inline FinishPlan finish_plan(int W, int olo, int ohi, bool tr, int to0, int to1, bool base,
-                                                  bool grouped, int Bt, int esz, int maxrows, uint32_t budget) {
-    FinishPlan f;
-    const int nout = imax(ohi - olo + 1, 0);
-    f.cmin = olo;
-    f.cmax = ohi;
-    if (tr) {
-        f.cmin = imin(f.cmin, imin(to0, to1));
-        f.cmax = imax(f.cmax, imax(to0, to1));
-    }
-    if (f.cmax < f.cmin) { f.cmin = 0; f.cmax = 0; }
-    f.ncs = f.cmax - f.cmin + 1;
-    f.y0 = f.cmin & ~1;
-    f.ny = ((f.cmax + 2) & ~1) - f.y0;
-    f.we = (W + 1) & ~1;
+__host__ __device__ inline XferPlan xfer_plan(int W, bool grouped, int Bt, int esz, int maxrows, uint32_t budget) {
+    XferPlan f;
     f.blk_bytes = (uint32_t)(W * spld(W) * esz);
-    f.vrow_bytes = (uint32_t)(f.we * esz);
-    f.spike_bytes = (uint32_t)(f.ncs * spld(W) * esz);
-    f.y_bytes = (uint32_t)(f.ny * esz);
-    f.base_bytes = base ? (uint32_t)(nout * 16) : 0u;
-    f.row_bytes = 2 * f.spike_bytes + (uint32_t)Bt * (f.y_bytes + f.base_bytes);
+    f.vrow_bytes = (uint32_t)(((W + 1) & ~1) * esz);
     const uint32_t p1 = (grouped ? 4 * f.blk_bytes : 0u) + 2u * Bt * 3 * f.vrow_bytes;
-    const uint32_t xsb = (uint32_t)(2 * Bt * 64 * esz);
-    const uint32_t per1 = f.row_bytes + (uint32_t)(Bt * 2 * esz);       // one buffer, per row
-    const uint32_t per2 = 2 * f.row_bytes + (uint32_t)(Bt * 2 * esz);   // two buffers, per row
-    // stage step 1 when batches of two rows still fit beside it
-    f.stage1 = xsb + 32 + p1 + 2 * per2 <= budget;
-    const uint32_t left = budget - xsb - 32 - (f.stage1 ? p1 : 0u);
-    if ((uint32_t)maxrows * per1 <= left) {
-        f.nbuf = 1;
-        f.rb = imax(maxrows, 1);
-    } else {
-        f.nbuf = 2;
-        f.rb = imax(1, (int)(left / per2));
-    }
+    const uint32_t xsb = (uint32_t)(2 * Bt * 64 * esz), xtb = (uint32_t)(maxrows * Bt * 2 * esz);
+    f.stage = xsb + p1 + 32 + xtb <= budget;
     f.xs = 0;
     f.p1 = xsb;
-    f.buf = f.p1 + (f.stage1 ? p1 : 0u);
-    f.mbar = f.buf + (uint32_t)f.nbuf * f.rb * f.row_bytes;
-    f.xt = f.mbar + 32;                                   // three barriers; then [rb][Bt][2] transfer columns
-    f.total = f.xt + (uint32_t)(f.rb * Bt * 2 * esz);
+    f.mbar = f.p1 + (f.stage ? p1 : 0u);
+    f.xt = f.mbar + 32;
+    f.total = f.xt + xtb;
     return f;
 }
 
-// One CTA per (chunk, RHS tile), after the chain kernel:
+// One CTA per (chunk, RHS tile), after the chain kernel; the part of the
+// strip solve the next strip waits for:
 //  1. the final values of the separators above and below the chunk: the chain
 //     kernel's values, for grouped separators corrected by the level-2 spikes,
-//     x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi}  (8 lanes per entry);
-//  2. x_k = y_k - GT_p(k) x_above - GB_p(k) x_below on the output and transfer
-//     columns of every chunk row (the separator row below is x_below itself),
-//     scattered (plus the base field) to the output, and the transfer
-//     difference x_k(to1) - x_k(to0) emitted.
-// Everything both steps read streams into shared memory with TMA bulk copies:
-// step 1's blocks first, then the chunk rows in batches, two in flight, while
-// the CTA works on step 1 and on the batch before.  Bounded waits as in
-// k_sweep_chunk.
+//     x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi}  (8 lanes per entry; the
+//     blocks are staged in shared memory by TMA bulk copies when they fit);
+//     the separator below is written to xsep for the output kernel;
+//  2. the transfer difference x_k(to1) - x_k(to0), x_k = y_k - GT_p(k) x_above -
+//     GB_p(k) x_below, for every chunk row and the separator row below.
+// The output columns are left to k_sweep_output, which needs no ordering with
+// the strips that follow.
 template <typename C>
-__global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __restrict__ GT,
-                                                      const C* __restrict__ GB, const C* __restrict__ GT2,
-                                                      const C* __restrict__ GB2) {
+__global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __restrict__ GT,
+                                                        const C* __restrict__ GB, const C* __restrict__ GT2,
+                                                        const C* __restrict__ GB2) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int p = blockIdx.x;
     const int b0 = blockIdx.y * A.Bt;
@@ -924,53 +885,39 @@ __global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __re
     const int P = A.g.P, NG = A.g.G;
     const int4 m0 = A.g.cmeta[2 * p], m1 = A.g.cmeta[2 * p + 1];
     const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
-    const int off = A.st.lo - A.st.lpml;
-    const int olo = imax(A.sp.olo - off, 0), ohi = imin(A.sp.ohi - off, W - 1);
-    const int nout = imax(ohi - olo + 1, 0);
     const bool tr = A.sp.tout != nullptr;
-    const bool hasb = A.sp.base != nullptr;
-    const FinishPlan F = finish_plan(W, olo, ohi, tr, A.sp.to0, A.sp.to1, hasb, NG > 1, A.Bt, esz, A.zrows,
-                                     kFinishBudget);
+    const XferPlan F = xfer_plan(W, NG > 1, A.Bt, esz, A.zrows, kXferBudget);
     C* xs = reinterpret_cast<C*>(smem + F.xs);       // [2][Bt][64]: separator above, below
-    unsigned char* p1 = smem + F.p1;                 // step-1 staging
-    unsigned char* buf = smem + F.buf;               // [2][rb] rows of staged segments
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + F.mbar);   // [0], [1]: batches, [2]: step 1
-    C* xt = reinterpret_cast<C*>(smem + F.xt);
-    __shared__ int fail;
+    unsigned char* p1 = smem + F.p1;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + F.mbar);
+    C* xt = reinterpret_cast<C*>(smem + F.xt);       // [m][Bt][2]
     const bool above = p > 0, below = p < P - 1;
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = l & 7;
     const int grp = tid >> 3, ngrp = blockDim.x >> 3;
-    const int nbatch = (m + F.rb - 1) / F.rb;
     const int64_t bs = A.st.bs;
-    // step-1 geometry per side: separator q and its row, its group (>= 0: corrected
-    // by level-2 spikes) and the rows of the level-2 separators around that group
+    // per side: separator q and its row, its group (>= 0: corrected by level-2
+    // spikes) and the rows of the level-2 separators around that group
     const int sq[2] = {p - 1, p}, srow[2] = {r0 - 1, r1};
     const int sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
     auto p1blk = [&](int side, int k) { return p1 + (size_t)(side * 2 + k) * F.blk_bytes; };   // k: GT2, GB2
     auto p1row = [&](int side, int b, int k) {   // k: y_q, x2 above, x2 below
         return p1 + 4 * (size_t)F.blk_bytes * (NG > 1) + ((size_t)(side * A.Bt + b) * 3 + k) * F.vrow_bytes;
     };
-    // base values of the separator row below, prefetched into registers (nb * nout <= 256)
-    double2 sep_base = make_double2(0.0, 0.0);
-    if (below && hasb && tid < nb * nout) {
-        const int b = tid / nout, c = olo + tid % nout;
-        sep_base = A.sp.base[((int64_t)(b0 + b) * A.g.Ny + r1) * A.g.Nx + off + c];
-    }
+    __shared__ int fail;
     if (tid == 0) {
         fail = 0;
-        for (int i = 0; i < 3; ++i) mbar_init(&mbar[i], 1);
+        mbar_init(&mbar[0], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    // warp 0, step 1's blocks
-    if (F.stage1 && w == 0) {
+    if (F.stage && w == 0 && (above || below)) {   // warp 0 stages step 1
         uint32_t total = 0;
         for (int side = 0; side < 2; ++side) {
             if (side == 0 ? !above : !below) continue;
-            total += (uint32_t)nb * F.vrow_bytes * (1 + (sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
-            total += F.blk_bytes * ((sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
+            const int nup = sg[side] > 0, ndn = sg[side] >= 0 && sg[side] < NG - 1;
+            total += (uint32_t)nb * F.vrow_bytes * (1 + nup + ndn) + F.blk_bytes * (nup + ndn);
         }
-        if (l == 0) mbar_expect_tx(&mbar[2], total);
+        if (l == 0) mbar_expect_tx(&mbar[0], total);
         __syncwarp();
         for (int ci = l; ci < 2 * (2 + 3 * nb); ci += 32) {
             const int side = ci / (2 + 3 * nb), k = ci % (2 + 3 * nb);
@@ -978,68 +925,25 @@ __global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __re
             const int gi = sg[side];
             const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
             const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
-            if (k == 0 && up) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[2]);
-            else if (k == 1 && dn) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[2]);
+            if (k == 0 && up) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[0]);
+            else if (k == 1 && dn) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[0]);
             else if (k >= 2) {
                 const int b = (k - 2) / 3, kind = (k - 2) % 3;
-                if (kind == 0)
-                    bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[2]);
+                if (kind == 0) bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[0]);
                 else if (kind == 1 && up)
-                    bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[2]);
+                    bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[0]);
                 else if (kind == 2 && dn)
-                    bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[2]);
+                    bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[0]);
             }
         }
     }
-    int nissued = 0;
-    // warp 0: batch i into buffer i % 2 (called by every thread)
-    auto issue = [&](int i) {
-        ++nissued;
-        if (w != 0) return;
-        const int k0 = r0 + i * F.rb, nr = imin(F.rb, r1 - k0);
-        const uint32_t total = (uint32_t)nr * ((above ? F.spike_bytes : 0u) + (below ? F.spike_bytes : 0u) +
-                                               (uint32_t)nb * (F.y_bytes + F.base_bytes));
-        uint64_t* mb = &mbar[i & 1];
-        if (l == 0) mbar_expect_tx(mb, total);
-        __syncwarp();
-        unsigned char* bb = buf + (size_t)(i & 1) * F.rb * F.row_bytes;
-        const int per = 2 + 2 * nb;
-        for (int ci = l; ci < nr * per; ci += 32) {
-            const int kk = ci / per, kind = ci % per, k = k0 + kk;
-            unsigned char* dst = bb + (size_t)kk * F.row_bytes;
-            if (kind == 0 && above)
-                bulk_g2s(dst, GT + A.st.fac + (int64_t)k * bs + (int64_t)F.cmin * SL, F.spike_bytes, mb);
-            else if (kind == 1 && below)
-                bulk_g2s(dst + F.spike_bytes, GB + A.st.fac + (int64_t)k * bs + (int64_t)F.cmin * SL, F.spike_bytes,
-                         mb);
-            else if (kind >= 2 && kind < 2 + nb)
-                bulk_g2s(dst + 2 * F.spike_bytes + (size_t)(kind - 2) * F.y_bytes,
-                         yrow<C>(A, b0 + kind - 2, k) + F.y0, F.y_bytes, mb);
-            else if (kind >= 2 + nb && F.base_bytes > 0) {
-                const int b = kind - 2 - nb;
-                bulk_g2s(dst + 2 * F.spike_bytes + (size_t)A.Bt * F.y_bytes + (size_t)b * F.base_bytes,
-                         A.sp.base + ((int64_t)(b0 + b) * A.g.Ny + k) * A.g.Nx + off + olo, F.base_bytes, mb);
-            }
-        }
-    };
-    // batch i has landed (false, the same on every thread, if a bounded wait gave up)
-    auto wait = [&](int i) -> bool {
-        if (!mbar_wait(&mbar[i & 1], (uint32_t)((i >> 1) & 1))) fail = 1;
-        __syncthreads();
-        return fail == 0;
-    };
-    if (nbatch > 0) issue(0);
-    if (nbatch > 1) issue(1);
     // ---- 1. separator values
-    if (F.stage1 && (above || below)) {
-        if (!mbar_wait(&mbar[2], 0u)) fail = 1;
-    }
+    if (F.stage && (above || below) && !mbar_wait(&mbar[0], 0u)) fail = 1;
     __syncthreads();
-    if (fail) {   // a bounded wait gave up: let the issued copies land (bounded), leave
+    if (fail) {   // a bounded wait gave up: report, let the copies land (bounded), leave
         if (tid == 0) {
             atomicExch(A.status, 7);
-            mbar_wait(&mbar[2], 0u);
-            for (int j = 0; j < nissued; ++j) mbar_wait(&mbar[j & 1], 0u);
+            mbar_wait(&mbar[0], 0u);
         }
         __syncthreads();
         return;
@@ -1049,20 +953,19 @@ __global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __re
         const int gi = sg[side];
         const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
         const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
-        const C* T2 = F.stage1 ? reinterpret_cast<const C*>(p1blk(side, 0)) : GT2 + o2;
-        const C* B2 = F.stage1 ? reinterpret_cast<const C*>(p1blk(side, 1)) : GB2 + o2;
+        const C* T2 = F.stage ? reinterpret_cast<const C*>(p1blk(side, 0)) : GT2 + o2;
+        const C* B2 = F.stage ? reinterpret_cast<const C*>(p1blk(side, 1)) : GB2 + o2;
         for (int b = 0; b < nb; ++b) {
-            const C* y = F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 0))
-                                  : yrow<C>(A, b0 + b, srow[side]);
+            const C* y = F.stage ? reinterpret_cast<const C*>(p1row(side, b, 0)) : yrow<C>(A, b0 + b, srow[side]);
             C* xo = xs + (side * A.Bt + b) * 64;
             if (gi < 0) {
                 for (int c = tid; c < W; c += blockDim.x) xo[c] = y[c];
                 continue;
             }
             C xa[8], xb[8];
-            lane_vec(xa, F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 1)) : yrow<C>(A, b0 + b, sra[side]),
+            lane_vec(xa, F.stage ? reinterpret_cast<const C*>(p1row(side, b, 1)) : yrow<C>(A, b0 + b, sra[side]),
                      up, g, W);
-            lane_vec(xb, F.stage1 ? reinterpret_cast<const C*>(p1row(side, b, 2)) : yrow<C>(A, b0 + b, srb[side]),
+            lane_vec(xb, F.stage ? reinterpret_cast<const C*>(p1row(side, b, 2)) : yrow<C>(A, b0 + b, srb[side]),
                      dn, g, W);
             for (int base = w * 4; base < W; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
                 const int c = base + (l >> 3);
@@ -1073,69 +976,130 @@ __global__ void __launch_bounds__(512) k_sweep_finish(SweepArgs A, const C* __re
         }
     }
     __syncthreads();
-    auto emit = [&](int b, int k, int c, const C& x, const double2& bv) {   // output column c of row k
-        double2 v = to_d2(x);
-        if (hasb) v = cadd(v, bv);
-        A.sp.dst[((int64_t)(b0 + b) * A.g.Ny + k) * A.g.Nx + off + c] = v;
-    };
-    // the separator row below the chunk is final: x_below
+    // the separator below is final: to the output kernel, and its transfer difference
     if (below) {
-        if (tid < nb * nout) {
-            const int b = tid / nout, c = olo + tid % nout;
-            emit(b, r1, c, xs[(A.Bt + b) * 64 + c], sep_base);
+        C* xsep = reinterpret_cast<C*>(A.xsep);
+        for (int o = tid; o < nb * W; o += blockDim.x) {
+            const int b = o / W, c = o % W;
+            xsep[((int64_t)(b0 + b) * imax(P - 1, 1) + p) * A.Wmax + c] = xs[(A.Bt + b) * 64 + c];
         }
         if (tr && tid < nb) {
             const C* xb = xs + (A.Bt + tid) * 64;
             A.sp.tout[(int64_t)(b0 + tid) * A.g.Ny + r1] = csub(to_d2(xb[A.sp.to1]), to_d2(xb[A.sp.to0]));
         }
     }
-    // ---- 2. chunk rows, one batch at a time; tasks: output columns, then the two
-    //      transfer columns (one column per 8-lane group, all lanes shuffle)
-    const int ntask = nout + (tr ? 2 : 0);
-    int i = 0;
-    for (; i < nbatch; ++i) {
-        if (!wait(i)) break;
-        const int k0 = r0 + i * F.rb, nr = imin(F.rb, r1 - k0);
-        const unsigned char* bb = buf + (size_t)(i & 1) * F.rb * F.row_bytes;
-        for (int b = 0; b < nb; ++b) {
-            C xa[8], xb[8];
-            lane_vec(xa, xs + b * 64, above, g, W);
-            lane_vec(xb, xs + (A.Bt + b) * 64, below, g, W);
-            for (int t0 = 0; t0 < nr * ntask; t0 += ngrp) {   // uniform trip count
-                const bool live = t0 + grp < nr * ntask;
-                const int task = imin(t0 + grp, nr * ntask - 1);
-                const int kk = task / ntask, j = task % ntask;
-                const unsigned char* rowp = bb + (size_t)kk * F.row_bytes;
-                const C* sT = reinterpret_cast<const C*>(rowp);
-                const C* sB = reinterpret_cast<const C*>(rowp + F.spike_bytes);
-                const C* ys = reinterpret_cast<const C*>(rowp + 2 * F.spike_bytes + (size_t)b * F.y_bytes);
-                const double2* bsv = reinterpret_cast<const double2*>(rowp + 2 * F.spike_bytes +
-                                                                      (size_t)A.Bt * F.y_bytes +
-                                                                      (size_t)b * F.base_bytes);
-                const int c = j < nout ? olo + j : (j == nout ? A.sp.to0 : A.sp.to1);
-                const C sum = spike_dot2(sT + (c - F.cmin) * SL, xa, above, sB + (c - F.cmin) * SL, xb, below, g, W);
-                if (live && g == 0) {
-                    const C x = csub(ys[c - F.y0], sum);
-                    if (j < nout) emit(b, k0 + kk, c, x, hasb ? bsv[j] : make_double2(0.0, 0.0));
-                    else xt[(kk * A.Bt + b) * 2 + (j - nout)] = x;
-                }
-            }
+    if (!tr) return;
+    // ---- 2. transfer columns of the chunk rows: tasks (row, to0 / to1), one per 8-lane group
+    const int ntask = m * 2;
+    for (int b = 0; b < nb; ++b) {
+        C xa[8], xb[8];
+        lane_vec(xa, xs + b * 64, above, g, W);
+        lane_vec(xb, xs + (A.Bt + b) * 64, below, g, W);
+        for (int t0 = 0; t0 < ntask; t0 += ngrp) {   // uniform trip count: every lane shuffles
+            const bool live = t0 + grp < ntask;
+            const int task = imin(t0 + grp, ntask - 1);
+            const int kk = task >> 1, c = (task & 1) ? A.sp.to1 : A.sp.to0;
+            const int64_t ro = A.st.fac + (int64_t)(r0 + kk) * bs + (int64_t)c * SL;
+            const C y = live && g == 0 ? yrow<C>(A, b0 + b, r0 + kk)[c] : CT<C>::zero();
+            const C sum = spike_dot2(GT + ro, xa, above, GB + ro, xb, below, g, W);
+            if (live && g == 0) xt[(kk * A.Bt + b) * 2 + (task & 1)] = csub(y, sum);
         }
-        __syncthreads();   // buffer i % 2 is free again; transfer columns complete
-        if (tr)
-            for (int o = tid; o < nr * nb; o += blockDim.x) {
-                const int kk = o / nb, b = o % nb;
-                A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + k0 + kk] =
-                    csub(to_d2(xt[(kk * A.Bt + b) * 2 + 1]), to_d2(xt[(kk * A.Bt + b) * 2]));
-            }
-        if (i + 2 < nbatch) issue(i + 2);
     }
-    if (i < nbatch) {   // a bounded wait gave up: report, let the issued copies land (bounded), leave
-        if (tid == 0) {
-            atomicExch(A.status, 7);
-            for (int j = i; j < nissued; ++j) mbar_wait(&mbar[j & 1], (uint32_t)((j >> 1) & 1));
+    __syncthreads();
+    for (int o = tid; o < m * nb; o += blockDim.x) {
+        const int kk = o / nb, b = o % nb;
+        A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + r0 + kk] =
+            csub(to_d2(xt[(kk * A.Bt + b) * 2 + 1]), to_d2(xt[(kk * A.Bt + b) * 2]));
+    }
+}
+
+// Output columns of many finished strip solves in one launch (grid: chunks x
+// strips x RHS tiles; throughput, not latency): row k of chunk p gets
+// x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p from the strip's chain solution y
+// and its final separator values, the separator row below the chunk its final
+// value; x (plus the base field) goes to the strip's output columns.  Tasks
+// (row, column) go to 8-lane groups, two per group at a time with all their
+// loads in flight together.
+template <typename C>
+__global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __restrict__ GT,
+                                                      const C* __restrict__ GB) {
+    __shared__ C xsv[2][4][64];   // separator above / below, per RHS (Bt <= 4)
+    const int p = blockIdx.x;
+    const int j = O.jlo + blockIdx.y;
+    const int b0 = blockIdx.z * O.Bt;
+    const int nb = imin(O.Bt, O.B - b0);
+    const StripDev st = O.g.strips[j];
+    const int W = st.W, SL = spld(W);
+    const int P = O.g.P, Q1 = imax(P - 1, 1);
+    const int off = st.lo - st.lpml;
+    const int olo = imax(st.olo[O.dir] - off, 0), ohi = imin(st.ohi[O.dir] - off, W - 1);
+    const int nout = ohi - olo + 1;
+    if (nout <= 0) return;
+    const int4 m0 = O.g.cmeta[2 * p];
+    const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
+    const C* Y = reinterpret_cast<const C*>(O.ybuf) + (int64_t)j * O.ystride;
+    const C* XS = reinterpret_cast<const C*>(O.xsep) + (int64_t)j * O.xstride;
+    const bool above = p > 0, below = p < P - 1;
+    const int tid = threadIdx.x, g = tid & 7, grp = tid >> 3, ngrp = blockDim.x >> 3;
+    for (int o = tid; o < 2 * nb * 64; o += blockDim.x) {
+        const int side = o / (nb * 64), b = (o / 64) % nb, c = o % 64;
+        const bool on = (side == 0 ? above : below) && c < W;
+        xsv[side][b][c] = on ? XS[((int64_t)(b0 + b) * Q1 + (side == 0 ? p - 1 : p)) * O.Wmax + c] : CT<C>::zero();
+    }
+    __syncthreads();
+    auto at = [&](int b, int k, int c) { return ((int64_t)(b0 + b) * O.g.Ny + k) * O.g.Nx + off + c; };
+    if (below)   // the separator row below the chunk: its final value
+        for (int o = tid; o < nb * nout; o += blockDim.x) {
+            const int b = o / nout, c = olo + o % nout;
+            double2 v = to_d2(xsv[1][b][c]);
+            if (O.base) v = cadd(v, O.base[at(b, r1, c)]);
+            O.dst[at(b, r1, c)] = v;
         }
-        __syncthreads();
+    const int ntask = m * nout;
+    for (int b = 0; b < nb; ++b) {
+        C xa[8], xb[8];
+        lane_vec(xa, xsv[0][b], above, g, W);
+        lane_vec(xb, xsv[1][b], below, g, W);
+        for (int t0 = 0; t0 < ntask; t0 += 2 * ngrp) {   // uniform trip count: every lane shuffles
+            int kk[2], c[2];
+            bool live[2];
+            C sa[2][8], sb[2][8], y[2];
+            double2 bv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {   // loads of both tasks first
+                const int t = t0 + u * ngrp + grp;
+                live[u] = t < ntask;
+                const int tc = imin(t, ntask - 1);
+                kk[u] = tc / nout;
+                c[u] = olo + tc % nout;
+                const int k = r0 + kk[u];
+                const int64_t ro = st.fac + (int64_t)k * st.bs + (int64_t)c[u] * SL;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int a = g + 8 * i;
+                    sa[u][i] = (above && a < W) ? GT[ro + a] : CT<C>::zero();
+                    sb[u][i] = (below && a < W) ? GB[ro + a] : CT<C>::zero();
+                }
+                y[u] = Y[((int64_t)(b0 + b) * O.g.Ny + k) * O.Wmax + c[u]];
+                bv[u] = O.base ? O.base[at(b, k, c[u])] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                C s0 = CT<C>::zero(), s1 = CT<C>::zero();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    s0 = cfma(sa[u][i], xa[i], s0);
+                    s1 = cfma(sb[u][i], xb[i], s1);
+                }
+                C sum = cadd(s0, s1);
+#pragma unroll
+                for (int o = 1; o <= 4; o <<= 1) {
+                    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+                    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+                }
+                if (live[u] && g == 0) O.dst[at(b, r0 + kk[u], c[u])] = cadd(to_d2(csub(y[u], sum)), bv[u]);
+            }
+        }
     }
 }
 
@@ -1161,6 +1125,7 @@ static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& s
     A.P2U = g.G > 1 ? pool[9] : nullptr;
     A.ybuf = wk.ybuf;
     A.parts = wk.parts;
+    A.xsep = wk.xsep;
     A.counters = wk.counters;
     A.status = wk.status;
     return A;
@@ -1218,26 +1183,33 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     {
-        // the plan the kernel derives, for the longest chunk (zrows bounds its rows):
-        // every chunk's own plan fits in this allocation
-        const int off = st.lo - st.lpml;
-        const int olo = imax(step.olo - off, 0), ohi = imin(step.ohi - off, st.W - 1);
-        const FinishPlan F = finish_plan(st.W, olo, ohi, step.tout != nullptr, step.to0, step.to1,
-                                         step.base != nullptr, g.G > 1, Bt, (int)sizeof(C), wk.zrows, kFinishBudget);
-        static bool fattr = false;
-        if (!fattr) {
-            err = cudaFuncSetAttribute(k_sweep_finish<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kFinishBudget);
+        const XferPlan F = xfer_plan(st.W, g.G > 1, Bt, (int)sizeof(C), wk.zrows, kXferBudget);
+        static bool xattr = false;
+        if (!xattr) {
+            err = cudaFuncSetAttribute(k_sweep_transfer<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kXferBudget);
             if (err != cudaSuccess) return err;
-            fattr = true;
+            xattr = true;
         }
-        if (F.total > kFinishBudget) return cudaErrorInvalidConfiguration;
-        TimedLaunch t(tm, "sweep_finish", s);
-        k_sweep_finish<C><<<dim3(g.P, ntile), 512, F.total, s>>>(A, (const C*)pool[1], (const C*)pool[2],
-                                                                 (const C*)pool[6], (const C*)pool[7]);
+        if (F.total > kXferBudget) return cudaErrorInvalidConfiguration;
+        TimedLaunch t(tm, "sweep_transfer", s);
+        k_sweep_transfer<C><<<dim3(g.P, ntile), 256, F.total, s>>>(A, (const C*)pool[1], (const C*)pool[2],
+                                                                   (const C*)pool[6], (const C*)pool[7]);
     }
     return cudaGetLastError();
 }
+
+template <typename C>
+cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm) {
+    if (O.nstrip <= 0) return cudaSuccess;
+    TimedLaunch t(tm, "sweep_output", s);
+    k_sweep_output<C><<<dim3(O.g.P, O.nstrip, (O.B + O.Bt - 1) / O.Bt), 256, 0, s>>>(O, (const C*)pool[1],
+                                                                                      (const C*)pool[2]);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_outputs<float2>(const OutArgs&, void* const*, cudaStream_t, KernelTimer*);
+template cudaError_t launch_outputs<double2>(const OutArgs&, void* const*, cudaStream_t, KernelTimer*);
 
 template cudaError_t launch_strip_solve<float2>(const Geom&, int, const StripDev&, const SweepStep&,
                                                 const SweepWork&, void* const*, cudaStream_t, KernelTimer*);
