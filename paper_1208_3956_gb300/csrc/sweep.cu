@@ -84,6 +84,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
         if (mbar_try_wait(m, parity)) return true;
     return false;
 }
+// Programmatic dependent launch: the chunk and transfer kernels of consecutive
+// strip solves are launched with programmatic stream serialisation.  A kernel
+// lets its successor's CTAs be scheduled at once (launch_dependents) and does
+// its own independent set-up (barriers, staging factor blocks, tables) before
+// waiting for its predecessor to complete and flush (wait); everything it
+// reads or writes that a predecessor touches comes after that wait.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ------------------------------------------------------------------ args
 struct SweepArgs {
@@ -257,6 +265,7 @@ __device__ __forceinline__ void dual_dispatch(bool dn, bool up, const C* Sd, con
 template <typename C, int NJ, int BT>
 __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_trigger();
     constexpr int LD = 4 * NJ + 2;
     const int W = A.st.W;
     const int esz = (int)sizeof(C);
@@ -414,11 +423,14 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         };
         if (Q > 0 && p == q0) stage_l2(nchunk, nchunk + ngroup);
         if (NG > 1 && p == 0) stage_l2(nchunk + ngroup, nload);
+        pdl_wait();
     } else {
-        // tables and the right-hand sides of the chunk rows (and of the separator
-        // row below), four entries per thread with all their loads in flight together
+        // tables, then (once the previous kernels are done) the right-hand sides of
+        // the chunk rows and of the separator row below, four entries per thread
+        // with all their loads in flight together
         for (int c = tid; c < W; c += ptid) csx[c] = ct[A.st.ctab + c];
         for (int k = r0 + tid; k <= r1; k += ptid) ccy[k - r0] = ct[A.g.ct_cy + k];
+        pdl_wait();
         const int tot = (m + (has_below ? 1 : 0)) * nb * W;
         const int cofs = A.st.lo - A.st.lpml;
         for (int o0 = tid; o0 < tot; o0 += 4 * ptid) {
@@ -877,6 +889,7 @@ __global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __
                                                         const C* __restrict__ GB, const C* __restrict__ GT2,
                                                         const C* __restrict__ GB2) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_trigger();
     const int p = blockIdx.x;
     const int b0 = blockIdx.y * A.Bt;
     const int nb = imin(A.Bt, A.B - b0);
@@ -907,43 +920,57 @@ __global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __
     if (tid == 0) {
         fail = 0;
         mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (F.stage && w == 0 && (above || below)) {   // warp 0 stages step 1
+    const bool stage = F.stage && (above || below);
+    // warp 0 stages step 1: the level-2 spike blocks (factor data) at once on
+    // barrier 0, the chain kernel's rows after the wait on barrier 1
+    if (stage && w == 0) {
         uint32_t total = 0;
         for (int side = 0; side < 2; ++side) {
             if (side == 0 ? !above : !below) continue;
-            const int nup = sg[side] > 0, ndn = sg[side] >= 0 && sg[side] < NG - 1;
-            total += (uint32_t)nb * F.vrow_bytes * (1 + nup + ndn) + F.blk_bytes * (nup + ndn);
+            total += F.blk_bytes * ((sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
         }
         if (l == 0) mbar_expect_tx(&mbar[0], total);
         __syncwarp();
-        for (int ci = l; ci < 2 * (2 + 3 * nb); ci += 32) {
-            const int side = ci / (2 + 3 * nb), k = ci % (2 + 3 * nb);
+        if (l < 4) {
+            const int side = l >> 1, k = l & 1, gi = sg[side];
+            const bool on = side == 0 ? above : below;
+            const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
+            if (on && k == 0 && gi > 0) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[0]);
+            if (on && k == 1 && gi >= 0 && gi < NG - 1) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[0]);
+        }
+    }
+    pdl_wait();
+    if (stage && w == 0) {
+        uint32_t total = 0;
+        for (int side = 0; side < 2; ++side) {
+            if (side == 0 ? !above : !below) continue;
+            total += (uint32_t)nb * F.vrow_bytes * (1 + (sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
+        }
+        if (l == 0) mbar_expect_tx(&mbar[1], total);
+        __syncwarp();
+        for (int ci = l; ci < 2 * 3 * nb; ci += 32) {
+            const int side = ci / (3 * nb), b = (ci / 3) % nb, kind = ci % 3;
             if (side == 0 ? !above : !below) continue;
             const int gi = sg[side];
-            const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
-            const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
-            if (k == 0 && up) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[0]);
-            else if (k == 1 && dn) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[0]);
-            else if (k >= 2) {
-                const int b = (k - 2) / 3, kind = (k - 2) % 3;
-                if (kind == 0) bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[0]);
-                else if (kind == 1 && up)
-                    bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[0]);
-                else if (kind == 2 && dn)
-                    bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[0]);
-            }
+            if (kind == 0) bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[1]);
+            else if (kind == 1 && gi > 0)
+                bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[1]);
+            else if (kind == 2 && gi >= 0 && gi < NG - 1)
+                bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[1]);
         }
     }
     // ---- 1. separator values
-    if (F.stage && (above || below) && !mbar_wait(&mbar[0], 0u)) fail = 1;
+    if (stage && !(mbar_wait(&mbar[0], 0u) && mbar_wait(&mbar[1], 0u))) fail = 1;
     __syncthreads();
     if (fail) {   // a bounded wait gave up: report, let the copies land (bounded), leave
         if (tid == 0) {
             atomicExch(A.status, 7);
             mbar_wait(&mbar[0], 0u);
+            mbar_wait(&mbar[1], 0u);
         }
         __syncthreads();
         return;
@@ -1164,23 +1191,37 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     }
     SweepArgs A = make_args<C>(g, st, step, wk, pool, Bt, ring);
     const int ntile = (wk.B + Bt - 1) / Bt;
+    // both kernels with programmatic stream serialisation (see pdl_wait)
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    auto config = [&](dim3 grid, int nthr, size_t bytes) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(nthr);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = s;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
+        return cfg;
+    };
+    cudaError_t err;
     {
-        TimedLaunch t(tm, "sweep_chunk", s);
-        const dim3 grid(g.P, ntile);
-        const int nthr = 32 * ((st.W + 7) / 8 + 1);   // compute warps + the producer warp
-#define HELM_LAUNCH_CHUNK(NJ)                                                         \
-    (Bt == 1 ? (k_sweep_chunk<C, NJ, 1><<<grid, nthr, smem, s>>>(A), 0)              \
-             : (k_sweep_chunk<C, NJ, 4><<<grid, nthr, smem, s>>>(A), 0))
+        void (*kfn)(SweepArgs) = nullptr;
+#define HELM_CHUNK_FN(NJ) kfn = Bt == 1 ? k_sweep_chunk<C, NJ, 1> : k_sweep_chunk<C, NJ, 4>
         switch (st.nj) {
-            case 8: HELM_LAUNCH_CHUNK(8); break;
-            case 10: HELM_LAUNCH_CHUNK(10); break;
-            case 12: HELM_LAUNCH_CHUNK(12); break;
-            case 14: HELM_LAUNCH_CHUNK(14); break;
-            default: HELM_LAUNCH_CHUNK(16); break;
+            case 8: HELM_CHUNK_FN(8); break;
+            case 10: HELM_CHUNK_FN(10); break;
+            case 12: HELM_CHUNK_FN(12); break;
+            case 14: HELM_CHUNK_FN(14); break;
+            default: HELM_CHUNK_FN(16); break;
         }
-#undef HELM_LAUNCH_CHUNK
+#undef HELM_CHUNK_FN
+        // compute warps + the producer warp
+        const cudaLaunchConfig_t cfg = config(dim3(g.P, ntile), 32 * ((st.W + 7) / 8 + 1), smem);
+        TimedLaunch t(tm, "sweep_chunk", s);
+        err = cudaLaunchKernelEx(&cfg, kfn, A);
     }
-    cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     {
         const XferPlan F = xfer_plan(st.W, g.G > 1, Bt, (int)sizeof(C), wk.zrows, kXferBudget);
@@ -1192,9 +1233,11 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
             xattr = true;
         }
         if (F.total > kXferBudget) return cudaErrorInvalidConfiguration;
+        const cudaLaunchConfig_t cfg = config(dim3(g.P, ntile), 256, F.total);
         TimedLaunch t(tm, "sweep_transfer", s);
-        k_sweep_transfer<C><<<dim3(g.P, ntile), 256, F.total, s>>>(A, (const C*)pool[1], (const C*)pool[2],
-                                                                   (const C*)pool[6], (const C*)pool[7]);
+        err = cudaLaunchKernelEx(&cfg, k_sweep_transfer<C>, A, (const C*)pool[1], (const C*)pool[2],
+                                 (const C*)pool[6], (const C*)pool[7]);
+        if (err != cudaSuccess) return err;
     }
     return cudaGetLastError();
 }
