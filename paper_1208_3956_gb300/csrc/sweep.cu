@@ -26,8 +26,6 @@
 //
 // Every mbarrier wait is bounded; on time-out the kernel records
 // HELM_ETIMEOUT in the status word, drains its copies (bounded) and returns.
-#include <type_traits>
-
 #include "common.cuh"
 #include "internal.h"
 
@@ -243,13 +241,6 @@ __device__ __forceinline__ void dual_rows(const C* __restrict__ Sd, const C* __r
             vu[b] = c;
         }
     }
-}
-template <typename C, int NJ, int BT>
-__device__ __forceinline__ void dual_dispatch(bool dn, bool up, const C* Sd, const C* td, const C* Su,
-                                              const C* tu, int nb, C (&vd)[BT], C (&vu)[BT]) {
-    if (dn && up) dual_rows<C, NJ, BT, true, true>(Sd, td, Su, tu, nb, vd, vu);
-    else if (dn) dual_rows<C, NJ, BT, true, false>(Sd, td, Su, tu, nb, vd, vu);
-    else if (up) dual_rows<C, NJ, BT, false, true>(Sd, td, Su, tu, nb, vd, vu);
 }
 
 // The CTA is ceil(W/8) compute warps plus one producer warp.  The producer's
@@ -490,16 +481,22 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         return true;
     };
     C vd[BT], vu[BT];
+    // The products of a step, vd = Sd-row . td and vu = Su-row . tu, in one
+    // instruction stream for both chains.  A step with one active chain passes
+    // its operands twice and ignores the second result, so that every step of
+    // the kernel runs the same code (fewer copies of it for the instruction cache).
+    auto step2 = [&](const C* Sd, const C* td, const C* Su, const C* tu) {
+        if (compute) dual_rows<C, NJ, BT, true, true>(Sd + lofs, td + vofs, Su + lofs, tu + vofs, nb, vd, vu);
+    };
     const bool own1 = rowok && g == 0;                 // BT = 1: the lane that stores a row
     auto owns = [&](int b) -> bool { return BT == 1 ? own1 : (b < nb && rowok && (b & 3) == g); };
     C* const zl = zb + row;                            // this lane's entry of z-buffer row r0, b = 0
     const int zs = BT * W;                             // z-buffer stride between grid rows
     // ---- forward elimination: both halves while both have rows, then the longer one
-    auto fwd = [&](auto Dc, auto Uc, int s) -> bool {
-        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+    auto fwd = [&](bool D, bool U, int s) -> bool {
         const C* Sd = D ? consume() : nullptr;
         const C* Su = U ? consume() : nullptr;
-        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
         if (D) {   // z_kd, kd = r0+s; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
             const C ck = cmul(csx_r, ccy[s + 1]);
             C* zp = zl + s * zs;
@@ -525,16 +522,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         return finish();
     };
-    {
-        int s = 0;
-        const int nboth = imin(nd, nu);
-        for (; s < nboth; ++s)
-            if (!fwd(std::true_type{}, std::true_type{}, s)) return;
-        for (; s < nd; ++s)
-            if (!fwd(std::true_type{}, std::false_type{}, s)) return;
-        for (; s < nu; ++s)
-            if (!fwd(std::false_type{}, std::true_type{}, s)) return;
-    }
+    for (int s = 0; s < nmx; ++s)
+        if (!fwd(s < nd, s < nu, s)) return;
     // ---- twist row: y_t = Sinv_t (b_t - C_t z_{t-1} - C_{t+1} z_{t+1})
     for (int o = tid; o < nb * W; o += blockDim.x) {
         const int c = o % W, b = o / W;
@@ -546,7 +535,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     __syncthreads();
     {
         const C* St = consume();
-        if (compute) dual_rows<C, NJ, BT, true, false>(St + lofs, vin_d + vofs, St, vin_u, nb, vd, vu);
+        step2(St, vin_d, St, vin_d);
         const C cd = cpl(t), cu = cpl(t + 1);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
@@ -558,8 +547,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!finish()) return;
     }
     // ---- outward back substitution: y_k = z_k - Sinv_k C y_inner
-    auto bwd = [&](auto Dc, auto Uc, int s) -> bool {
-        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+    auto bwd = [&](bool D, bool U, int s) -> bool {
         const int di = nd - 1 - s;              // kd - r0, kd = t-1-s
         const int ui = nd + 1 + s;              // ku - r0, ku = t+1+s
         const C* Sd = nullptr;
@@ -572,7 +560,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             if (D) Sd = consume();
             if (U) Su = consume();
         }
-        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
         if (D) {
             const C ck = cmul(csx_r, ccy[di]);      // C_kd y_kd for row kd-1
             C* zp = zl + di * zs;
@@ -597,16 +585,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         return finish();
     };
-    {
-        int s = 0;
-        const int nboth = imin(nd, nu);
-        for (; s < nboth; ++s)
-            if (!bwd(std::true_type{}, std::true_type{}, s)) return;
-        for (; s < nd; ++s)
-            if (!bwd(std::true_type{}, std::false_type{}, s)) return;
-        for (; s < nu; ++s)
-            if (!bwd(std::false_type{}, std::true_type{}, s)) return;
-    }
+    for (int s = 0; s < nmx; ++s)
+        if (!bwd(s < nd, s < nu, s)) return;
     hold = false;   // the chunk's slots are free from here on: the next refill streams the separator chains
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
@@ -629,9 +609,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     {
         const C* SA = has_below ? consume() : nullptr;
         const C* SB = has_above ? consume() : nullptr;
-        if (compute)
-            dual_dispatch<C, NJ, BT>(has_below, has_above, SA + lofs, vin_d + vofs, SB + lofs, vin_u + vofs, nb,
-                                     vd, vu);
+        step2(has_below ? SA : SB, has_below ? vin_d : vin_u, has_above ? SB : SA, has_above ? vin_u : vin_d);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
@@ -664,11 +642,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     }
     auto zq = [&](int i) -> C* { return zb + i * BT * W; };
     // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
-    auto sep = [&](auto Dc, auto Uc, int qd, int qu) -> bool {
-        constexpr bool D = decltype(Dc)::value, U = decltype(Uc)::value;
+    auto sep = [&](bool D, bool U, int qd, int qu) -> bool {
         const C* Sd = D ? consume() : nullptr;
         const C* Su = U ? consume() : nullptr;
-        if (compute) dual_rows<C, NJ, BT, D, U>(Sd + lofs, vin_d + vofs, Su + lofs, vin_u + vofs, nb, vd, vu);
+        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (owns(b)) {
@@ -694,16 +671,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         const int fd = imax(tq - 1, 0), fu = imax(n - 2 - tq, 0);   // forward steps
         const int bd = tq, bu = n - 1 - tq;                          // back steps
         // forward: z_i = a_i - E_i z_outer, down i = 1..tq-1, up i = n-2..tq+1
-        {
-            int s = 0;
-            const int nboth = imin(fd, fu);
-            for (; s < nboth; ++s)
-                if (!sep(std::true_type{}, std::true_type{}, 1 + s, n - 2 - s)) return false;
-            for (; s < fd; ++s)
-                if (!sep(std::true_type{}, std::false_type{}, 1 + s, 0)) return false;
-            for (; s < fu; ++s)
-                if (!sep(std::false_type{}, std::true_type{}, 0, n - 2 - s)) return false;
-        }
+        for (int s = 0; s < imax(fd, fu); ++s)
+            if (!sep(s < fd, s < fu, 1 + s, n - 2 - s)) return false;
         // twist: x_tq = a_tq - E_tq z_{tq-1} - F_tq z_{tq+1}
         for (int o = tid; o < nb * W; o += blockDim.x) {
             const int c = o % W, b = o / W;
@@ -715,8 +684,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             const bool he = tq >= 1, hf = tq <= n - 2;
             const C* Se = he ? consume() : nullptr;
             const C* Sf = hf ? consume() : nullptr;
-            if (compute)
-                dual_dispatch<C, NJ, BT>(he, hf, Se + lofs, vin_d + vofs, Sf + lofs, vin_u + vofs, nb, vd, vu);
+            step2(he ? Se : Sf, he ? vin_d : vin_u, hf ? Sf : Se, hf ? vin_u : vin_d);
 #pragma unroll
             for (int b = 0; b < BT; ++b)
                 if (b < nb && rowok && (b & 3) == g) {
@@ -731,16 +699,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             if (!finish()) return false;
         }
         // back: x_i = z_i - F_i x_inner, down i = tq-1..0, up i = tq+1..n-1
-        {
-            int s = 0;
-            const int nboth = imin(bd, bu);
-            for (; s < nboth; ++s)
-                if (!sep(std::true_type{}, std::true_type{}, tq - 1 - s, tq + 1 + s)) return false;
-            for (; s < bd; ++s)
-                if (!sep(std::true_type{}, std::false_type{}, tq - 1 - s, 0)) return false;
-            for (; s < bu; ++s)
-                if (!sep(std::false_type{}, std::true_type{}, 0, tq + 1 + s)) return false;
-        }
+        for (int s = 0; s < imax(bd, bu); ++s)
+            if (!sep(s < bd, s < bu, tq - 1 - s, tq + 1 + s)) return false;
         return true;
     };
     // right-hand sides a_i = sum of the parts of separator slot(i), two entries
@@ -773,41 +733,39 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         __syncthreads();
     };
-    // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at zero
-    load_a(n1, 1);
-    if (!chain(n1)) return;
-    for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-        yrow<C>(A, b0 + b, A.g.r1[q0 + i])[c] = zb[(i * BT + b) * W + c];
-    }
-    if (NG == 1) return;
-    // ---- the group's parts of the level-2 right-hand sides:
-    //   -P2L_{gi} y(last) to the separator below, -P2U_{gi-1} y(first) to the one above
-    for (int o = tid; o < nb * W; o += blockDim.x) {
-        const int c = o % W, b = o / W;
-        if (dn2) vin_d[b * 64 + c] = zq(n1 - 1)[b * W + c];
-        if (up2) vin_u[b * 64 + c] = zq(0)[b * W + c];
-    }
-    __syncthreads();
-    {
-        const C* SL = dn2 ? consume() : nullptr;
-        const C* SU = up2 ? consume() : nullptr;
-        if (compute) dual_dispatch<C, NJ, BT>(dn2, up2, SL + lofs, vin_d + vofs, SU + lofs, vin_u + vofs, nb, vd, vu);
+    // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at
+    //      zero; level 2: the level-2 separators (one code path for both levels)
+    for (int lvl = 1; lvl <= 2; ++lvl) {
+        const int n = lvl == 1 ? n1 : n2;
+        load_a(n, lvl);
+        if (!chain(n)) return;
+        for (int o = tid; o < n * nb * W; o += blockDim.x) {
+            const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+            yrow<C>(A, b0 + b, A.g.r1[lvl == 1 ? q0 + i : A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
+        }
+        if (lvl == 2 || NG == 1) return;
+        // the group's parts of the level-2 right-hand sides:
+        //   -P2L_{gi} y(last) to the separator below, -P2U_{gi-1} y(first) to the one above
+        for (int o = tid; o < nb * W; o += blockDim.x) {
+            const int c = o % W, b = o / W;
+            if (dn2) vin_d[b * 64 + c] = zq(n1 - 1)[b * W + c];
+            if (up2) vin_u[b * 64 + c] = zq(0)[b * W + c];
+        }
+        __syncthreads();
+        {
+            const C* SL = dn2 ? consume() : nullptr;
+            const C* SU = up2 ? consume() : nullptr;
+            step2(dn2 ? SL : SU, dn2 ? vin_d : vin_u, up2 ? SU : SL, up2 ? vin_u : vin_d);
 #pragma unroll
-        for (int b = 0; b < BT; ++b)
-            if (b < nb && rowok && (b & 3) == g) {
-                if (dn2) parts[pidx(b, q1, 2) + row] = cneg(vd[b]);
-                if (up2) parts[pidx(b, q0 - 1, 3) + row] = cneg(vu[b]);
-            }
-        if (!finish()) return;
-    }
-    // ---- arrival: the last group to finish solves the level-2 system
-    if (!arrive(&cnt[NG], NG - 1)) return;
-    load_a(n2, 2);
-    if (!chain(n2)) return;
-    for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
-        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-        yrow<C>(A, b0 + b, A.g.r1[A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
+            for (int b = 0; b < BT; ++b)
+                if (b < nb && rowok && (b & 3) == g) {
+                    if (dn2) parts[pidx(b, q1, 2) + row] = cneg(vd[b]);
+                    if (up2) parts[pidx(b, q0 - 1, 3) + row] = cneg(vu[b]);
+                }
+            if (!finish()) return;
+        }
+        // arrival: the last group to finish solves the level-2 system
+        if (!arrive(&cnt[NG], NG - 1)) return;
     }
 }
 
