@@ -337,12 +337,35 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         issued = lim;
     };
+    bool late = false;   // this thread's bounded wait gave up (reduced over the CTA in finish)
     auto consume = [&]() -> const C* {
         const C* S = reinterpret_cast<const C*>(slots + (size_t)cslot * sb);
-        if (compute && !mbar_wait(&mbar[cslot], cpar)) flags[1] = 1;
+        if (compute && !mbar_wait(&mbar[cslot], cpar)) late = true;
         ++consumed;
         if (++cslot == ring) { cslot = 0; cpar ^= 1u; }
         return S;
+    };
+    // the next one or two loads of the sequence, their barriers polled together
+    auto consume2 = [&](bool two, const C*& S1, const C*& S2) {
+        const int s1 = cslot;
+        const uint32_t p1 = cpar;
+        int s2 = cslot + 1;
+        uint32_t p2 = cpar;
+        if (s2 == ring) { s2 = 0; p2 ^= 1u; }
+        S1 = reinterpret_cast<const C*>(slots + (size_t)s1 * sb);
+        S2 = two ? reinterpret_cast<const C*>(slots + (size_t)s2 * sb) : S1;
+        if (compute) {
+            bool ok1 = false, ok2 = !two;
+            for (uint32_t it = 0; it < kWaitLimit && !(ok1 && ok2); ++it) {
+                if (!ok1) ok1 = mbar_try_wait(&mbar[s1], p1);
+                if (!ok2) ok2 = mbar_try_wait(&mbar[s2], p2);
+            }
+            if (!(ok1 && ok2)) late = true;
+        }
+        const int k = two ? 2 : 1;
+        consumed += k;
+        cslot += k;
+        if (cslot >= ring) { cslot -= ring; cpar ^= 1u; }
     };
     // producer warp, after a barrier: keep kAhead loads in flight, each into a
     // slot whose previous load has been consumed (and is no longer held)
@@ -357,11 +380,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     };
     auto abort_wait = [&]() {   // a bounded wait gave up: report, let the copies land, leave
         if (producer) atomicExch(A.status, 7);
-        land(consumed - 1);
+        land(consumed - 2);   // the step's one or two loads and every later copy
         __syncthreads();
     };
     if (producer) {
-        flags[1] = 0;
         for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
@@ -473,8 +495,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     auto zr = [&](int k) -> C* { return zb + (k - r0) * BT * W; };   // row k, b = 0
     auto cpl = [&](int k) -> C { return cmul(csx_r, ccy[k - r0]); }; // C_k at this lane's row
     auto finish = [&]() -> bool {
-        __syncthreads();
-        if (flags[1]) { abort_wait(); return false; }
+        if (__syncthreads_or(late)) { abort_wait(); return false; }
         if (pwarp) refill();
         C* x = vin_d; vin_d = vout_d; vout_d = x;
         x = vin_u; vin_u = vout_u; vout_u = x;
@@ -488,15 +509,24 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     auto step2 = [&](const C* Sd, const C* td, const C* Su, const C* tu) {
         if (compute) dual_rows<C, NJ, BT, true, true>(Sd + lofs, td + vofs, Su + lofs, tu + vofs, nb, vd, vu);
     };
+    // the blocks of a step with chains a (first in load order) and b, either may be off
+    auto consume_ab = [&](bool a, bool b, const C*& Sa, const C*& Sb) {
+        Sa = Sb = nullptr;
+        if (!a && !b) return;
+        const C *S1, *S2;
+        consume2(a && b, S1, S2);
+        Sa = a ? S1 : nullptr;
+        Sb = b ? (a ? S2 : S1) : nullptr;
+    };
     const bool own1 = rowok && g == 0;                 // BT = 1: the lane that stores a row
     auto owns = [&](int b) -> bool { return BT == 1 ? own1 : (b < nb && rowok && (b & 3) == g); };
     C* const zl = zb + row;                            // this lane's entry of z-buffer row r0, b = 0
     const int zs = BT * W;                             // z-buffer stride between grid rows
     // ---- forward elimination: both halves while both have rows, then the longer one
     auto fwd = [&](bool D, bool U, int s) -> bool {
-        const C* Sd = D ? consume() : nullptr;
-        const C* Su = U ? consume() : nullptr;
-        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
+        const C *S1, *S2;
+        consume2(D && U, S1, S2);   // in order: the down block, then the up block
+        step2(S1, D ? vin_d : vin_u, S2, U ? vin_u : vin_d);
         if (D) {   // z_kd, kd = r0+s; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
             const C ck = cmul(csx_r, ccy[s + 1]);
             C* zp = zl + s * zs;
@@ -557,8 +587,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             if (D) Sd = reinterpret_cast<const C*>(slots + (size_t)(di + imin(di, nu)) * sb);
             if (U) { const int i = m - 1 - ui; Su = reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb); }
         } else {
-            if (D) Sd = consume();
-            if (U) Su = consume();
+            const C *S1, *S2;
+            consume2(D && U, S1, S2);
+            Sd = D ? S1 : nullptr;
+            Su = U ? (D ? S2 : S1) : nullptr;
         }
         step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
         if (D) {
@@ -607,8 +639,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     }
     __syncthreads();
     {
-        const C* SA = has_below ? consume() : nullptr;
-        const C* SB = has_above ? consume() : nullptr;
+        const C *SA, *SB;
+        consume_ab(has_below, has_above, SA, SB);
         step2(has_below ? SA : SB, has_below ? vin_d : vin_u, has_above ? SB : SA, has_above ? vin_u : vin_d);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
@@ -643,9 +675,9 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     auto zq = [&](int i) -> C* { return zb + i * BT * W; };
     // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
     auto sep = [&](bool D, bool U, int qd, int qu) -> bool {
-        const C* Sd = D ? consume() : nullptr;
-        const C* Su = U ? consume() : nullptr;
-        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
+        const C *S1, *S2;
+        consume2(D && U, S1, S2);
+        step2(S1, D ? vin_d : vin_u, S2, U ? vin_u : vin_d);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (owns(b)) {
@@ -682,8 +714,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         __syncthreads();
         {
             const bool he = tq >= 1, hf = tq <= n - 2;
-            const C* Se = he ? consume() : nullptr;
-            const C* Sf = hf ? consume() : nullptr;
+            const C *Se, *Sf;
+            consume_ab(he, hf, Se, Sf);
             step2(he ? Se : Sf, he ? vin_d : vin_u, hf ? Sf : Se, hf ? vin_u : vin_d);
 #pragma unroll
             for (int b = 0; b < BT; ++b)
@@ -753,8 +785,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         __syncthreads();
         {
-            const C* SL = dn2 ? consume() : nullptr;
-            const C* SU = up2 ? consume() : nullptr;
+            const C *SL, *SU;
+            consume_ab(dn2, up2, SL, SU);
             step2(dn2 ? SL : SU, dn2 ? vin_d : vin_u, up2 ? SU : SL, up2 ? vin_u : vin_d);
 #pragma unroll
             for (int b = 0; b < BT; ++b)
