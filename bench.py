@@ -6,6 +6,9 @@ source per GPU) through the library, with factors and inputs resident on the
 device.  Metric: Mdof*RHS/s = padded unknowns x right-hand sides / solve time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+
+With the mixed-precision sweep (default) the line also carries "fp64_sweep": the same
+solve with complex128 factors and sweep (FP64 GMRES), and the mixed / FP64 ratio.
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 
 Multi-GPU (torchrun, one process per GPU): every rank solves its own source
@@ -250,6 +253,27 @@ def run_ours(args):
     stats = solver.kernel_stats()
     solver.set_timing(False)
 
+    # the same solve with the complex128 sweep (FP64 factors, FP64 GMRES), same GPU code
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64:
+        s64 = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "fp64", chunks=args.chunks)
+        s64.set_stream(stream.cuda_stream)
+        s64.factor()
+        s64.solve(f_dev, tol=1e-6, restart=20, maxit=200)
+        k64 = max(2, args.steps // 3)
+        e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e64[0].record()
+        for _ in range(k64):
+            _, info64 = s64.solve(f_dev, tol=1e-6, restart=20, maxit=200)
+        e64[1].record()
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(e64[0].elapsed_time(e64[1]) / k64, world)
+        v64 = ndof * nrhs * world / (t64 * 1e-3) / 1e6
+        fp64 = {"value": v64, "unit": "Mdof*RHS/s", "ms_per_step": t64, "steps": k64,
+                "iters": [i["iters"] for i in info64], "rel_res": max(i["rel_res"] for i in info64),
+                "mixed_over_fp64": value / v64}
+        s64.close()
+
     line = None
     if rank == 0:
         peaks = load_peaks()
@@ -292,6 +316,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(f_host.nbytes)},
             "clocks": clk.summary(),
         }
+        if fp64:
+            line["fp64_sweep"] = fp64
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_oracle_solve_time(max_seconds=40.0, steps=1)
         line["cpu_baseline"] = {"value": r["ndof"] / r["t_solve"] / 1e6, "unit": "Mdof*RHS/s", "cores": 1,
@@ -317,6 +343,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--chunks", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the complex128-sweep comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

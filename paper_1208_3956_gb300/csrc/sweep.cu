@@ -221,7 +221,7 @@ __device__ __forceinline__ void dual_rows(const C* __restrict__ Sd, const C* __r
     if (U) load_row<C, NJ>(su, Su);
 #pragma unroll
     for (int b = 0; b < BT; ++b) {
-        if (b < nb) {
+        if (BT == 1 || b < nb) {   // nb >= 1: no test for a single right-hand side
             C xd[NJ], xu[NJ];
             if (D) load_row<C, NJ>(xd, td + b * 64);
             if (U) load_row<C, NJ>(xu, tu + b * 64);
@@ -255,6 +255,7 @@ __device__ __forceinline__ void dual_rows(const C* __restrict__ Sd, const C* __r
 // wait for their copies to land and exit.
 template <typename C, int NJ, int BT>
 __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
+    using R = typename CT<C>::R;
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_trigger();
     constexpr int LD = 4 * NJ + 2;
@@ -522,38 +523,56 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     auto owns = [&](int b) -> bool { return BT == 1 ? own1 : (b < nb && rowok && (b & 3) == g); };
     C* const zl = zb + row;                            // this lane's entry of z-buffer row r0, b = 0
     const int zs = BT * W;                             // z-buffer stride between grid rows
-    // ---- forward elimination: both halves while both have rows, then the longer one
-    auto fwd = [&](bool D, bool U, int s) -> bool {
-        const C *S1, *S2;
-        consume2(D && U, S1, S2);   // in order: the down block, then the up block
+    // One chain step of both halves, one code path for the forward, back and separator
+    // steps.  S1 is the first active half's block, S2 the second's (S1 again when only
+    // one half is active).  Per half h (this lane's row, RHS b), with v the product:
+    //   out = az * z[h] + sv * v,   z[h] <- out,   and, if wv[h],
+    //   vout[h] = ez * zn[h] + fc * ck[h] * out
+    // forward (az 0, sv 1, ez 1, fc -1): z = v, next input b_next - C z;
+    // back (az 1, sv -1, ez 0, fc 1): y = z - v, C y to the next row;
+    // separator (as back with ck = 1): x = z - v, x to the next separator.
+    // The owner lanes read z and zn before the product, off the critical path.
+    auto gstep = [&](bool D, bool U, const C* S1, const C* S2, C* zd, C* zu, const C* znd, const C* znu, C ckd,
+                     C cku, bool wvd, bool wvu, R az, R sv, R ez, R fc) -> bool {
+        C pzd[BT], pzu[BT], pnd[BT], pnu[BT];
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            const bool ob = owns(b);
+            pzd[b] = (ob && D && az != (R)0) ? zd[b * W] : CT<C>::zero();
+            pzu[b] = (ob && U && az != (R)0) ? zu[b * W] : CT<C>::zero();
+            pnd[b] = (ob && D && wvd && ez != (R)0) ? znd[b * W] : CT<C>::zero();
+            pnu[b] = (ob && U && wvu && ez != (R)0) ? znu[b * W] : CT<C>::zero();
+        }
         step2(S1, D ? vin_d : vin_u, S2, U ? vin_u : vin_d);
-        if (D) {   // z_kd, kd = r0+s; next down input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
-            const C ck = cmul(csx_r, ccy[s + 1]);
-            C* zp = zl + s * zs;
-            const bool more = r0 + s + 1 < t;
 #pragma unroll
-            for (int b = 0; b < BT; ++b)
-                if (owns(b)) {
-                    zp[b * W] = vd[b];
-                    if (more) vout_d[b * 64 + row] = csub(zp[zs + b * W], cmul(ck, vd[b]));
+        for (int b = 0; b < BT; ++b)
+            if (owns(b)) {
+                if (D) {
+                    const C out = cadd(cscale(pzd[b], az), cscale(vd[b], sv));
+                    zd[b * W] = out;
+                    if (wvd) vout_d[b * 64 + row] = cadd(cscale(pnd[b], ez), cscale(cmul(ckd, out), fc));
                 }
-        }
-        if (U) {   // z_ku, ku = r1-1-s; next up input b_{ku-1} - C_ku z_ku (if ku-1 > t)
-            const int ui = m - 1 - s;                      // ku - r0
-            const C ck = cmul(csx_r, ccy[ui]);
-            C* zp = zl + ui * zs;
-            const bool more = r1 - 2 - s > t;
-#pragma unroll
-            for (int b = 0; b < BT; ++b)
-                if (owns(b)) {
-                    zp[b * W] = vu[b];
-                    if (more) vout_u[b * 64 + row] = csub(zp[-zs + b * W], cmul(ck, vu[b]));
+                if (U) {
+                    const C out = cadd(cscale(pzu[b], az), cscale(vu[b], sv));
+                    zu[b * W] = out;
+                    if (wvu) vout_u[b * 64 + row] = cadd(cscale(pnu[b], ez), cscale(cmul(cku, out), fc));
                 }
-        }
+            }
         return finish();
     };
-    for (int s = 0; s < nmx; ++s)
-        if (!fwd(s < nd, s < nu, s)) return;
+    // ---- forward elimination: both halves while both have rows, then the longer one
+    //   down: z_kd, kd = r0+s; next input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
+    //   up:   z_ku, ku = r1-1-s; next input b_{ku-1} - C_ku z_ku (if ku-1 > t)
+    for (int s = 0; s < nmx; ++s) {
+        const bool D = s < nd, U = s < nu;
+        const int ui = m - 1 - s;                          // ku - r0
+        const C *S1, *S2;
+        consume2(D && U, S1, S2);                          // in order: the down block, then the up block
+        if (!gstep(D, U, S1, S2, zl + s * zs, zl + ui * zs, zl + (s + 1) * zs, zl + (ui - 1) * zs,
+                   cmul(csx_r, ccy[s + 1]), cmul(csx_r, ccy[ui]), r0 + s + 1 < t, r1 - 2 - s > t, (R)0, (R)1,
+                   (R)1, (R)-1))
+            return;
+    }
     // ---- twist row: y_t = Sinv_t (b_t - C_t z_{t-1} - C_{t+1} z_{t+1})
     for (int o = tid; o < nb * W; o += blockDim.x) {
         const int c = o % W, b = o / W;
@@ -577,48 +596,26 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!finish()) return;
     }
     // ---- outward back substitution: y_k = z_k - Sinv_k C y_inner
-    auto bwd = [&](bool D, bool U, int s) -> bool {
-        const int di = nd - 1 - s;              // kd - r0, kd = t-1-s
-        const int ui = nd + 1 + s;              // ku - r0, ku = t+1+s
-        const C* Sd = nullptr;
-        const C* Su = nullptr;
+    //   down: kd = t-1-s, C_kd y_kd to row kd-1;  up: ku = t+1+s, C_{ku+1} y_ku to row ku+1
+    for (int s = 0; s < nmx; ++s) {
+        const bool D = s < nd, U = s < nu;
+        const int di = nd - 1 - s;              // kd - r0
+        const int ui = nd + 1 + s;              // ku - r0
+        const C *S1, *S2;
         if (resident) {
             // forward position: down row r0+i at i + min(i, nu); up row r1-1-i at min(i+1, nd) + i
-            if (D) Sd = reinterpret_cast<const C*>(slots + (size_t)(di + imin(di, nu)) * sb);
-            if (U) { const int i = m - 1 - ui; Su = reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb); }
+            const C* Sd = D ? reinterpret_cast<const C*>(slots + (size_t)(di + imin(di, nu)) * sb) : nullptr;
+            const int i = m - 1 - ui;
+            const C* Su = U ? reinterpret_cast<const C*>(slots + (size_t)(imin(i + 1, nd) + i) * sb) : nullptr;
+            S1 = D ? Sd : Su;
+            S2 = (D && U) ? Su : S1;
         } else {
-            const C *S1, *S2;
             consume2(D && U, S1, S2);
-            Sd = D ? S1 : nullptr;
-            Su = U ? (D ? S2 : S1) : nullptr;
         }
-        step2(D ? Sd : Su, D ? vin_d : vin_u, U ? Su : Sd, U ? vin_u : vin_d);
-        if (D) {
-            const C ck = cmul(csx_r, ccy[di]);      // C_kd y_kd for row kd-1
-            C* zp = zl + di * zs;
-#pragma unroll
-            for (int b = 0; b < BT; ++b)
-                if (owns(b)) {
-                    const C y = csub(zp[b * W], vd[b]);
-                    zp[b * W] = y;
-                    vout_d[b * 64 + row] = cmul(ck, y);
-                }
-        }
-        if (U) {
-            const C ck = cmul(csx_r, ccy[ui + 1]);  // C_{ku+1} y_ku for row ku+1
-            C* zp = zl + ui * zs;
-#pragma unroll
-            for (int b = 0; b < BT; ++b)
-                if (owns(b)) {
-                    const C y = csub(zp[b * W], vu[b]);
-                    zp[b * W] = y;
-                    vout_u[b * 64 + row] = cmul(ck, y);
-                }
-        }
-        return finish();
-    };
-    for (int s = 0; s < nmx; ++s)
-        if (!bwd(s < nd, s < nu, s)) return;
+        if (!gstep(D, U, S1, S2, zl + di * zs, zl + ui * zs, nullptr, nullptr, cmul(csx_r, ccy[D ? di : 0]),
+                   cmul(csx_r, ccy[U ? ui + 1 : 0]), true, true, (R)1, (R)-1, (R)0, (R)1))
+            return;
+    }
     hold = false;   // the chunk's slots are free from here on: the next refill streams the separator chains
     // ---- chunk solution to global memory
     for (int o = tid; o < m * nb * W; o += blockDim.x) {
@@ -677,24 +674,9 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     auto sep = [&](bool D, bool U, int qd, int qu) -> bool {
         const C *S1, *S2;
         consume2(D && U, S1, S2);
-        step2(S1, D ? vin_d : vin_u, S2, U ? vin_u : vin_d);
-#pragma unroll
-        for (int b = 0; b < BT; ++b)
-            if (owns(b)) {
-                if (D) {
-                    C* zp = zq(qd) + b * W + row;
-                    const C x = csub(*zp, vd[b]);
-                    *zp = x;
-                    vout_d[b * 64 + row] = x;
-                }
-                if (U) {
-                    C* zp = zq(qu) + b * W + row;
-                    const C x = csub(*zp, vu[b]);
-                    *zp = x;
-                    vout_u[b * 64 + row] = x;
-                }
-            }
-        return finish();
+        const C one = CT<C>::from(make_double2(1.0, 0.0));
+        return gstep(D, U, S1, S2, zq(qd) + row, zq(qu) + row, nullptr, nullptr, one, one, true, true, (R)1, (R)-1,
+                     (R)0, (R)1);
     };
     // Twisted solve of n separators in the load order of chain_order; a_i is in
     // zq(i), a_0 / a_{n-1} in vin_d / vin_u.
