@@ -136,7 +136,7 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     uint32_t o = 0;
     s.slots = o; o += ring * slot_bytes;
     s.zb = o; o += ((uint32_t)zrows * Bt * W * esz + 15u) & ~15u;
-    s.tv = o; o += 5u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs
+    s.tv = o; o += 7u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs, parts inputs
     s.cx = o; o += 64u * esz;
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
     s.order = o; o += ((uint32_t)(6 * zrows + 8) * 4 + 15u) & ~15u;   // load order table
@@ -271,6 +271,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     C* vout_d = v0 + 2 * BT * 64;
     C* vout_u = v0 + 3 * BT * 64;
     C* rsep = v0 + 4 * BT * 64;                      // S r on the separator row below the chunk
+    // inputs of the steps after a chain (separator right-hand-side parts), written by
+    // the owner lanes of each half's last step: pv_d from the down half, pv_u from the up half
+    C* pv_d = v0 + 5 * BT * 64;
+    C* pv_u = v0 + 6 * BT * 64;
     C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
     C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
     int* order = reinterpret_cast<int*>(smem + L.order);
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
-    for (int o = tid; o < 5 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
+    for (int o = tid; o < 7 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
     __syncthreads();   // barriers initialised, vectors zeroed
     const C* ct = ctab<C>(A.g);
     if (producer) {
@@ -439,16 +443,26 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (NG > 1 && p == 0) stage_l2(nchunk + ngroup, nload);
         pdl_wait();
     } else {
-        // tables, then (once the previous kernels are done) the right-hand sides of
-        // the chunk rows and of the separator row below, four entries per thread
-        // with all their loads in flight together
+        // tables and the source part of the right-hand sides S^(j) r of the chunk
+        // rows and of the separator row below (the source field is complete before
+        // the sweep starts), four entries per thread with all their loads in flight;
+        // then, once the previous strip solve is done, its transfer on two columns
         for (int c = tid; c < W; c += ptid) csx[c] = ct[A.st.ctab + c];
         for (int k = r0 + tid; k <= r1; k += ptid) ccy[k - r0] = ct[A.g.ct_cy + k];
-        pdl_wait();
-        const int tot = (m + (has_below ? 1 : 0)) * nb * W;
+        const int nrow = m + (has_below ? 1 : 0);
+        const int tot = nrow * nb * W;
         const int cofs = A.st.lo - A.st.lpml;
+        auto put = [&](int r, int b, int c, const C& v) {   // chain inputs and the separator row
+            if (r < m) {
+                zb[(r * BT + b) * W + c] = v;
+                if (r == 0 && nd > 0) vin_d[b * 64 + c] = v;       // down chain starts at r0
+                if (r == m - 1 && nu > 0) vin_u[b * 64 + c] = v;   // up chain starts at r1-1
+            } else {
+                rsep[b * 64 + c] = v;
+            }
+        };
         for (int o0 = tid; o0 < tot; o0 += 4 * ptid) {
-            double2 sv[4], tv2[4];
+            double2 sv[4];
             C sx[4], sy[4];
             int cc[4], bb[4], rr[4];
 #pragma unroll
@@ -459,27 +473,29 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 rr[u] = o / (W * nb);
                 const int64_t rowi = (int64_t)(b0 + bb[u]) * A.g.Ny + r0 + rr[u];
                 sv[u] = __ldg(A.sp.src + rowi * A.g.Nx + imin(imax(cofs + cc[u], 0), A.g.Nx - 1));
-                tv2[u] = A.sp.tin ? __ldg(A.sp.tin + rowi) : make_double2(0.0, 0.0);
                 sx[u] = ct[A.st.ctab + cc[u]];
                 sy[u] = ct[A.g.ct_sy + r0 + rr[u]];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (o0 + u * ptid >= tot) continue;
-                const int c = cc[u], b = bb[u], r = rr[u], gc = cofs + c;
-                double2 f = (gc >= A.sp.mlo && gc <= A.sp.mhi) ? sv[u] : make_double2(0.0, 0.0);
-                if (A.sp.tin && (gc == A.sp.t0 || gc == A.sp.t0 + 1)) {
-                    f.x = fma(A.sp.tcoef, tv2[u].x, f.x);
-                    f.y = fma(A.sp.tcoef, tv2[u].y, f.y);
-                }
-                const C v = cmul(CT<C>::from(f), cmul(sx[u], sy[u]));   // S^(j) r
-                if (r < m) {
-                    zb[(r * BT + b) * W + c] = v;
-                    if (r == 0 && nd > 0) vin_d[b * 64 + c] = v;       // down chain starts at r0
-                    if (r == m - 1 && nu > 0) vin_u[b * 64 + c] = v;   // up chain starts at r1-1
-                } else {
-                    rsep[b * 64 + c] = v;
-                }
+                const int gc = cofs + cc[u];
+                const double2 f = (gc >= A.sp.mlo && gc <= A.sp.mhi) ? sv[u] : make_double2(0.0, 0.0);
+                put(rr[u], bb[u], cc[u], cmul(CT<C>::from(f), cmul(sx[u], sy[u])));
+            }
+        }
+        pdl_wait();
+        if (A.sp.tin) {
+            asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");   // compute warps: source part written
+            for (int o = tid; o < nrow * nb * 2; o += ptid) {
+                const int i = o & 1, b = (o >> 1) % nb, r = (o >> 1) / nb;
+                const int c = A.sp.t0 + i - cofs;
+                if (c < 0 || c >= W) continue;
+                const double2 tv = A.sp.tin[(int64_t)(b0 + b) * A.g.Ny + r0 + r];
+                const C add = cmul(CT<C>::from(make_double2(A.sp.tcoef * tv.x, A.sp.tcoef * tv.y)),
+                                   cmul(ct[A.st.ctab + c], ct[A.g.ct_sy + r0 + r]));
+                const C* cur = r < m ? &zb[(r * BT + b) * W + c] : &rsep[b * 64 + c];
+                put(r, b, c, cadd(*cur, add));
             }
         }
     }
@@ -532,8 +548,11 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     // back (az 1, sv -1, ez 0, fc 1): y = z - v, C y to the next row;
     // separator (as back with ck = 1): x = z - v, x to the next separator.
     // The owner lanes read z and zn before the product, off the critical path.
+    //   the last step of a half also leaves ps * vout (plus pbase for the up half)
+    //   in pv_d / pv_u when pd / pu is set
     auto gstep = [&](bool D, bool U, const C* S1, const C* S2, C* zd, C* zu, const C* znd, const C* znu, C ckd,
-                     C cku, bool wvd, bool wvu, R az, R sv, R ez, R fc) -> bool {
+                     C cku, bool wvd, bool wvu, R az, R sv, R ez, R fc, bool pd = false, bool pu = false,
+                     const C* pbase = nullptr, R ps = (R)1) -> bool {
         C pzd[BT], pzu[BT], pnd[BT], pnu[BT];
 #pragma unroll
         for (int b = 0; b < BT; ++b) {
@@ -550,12 +569,16 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 if (D) {
                     const C out = cadd(cscale(pzd[b], az), cscale(vd[b], sv));
                     zd[b * W] = out;
-                    if (wvd) vout_d[b * 64 + row] = cadd(cscale(pnd[b], ez), cscale(cmul(ckd, out), fc));
+                    const C vo = cadd(cscale(pnd[b], ez), cscale(cmul(ckd, out), fc));
+                    if (wvd) vout_d[b * 64 + row] = vo;
+                    if (pd) pv_d[b * 64 + row] = cscale(vo, ps);
                 }
                 if (U) {
                     const C out = cadd(cscale(pzu[b], az), cscale(vu[b], sv));
                     zu[b * W] = out;
-                    if (wvu) vout_u[b * 64 + row] = cadd(cscale(pnu[b], ez), cscale(cmul(cku, out), fc));
+                    const C vo = cadd(cscale(pnu[b], ez), cscale(cmul(cku, out), fc));
+                    if (wvu) vout_u[b * 64 + row] = vo;
+                    if (pu) pv_u[b * 64 + row] = cadd(pbase ? pbase[b * 64 + row] : CT<C>::zero(), cscale(vo, ps));
                 }
             }
         return finish();
@@ -592,6 +615,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 zr(t)[b * W + row] = vd[b];
                 vout_d[b * 64 + row] = cmul(cd, vd[b]);   // C_t y_t for row t-1
                 vout_u[b * 64 + row] = cmul(cu, vd[b]);   // C_{t+1} y_t for row t+1
+                if (nd == 0) pv_d[b * 64 + row] = cneg(cmul(cd, vd[b]));              // t = r0
+                if (nu == 0) pv_u[b * 64 + row] = csub(rsep[b * 64 + row], cmul(cu, vd[b]));   // t = r1-1
             }
         if (!finish()) return;
     }
@@ -612,8 +637,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         } else {
             consume2(D && U, S1, S2);
         }
+        // the last steps leave the parts inputs: -C_r0 y(first) and S r(r1) - C_r1 y(last)
         if (!gstep(D, U, S1, S2, zl + di * zs, zl + ui * zs, nullptr, nullptr, cmul(csx_r, ccy[D ? di : 0]),
-                   cmul(csx_r, ccy[U ? ui + 1 : 0]), true, true, (R)1, (R)-1, (R)0, (R)1))
+                   cmul(csx_r, ccy[U ? ui + 1 : 0]), true, true, (R)1, (R)-1, (R)0, (R)1, s == nd - 1, s == nu - 1,
+                   rsep, (R)-1))
             return;
     }
     hold = false;   // the chunk's slots are free from here on: the next refill streams the separator chains
@@ -628,17 +655,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     // ---- separator right-hand-side parts, both in one step:
     //   down chain: A_p     = Rinv_p     (b_s - C_s y(last)),   s = r1      (separator below)
     //   up chain:   B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first),     s' = r0 - 1 (separator above)
-    for (int o = tid; o < nb * W; o += blockDim.x) {
-        const int c = o % W, b = o / W;
-        if (has_below)
-            vin_d[b * 64 + c] = csub(rsep[b * 64 + c], cmul(cmul(csx[c], ccy[r1 - r0]), zr(r1 - 1)[b * W + c]));
-        if (has_above) vin_u[b * 64 + c] = cneg(cmul(cmul(csx[c], ccy[0]), zr(r0)[b * W + c]));
-    }
-    __syncthreads();
-    {
+    {   // inputs left by the last back steps (or the twist): pv_u = S r(r1) - C_r1 y(last), pv_d = -C_r0 y(first)
         const C *SA, *SB;
         consume_ab(has_below, has_above, SA, SB);
-        step2(has_below ? SA : SB, has_below ? vin_d : vin_u, has_above ? SB : SA, has_above ? vin_u : vin_d);
+        step2(has_below ? SA : SB, has_below ? pv_u : pv_d, has_above ? SB : SA, has_above ? pv_d : pv_u);
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
@@ -671,12 +691,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     }
     auto zq = [&](int i) -> C* { return zb + i * BT * W; };
     // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
-    auto sep = [&](bool D, bool U, int qd, int qu) -> bool {
+    auto sep = [&](bool D, bool U, int qd, int qu, bool pd = false, bool pu = false) -> bool {
         const C *S1, *S2;
         consume2(D && U, S1, S2);
         const C one = CT<C>::from(make_double2(1.0, 0.0));
         return gstep(D, U, S1, S2, zq(qd) + row, zq(qu) + row, nullptr, nullptr, one, one, true, true, (R)1, (R)-1,
-                     (R)0, (R)1);
+                     (R)0, (R)1, pd, pu);
     };
     // Twisted solve of n separators in the load order of chain_order; a_i is in
     // zq(i), a_0 / a_{n-1} in vin_d / vin_u.
@@ -709,23 +729,27 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                     *zp = x;
                     vout_d[b * 64 + row] = x;
                     vout_u[b * 64 + row] = x;
+                    if (tq == 0) pv_d[b * 64 + row] = x;        // x_0
+                    if (tq == n - 1) pv_u[b * 64 + row] = x;    // x_{n-1}
                 }
             if (!finish()) return false;
         }
-        // back: x_i = z_i - F_i x_inner, down i = tq-1..0, up i = tq+1..n-1
+        // back: x_i = z_i - F_i x_inner, down i = tq-1..0, up i = tq+1..n-1; the last
+        // steps leave x_0 in pv_d and x_{n-1} in pv_u
         for (int s = 0; s < imax(bd, bu); ++s)
-            if (!sep(s < bd, s < bu, tq - 1 - s, tq + 1 + s)) return false;
+            if (!sep(s < bd, s < bu, tq - 1 - s, tq + 1 + s, s == bd - 1, s == bu - 1)) return false;
         return true;
     };
     // right-hand sides a_i = sum of the parts of separator slot(i), two entries
     // per thread with their loads in flight together
-    auto load_a = [&](int n, int lvl) {
+    auto load_a = [&](int n, int lvl) {   // compute warps only: the producer warp streams blocks meanwhile
+        if (!compute) return;
         const int tot = n * nb * W;
-        for (int o0 = tid; o0 < tot; o0 += 2 * blockDim.x) {
-            C v[2];
+        for (int o0 = tid; o0 < tot; o0 += 4 * ptid) {
+            C v[4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int o = o0 + u * blockDim.x;
+            for (int u = 0; u < 4; ++u) {
+                const int o = o0 + u * ptid;
                 if (o < tot) {
                     const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
                     const int64_t pb = pidx(b, lvl == 1 ? q0 + i : A.g.gq1[i], 0) + c;
@@ -735,8 +759,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int o = o0 + u * blockDim.x;
+            for (int u = 0; u < 4; ++u) {
+                const int o = o0 + u * ptid;
                 if (o < tot) {
                     const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
                     zb[(i * BT + b) * W + c] = v[u];
@@ -745,7 +769,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 }
             }
         }
-        __syncthreads();
+        asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");
     };
     // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at
     //      zero; level 2: the level-2 separators (one code path for both levels)
@@ -760,16 +784,10 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (lvl == 2 || NG == 1) return;
         // the group's parts of the level-2 right-hand sides:
         //   -P2L_{gi} y(last) to the separator below, -P2U_{gi-1} y(first) to the one above
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int c = o % W, b = o / W;
-            if (dn2) vin_d[b * 64 + c] = zq(n1 - 1)[b * W + c];
-            if (up2) vin_u[b * 64 + c] = zq(0)[b * W + c];
-        }
-        __syncthreads();
-        {
+        {   // x_{n1-1} (pv_u) and x_0 (pv_d), left by the chain's last steps
             const C *SL, *SU;
             consume_ab(dn2, up2, SL, SU);
-            step2(dn2 ? SL : SU, dn2 ? vin_d : vin_u, up2 ? SU : SL, up2 ? vin_u : vin_d);
+            step2(dn2 ? SL : SU, dn2 ? pv_u : pv_d, up2 ? SU : SL, up2 ? pv_d : pv_u);
 #pragma unroll
             for (int b = 0; b < BT; ++b)
                 if (b < nb && rowok && (b & 3) == g) {
@@ -915,6 +933,21 @@ __global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __
             if (on && k == 1 && gi >= 0 && gi < NG - 1) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[0]);
         }
     }
+    // the spike rows of this group's first transfer task (factor data, independent of
+    // the chain kernel): in registers before the wait
+    const int ntask = tr ? m * 2 : 0;
+    C pa[8], pb[8];
+    {
+        const int task = imin(grp, imax(ntask - 1, 0));
+        const int c = (task & 1) ? A.sp.to1 : A.sp.to0;
+        const int64_t ro = A.st.fac + (int64_t)(r0 + (task >> 1)) * bs + (int64_t)imin(imax(c, 0), W - 1) * SL;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int a = g + 8 * i;
+            pa[i] = (tr && above && a < W) ? GT[ro + a] : CT<C>::zero();
+            pb[i] = (tr && below && a < W) ? GB[ro + a] : CT<C>::zero();
+        }
+    }
     pdl_wait();
     if (stage && w == 0) {
         uint32_t total = 0;
@@ -989,7 +1022,6 @@ __global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __
     }
     if (!tr) return;
     // ---- 2. transfer columns of the chunk rows: tasks (row, to0 / to1), one per 8-lane group
-    const int ntask = m * 2;
     for (int b = 0; b < nb; ++b) {
         C xa[8], xb[8];
         lane_vec(xa, xs + b * 64, above, g, W);
@@ -1000,7 +1032,23 @@ __global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __
             const int kk = task >> 1, c = (task & 1) ? A.sp.to1 : A.sp.to0;
             const int64_t ro = A.st.fac + (int64_t)(r0 + kk) * bs + (int64_t)c * SL;
             const C y = live && g == 0 ? yrow<C>(A, b0 + b, r0 + kk)[c] : CT<C>::zero();
-            const C sum = spike_dot2(GT + ro, xa, above, GB + ro, xb, below, g, W);
+            C sum;
+            if (t0 == 0) {   // the prefetched rows
+                C s0 = CT<C>::zero(), s1 = CT<C>::zero();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    s0 = cfma(pa[i], xa[i], s0);
+                    s1 = cfma(pb[i], xb[i], s1);
+                }
+                sum = cadd(s0, s1);
+#pragma unroll
+                for (int o = 1; o <= 4; o <<= 1) {
+                    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+                    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+                }
+            } else {
+                sum = spike_dot2(GT + ro, xa, above, GB + ro, xb, below, g, W);
+            }
             if (live && g == 0) xt[(kk * A.Bt + b) * 2 + (task & 1)] = csub(y, sum);
         }
     }
