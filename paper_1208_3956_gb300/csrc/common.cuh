@@ -75,11 +75,13 @@ struct StripDev {
     int64_t tab;   // offset of this strip's x tables: alpha at integer points (W), then half points (W+1)
     int64_t fac;   // element offset of this strip's blocks in the factor pools (Ny blocks of BS)
     int64_t red;   // element offset of this strip's reduced-system blocks ((P-1) blocks of BS)
+    int64_t xf;    // element offset of this strip's transfer composites (Ny rows of 16 spld(W))
     int64_t bs;    // elements per stored W x W block (column-major, padded to 16 bytes)
     int64_t ctab;  // offset of this strip's s_x(c) (W entries) in the working-precision table
     int nj;        // columns per lane in the sweep products (W <= 4 nj)
     int ld;        // leading dimension of the sweep-layout blocks (4 nj + 2)
     int olo[2], ohi[2];   // padded output columns of the forward (0) and backward (1) sweeps
+    int xc[4];            // strip-local transfer columns: forward to0, to1, backward to0, to1
 };
 
 // Sweep layout of the W x W blocks Sinv, Rinv, E, F: row-major with leading

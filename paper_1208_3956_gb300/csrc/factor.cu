@@ -458,6 +458,53 @@ __global__ void k_factor_sep(Geom g, const C* __restrict__ GT, const C* __restri
     }
 }
 
+// Transfer composites (with separator groups): for every chunk row k of chunk p and
+// transfer column c (forward to0, to1, backward to0, to1; StripDev::xc) the row vectors
+//   XF[k][col][0] = GT_p(k)[c,:] GT2_{p-1},   XF[k][col][1] = GT_p(k)[c,:] GB2_{p-1},
+//   XF[k][col][2] = GB_p(k)[c,:] GT2_p,       XF[k][col][3] = GB_p(k)[c,:] GB2_p
+// (zero where the level-2 spike does not exist).  With them the transfer of row k
+// follows from the chain solution, the group solutions of the chunk's two separators
+// and the level-2 values around their groups, before those separators are final:
+//   x_k[c] = y_k[c] - GT[c,:] y2_{p-1} - GB[c,:] y2_p + XF[0] x2a + XF[1] x2b + XF[2] x2a' + XF[3] x2b'.
+// One CTA per (chunk, strip); two level-2 blocks staged at a time.
+template <typename C>
+__global__ void k_factor_xfer(Geom g, const C* __restrict__ GT, const C* __restrict__ GB,
+                              const C* __restrict__ GT2, const C* __restrict__ GB2, C* __restrict__ XF) {
+    const StripDev st = g.strips[blockIdx.y];
+    const int p = blockIdx.x;
+    const int W = st.W, SL = spld(W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* blk = reinterpret_cast<C*>(smem_raw);   // [2][W][SL]
+    const int4 m0 = g.cmeta[2 * p];
+    const int r0 = m0.x, r1 = m0.y, gA = m0.z, gB = m0.w;
+    const int G = g.G;
+    for (int half = 0; half < 2; ++half) {   // 0: separator above (p-1), 1: separator below (p)
+        const int gi = half == 0 ? gA : gB;
+        const bool has[2] = {gi > 0, gi >= 0 && gi < G - 1};   // GT2, GB2 of that separator exist
+        const int q = half == 0 ? p - 1 : p;
+        __syncthreads();
+        for (int e = threadIdx.x; e < 2 * W * SL; e += blockDim.x) {
+            const int k = e / (W * SL), o = e % (W * SL);
+            blk[e] = has[k] ? (k == 0 ? GT2 : GB2)[st.red + (int64_t)q * st.bs + o] : CT<C>::zero();
+        }
+        __syncthreads();
+        for (int k = r0; k < r1; ++k)
+            for (int col = 0; col < 4; ++col) {
+                const int c = st.xc[col];
+                const C* v = (half == 0 ? GT : GB) + st.fac + (int64_t)k * st.bs + (int64_t)c * SL;
+                for (int o = threadIdx.x; o < 2 * SL; o += blockDim.x) {
+                    const int k2 = o / SL, a = o % SL;
+                    C acc = CT<C>::zero();
+                    if (has[k2] && a < W) {
+                        const C* M = blk + k2 * W * SL + a;
+                        for (int cc = 0; cc < W; ++cc) acc = cfma(v[cc], M[cc * SL], acc);
+                    }
+                    XF[st.xf + (((int64_t)k * 4 + col) * 4 + half * 2 + k2) * SL + a] = acc;
+                }
+            }
+    }
+}
+
 size_t factor_smem_bytes(int Wmax, size_t esize, int nbuf) {
     return (size_t)nbuf * Wmax * Wmax * esize + (size_t)3 * Wmax * esize + (size_t)((Wmax + 3) & ~3) * 4 + 16;
 }
@@ -481,6 +528,15 @@ cudaError_t launch_factor(const Geom& g, int Wmax, void* const* pool, int* statu
         SepPools<C> pl{(C*)pool[3], (C*)pool[4], (C*)pool[5], (C*)pool[6], (C*)pool[7], (C*)pool[8], (C*)pool[9]};
         TimedLaunch t(tm, "factor_sep", s);
         k_factor_sep<C><<<g.J, 256, smem_sep, s>>>(g, (const C*)pool[1], (const C*)pool[2], pl, status);
+    }
+    if (g.G > 1) {
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const size_t xs = (size_t)2 * Wmax * spld(Wmax) * sizeof(C);
+        err = cudaFuncSetAttribute(k_factor_xfer<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs);
+        if (err != cudaSuccess) return err;
+        TimedLaunch t(tm, "factor_xfer", s);
+        k_factor_xfer<C><<<dim3(g.P, g.J), 256, xs, s>>>(g, (const C*)pool[1], (const C*)pool[2], (const C*)pool[6],
+                                                          (const C*)pool[7], (C*)pool[10]);
     }
     return cudaGetLastError();
 }

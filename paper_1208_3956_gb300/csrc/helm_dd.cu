@@ -80,8 +80,9 @@ struct helm_dd {
     int zrows = 1;
     StripDev* d_strips = nullptr;
     int* d_ints = nullptr;          // cmeta (8 per chunk) | r0 | r1 | rowmap | gq0 | gq1 | sepmap
-    // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator)
-    void* d_pool[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator), transfer composites
+    void* d_pool[11] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr};
     int* d_status = nullptr;
     size_t esize = 16;
     bool factored = false;
@@ -89,7 +90,7 @@ struct helm_dd {
     bool dev_ready = false;
     // workspaces
     struct Ws { void* p = nullptr; size_t bytes = 0; };
-    Ws ws_V, ws_G, ws_T0, ws_T1, ws_Y, ws_parts, ws_xsep, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
+    Ws ws_V, ws_G, ws_Y, ws_parts, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
     KernelTimer timer;
     std::string err;
 };
@@ -505,7 +506,7 @@ helm_status helm_dd_factor(helm_dd* h) {
     if (ps != HELM_OK) return ps;
     if (h->dim != 2) return fail(h, HELM_EINVAL, "strip factorisation is implemented for 2-D grids");
     const int Ny = (int)h->N[1];
-    int64_t fac = 0, red = 0;
+    int64_t fac = 0, red = 0, xf = 0;
     for (size_t jj = 0; jj < h->strips.size(); ++jj) {
         auto& s = h->strips[jj];
         const int j = (int)jj;
@@ -519,8 +520,15 @@ helm_status helm_dd_factor(helm_dd* h) {
         s.bs = (int64_t)s.W * s.ld;   // sweep layout; even, so blocks stay 16-byte aligned
         s.fac = fac;
         s.red = red;
+        s.xf = xf;
+        // transfer columns (strip-local): forward to the right neighbour, backward to the left
+        s.xc[1] = s.lpml + (s.hi - s.lo);
+        s.xc[0] = s.xc[1] - 1;
+        s.xc[2] = s.lpml;
+        s.xc[3] = s.lpml + 1;
         fac += (int64_t)Ny * s.bs;
         red += (int64_t)std::max(h->P - 1, 1) * s.bs;
+        xf += (int64_t)Ny * 16 * spld(s.W);
     }
     for (auto& p : h->d_pool) { if (p) cudaFree(p); p = nullptr; }
     h->factored = false;
@@ -531,8 +539,10 @@ helm_status helm_dd_factor(helm_dd* h) {
     CK(h, cudaMalloc(&h->d_pool[3], redb));
     CK(h, cudaMalloc(&h->d_pool[4], redb));
     CK(h, cudaMalloc(&h->d_pool[5], redb));
-    if (h->G > 1)
+    if (h->G > 1) {
         for (int i = 6; i < 10; ++i) CK(h, cudaMalloc(&h->d_pool[i], redb));
+        CK(h, cudaMalloc(&h->d_pool[10], (size_t)xf * h->esize));
+    }
     CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
                           cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
@@ -578,26 +588,20 @@ helm_status check_device_status(helm_dd* h) {
 struct PrecondBufs {
     double2* V;      // [B][N] forward-sweep field v
     double2* G;      // [B][N] residual g = f - A v
-    double2* T0;     // [B][Ny] transfer differences (two, swapped per strip)
-    double2* T1;
     void* Y;         // [J][B][Ny][ws] chain solutions of every strip, working precision (ws = work_stride)
     void* parts;     // [B][P-1][4][ws] separator right-hand-side parts
-    void* xsep;      // [J][B][max(P-1,1)][ws] final separator values of every strip
     int* counters;   // [kMaxTiles][G+1] arrival counters, zero on entry
 };
-constexpr int kPrecondBufs = 7;
+constexpr int kPrecondBufs = 4;
 
-// Bytes of each PrecondBufs member (V, G, T0, T1, Y, parts, xsep) for B right-hand sides.
+// Bytes of each PrecondBufs member (V, G, Y, parts) for B right-hand sides.
 void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
     const int64_t NV = nvol(h);
     const int Ny = (int)h->N[1];
     sz[0] = (size_t)B * NV * sizeof(double2);
     sz[1] = sz[0];
-    sz[2] = (size_t)B * Ny * sizeof(double2);
-    sz[3] = sz[2];
-    sz[4] = (size_t)h->J * B * Ny * work_stride(h) * h->esize;
-    sz[5] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
-    sz[6] = (size_t)h->J * B * std::max(h->P - 1, 1) * work_stride(h) * h->esize;
+    sz[2] = (size_t)h->J * B * Ny * work_stride(h) * h->esize;
+    sz[3] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
@@ -609,13 +613,9 @@ helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     precond_buf_bytes(h, B, sz);
     if ((s = ws_reserve(h, h->ws_V, sz[0])) != HELM_OK) return s;
     if ((s = ws_reserve(h, h->ws_G, sz[1])) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_T0, sz[2])) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_T1, sz[3])) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_Y, sz[4])) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_parts, sz[5])) != HELM_OK) return s;
-    if ((s = ws_reserve(h, h->ws_xsep, sz[6])) != HELM_OK) return s;
-    PrecondBufs bf{(double2*)h->ws_V.p, (double2*)h->ws_G.p, (double2*)h->ws_T0.p, (double2*)h->ws_T1.p,
-                   h->ws_Y.p, h->ws_parts.p, h->ws_xsep.p, h->d_counters};
+    if ((s = ws_reserve(h, h->ws_Y, sz[2])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_parts, sz[3])) != HELM_OK) return s;
+    PrecondBufs bf{(double2*)h->ws_V.p, (double2*)h->ws_G.p, h->ws_Y.p, h->ws_parts.p, h->d_counters};
     return run_precond(h, in, out, B, bf);
 }
 
@@ -626,70 +626,58 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
     double2* V = bf.V;
     double2* G = bf.G;
-    double2* Tin = bf.T0;
-    double2* Tout = bf.T1;
     const int ws = work_stride(h);
-    const int64_t ystride = (int64_t)B * Ny * ws, xstride = (int64_t)B * std::max(h->P - 1, 1) * ws;
+    const int64_t ystride = (int64_t)B * Ny * ws;
     const int J = h->J;
     const auto& beta = h->beta;
     const double ih2 = 1.0 / (h->h * h->h);
     const bool mixed = h->prec == HELM_PREC_MIXED;
-    // strip j: chain solution and final separator values in its own slices, so that
-    // the output columns of a whole sweep are written afterwards in one launch
+    // strip j keeps its chain solution in its own slice: the next strip solve takes its
+    // transfer from it, and the output columns of a whole sweep are written afterwards
+    // in one launch
+    auto ybuf = [&](int j) { return (char*)bf.Y + j * ystride * (int64_t)h->esize; };
     auto strip_solve = [&](int j, const SweepStep& sp) -> cudaError_t {
-        SweepWork wk{(char*)bf.Y + j * ystride * (int64_t)h->esize, bf.parts, bf.counters, h->d_status, ws, B,
-                     h->zrows, (char*)bf.xsep + j * xstride * (int64_t)h->esize};
-        if (mixed) return launch_strip_solve<float2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
-        return launch_strip_solve<double2>(h->geom, j, h->strips[j], sp, wk, h->d_pool, h->stream, &h->timer);
+        SweepWork wk{ybuf(j), bf.parts, bf.counters, h->d_status, ws, B, h->zrows,
+                     sp.prev >= 0 ? ybuf(sp.prev) : nullptr};
+        const StripDev* pst = sp.prev >= 0 ? &h->strips[sp.prev] : nullptr;
+        if (mixed)
+            return launch_strip_solve<float2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, h->stream, &h->timer);
+        return launch_strip_solve<double2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, h->stream, &h->timer);
     };
     auto outputs = [&](int dir, int nstrip, double2* dst, const double2* base) -> cudaError_t {
-        OutArgs O{h->geom, dir, 0, nstrip, bf.Y, ystride, bf.xsep, xstride, ws, B, B > 1 ? 4 : 1, dst, base};
+        OutArgs O{h->geom, dir, 0, nstrip, bf.Y, ystride, ws, B, B > 1 ? 4 : 1, dst, base};
         if (mixed) return launch_outputs<float2>(O, h->d_pool, h->stream, &h->timer);
         return launch_outputs<double2>(O, h->d_pool, h->stream, &h->timer);
     };
-    // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1)
+    // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1),
+    // the transfer on the first two columns of strip j taken from the solve of strip j-1
     for (int j = 0; j < J; ++j) {
-        const StripDev& st = h->strips[j];
         SweepStep sp{};
         sp.src = in;
         sp.mlo = beta[j] + 1;
         sp.mhi = beta[j + 1];
-        sp.tin = j > 0 ? Tin : nullptr;
+        sp.prev = j > 0 ? j - 1 : -1;
+        sp.pdir = 0;
         sp.t0 = beta[j];
         sp.tcoef = -ih2;
-        sp.dst = (J == 1) ? out : V;
-        sp.base = nullptr;
-        sp.olo = beta[j] + 1;
-        sp.ohi = beta[j + 1];
-        sp.tout = j < J - 1 ? Tout : nullptr;
-        sp.to1 = st.lpml + (st.hi - st.lo);
-        sp.to0 = sp.to1 - 1;
         CK(h, strip_solve(j, sp));
-        std::swap(Tin, Tout);
     }
     CK(h, outputs(0, J, (J == 1) ? out : V, nullptr));
     if (J == 1) return HELM_OK;
     // residual g = f - A v
     if ((s = dev_stencil(h, V, in, G, B)) != HELM_OK) return s;
-    // backward sweep j = J-1..1 (Eq. solve_downward), w^(J) = 0, out = v + w on D~^(j)
+    // backward sweep j = J-1..1 (Eq. solve_downward), w^(J) = 0, out = v + w on D~^(j),
+    // the transfer on columns beta_{j+1}+1, +2 taken from the solve of strip j+1
     for (int j = J - 2; j >= 0; --j) {
-        const StripDev& st = h->strips[j];
         SweepStep sp{};
         sp.src = G;
         sp.mlo = j > 0 ? beta[j] + 2 : 0;
         sp.mhi = beta[j + 1] + 1;
-        sp.tin = (j + 1 <= J - 2) ? Tin : nullptr;
+        sp.prev = (j + 1 <= J - 2) ? j + 1 : -1;
+        sp.pdir = 1;
         sp.t0 = beta[j + 1] + 1;
         sp.tcoef = ih2;
-        sp.dst = out;
-        sp.base = V;
-        sp.olo = sp.mlo;
-        sp.ohi = sp.mhi;
-        sp.tout = j > 0 ? Tout : nullptr;
-        sp.to0 = st.lpml;
-        sp.to1 = st.lpml + 1;
         CK(h, strip_solve(j, sp));
-        std::swap(Tin, Tout);
     }
     CK(h, outputs(1, J - 1, out, V));
     // D~^(J) keeps v (w = 0 there)
@@ -1094,7 +1082,7 @@ void helm_dd_destroy(helm_dd* h) {
     for (auto p : h->d_pool) cudaFree(p);
     cudaFree(h->d_ct);
     cudaFree(h->d_counters);
-    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_T0, &h->ws_T1, &h->ws_Y, &h->ws_parts, &h->ws_xsep, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
                     &h->ws_small, &h->ws_grad})
         ws_free(*w);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -1165,8 +1153,8 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
     void* base = nullptr;
     CK(h, noalloc_scratch(&base));
     unsigned char* b = (unsigned char*)base;
-    PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), (double2*)(b + off[2]), (double2*)(b + off[3]),
-                   b + off[4], b + off[5], b + off[6], (int*)(b + off[7])};
+    PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), b + off[2], b + off[3],
+                   (int*)(b + off[kPrecondBufs])};
     // the array keeps whatever the previous call left: the arrival counters must start at zero
     CK(h, cudaMemsetAsync(bf.counters, 0, h->counter_bytes, h->stream));
     helm_status s = run_precond(h, (const double2*)in, (double2*)out, nrhs, bf);

@@ -96,14 +96,10 @@ cudaError_t launch_factor(const Geom& g, int Wmax, void* const* pool, int* statu
 struct SweepStep {
     const double2* src;     // [B][Ny][Nx] FP64
     int mlo, mhi;           // mask of src columns entering the right-hand side
-    const double2* tin;     // [B][Ny] incoming transfer difference, or null
+    int prev;               // strip whose solve passes its transfer into this one, or -1
+    int pdir;               // that strip's transfer columns: 0 forward (its right end), 1 backward (its left end)
     int t0;                 // first padded column receiving the transfer
     double tcoef;           // transfer coefficient (-1/h^2 forward, +1/h^2 backward)
-    double2* dst;           // [B][Ny][Nx] output field
-    const double2* base;    // optional field added to x on output
-    int olo, ohi;           // padded output columns
-    double2* tout;          // [B][Ny] outgoing transfer difference, or null
-    int to0, to1;           // strip-local columns of the outgoing difference
 };
 
 struct SweepWork {
@@ -111,23 +107,20 @@ struct SweepWork {
     void* parts;            // [B][P-1][4][Wmax] working precision
     int* counters;          // [RHS tile][G+1], zero between launches
     int* status;            // error word (7 = bounded wait timed out)
-    int Wmax;               // row stride of ybuf, parts and xsep: even, >= every strip width
+    int Wmax;               // row stride of ybuf and parts: even, >= every strip width
     int B;
     int zrows;              // longest chain of one CTA (chunk rows, group size, G-1)
-    void* xsep;             // [B][max(P-1,1)][Wmax] this strip's final separator values
+    const void* pybuf;      // the previous strip solve's chain solution (when SweepStep::prev >= 0)
 };
 
 // Output pass of a sweep (k_sweep_output) over strips jlo .. jlo+nstrip-1,
-// after their strip solves: strip j's chain solution sits at ybuf + j*ystride
-// and its final separator values at xsep + j*xstride (elements).
+// after their strip solves.
 struct OutArgs {
     Geom g;
     int dir;                // output ranges of the forward (0) or backward (1) sweep
     int jlo, nstrip;
-    const void* ybuf;
+    const void* ybuf;       // strip j's chain solution at ybuf + j*ystride (elements)
     int64_t ystride;
-    const void* xsep;
-    int64_t xstride;
     int Wmax, B, Bt;
     double2* dst;           // [B][Ny][Nx] output field
     const double2* base;    // optional field added on output
@@ -136,8 +129,10 @@ template <typename C>
 cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm);
 
 template <typename C>
-cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const SweepStep& step,
-                               const SweepWork& wk, void* const* pool, cudaStream_t s, KernelTimer* tm);
+// pst: the strip of the previous solve whose transfer enters this one (step.prev >= 0), host copy
+cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const StripDev* pst,
+                               const SweepStep& step, const SweepWork& wk, void* const* pool, cudaStream_t s,
+                               KernelTimer* tm);
 
 // ---- field.cu: FP64 grid kernels
 cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, int nz, int w, double omega,

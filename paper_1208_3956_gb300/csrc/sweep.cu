@@ -3,7 +3,9 @@
 //
 // k_sweep_chunk (grid: chunks x RHS tiles)
 //   * builds the strip right-hand side S^(j) r for every row of its chunk
-//     (masked source plus the single-layer-potential transfer on two columns);
+//     (masked source plus the single-layer-potential transfer on two columns,
+//     which it takes directly from the previous strip solve's chain and group
+//     solutions through the transfer composites of factor.cu);
 //   * streams the chunk's Sinv_k blocks global -> shared memory with TMA bulk
 //     copies (cp.async.bulk + mbarrier ring; the whole chunk stays resident when
 //     it fits, so the back substitution reads no HBM);
@@ -16,13 +18,10 @@
 //     level-2 separators held at zero (twisted chain z_i = a_i - E_i z_outer,
 //     x_i = z_i - F_i x_inner) and adds the group's parts of the level-2
 //     right-hand sides; the last group to finish solves the level-2 system.
-// k_sweep_transfer (grid: chunks x RHS tiles)
-//   final separator values (grouped separators: x_q = y_q - GT2_q x2_above -
-//   GB2_q x2_below) and the transfer difference of every row, which is all the
-//   next strip solve waits for;
 // k_sweep_output (grid: chunks x strips x RHS tiles, once per sweep)
-//   x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output columns of every
-//   strip, scattered (plus the base field) to the output field.
+//   final separator values (grouped separators: x_q = y_q - GT2_q x2_above -
+//   GB2_q x2_below), then x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output
+//   columns of every strip, scattered (plus the base field) to the output field.
 //
 // Every mbarrier wait is bounded; on time-out the kernel records
 // HELM_ETIMEOUT in the status word, drains its copies (bounded) and returns.
@@ -35,7 +34,6 @@ static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
 static constexpr int kParts = 4;   // separator right-hand-side parts: 2 from chunks, 2 from groups
 static constexpr int kAhead = 6;   // block loads in flight ahead of the chain (three dual steps)
-static constexpr uint32_t kXferBudget = 216 * 1024;   // k_sweep_transfer: shared-memory budget
 
 // load-order table entries: factor pool << 24 | block index in that pool
 enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kP2L = 4, kP2U = 5 };
@@ -108,7 +106,15 @@ struct SweepArgs {
     const void* P2U;
     void* ybuf;              // [B][Ny][Wmax] chunk solutions, then separator values
     void* parts;             // [B][P-1][kParts][Wmax] separator right-hand-side parts
-    void* xsep;              // [B][max(P-1,1)][Wmax] final separator values (for the output kernel)
+    // the previous strip solve, whose transfer enters this one (has_prev)
+    int has_prev;
+    StripDev pst;
+    const void* pybuf;       // its chain solution [B][Ny][Wmax]
+    const void* GT;          // spike pools (all strips)
+    const void* GB;
+    const void* GT2;
+    const void* GB2;
+    const void* XF;          // transfer composites (with separator groups)
     int* counters;           // [ntile][G+1] arrival counters, left at zero
     int* status;
 };
@@ -128,7 +134,7 @@ __device__ __forceinline__ C* yrow(const SweepArgs& A, int b, int k) {
 
 // Shared-memory carve-up (bytes), identical on host and device.
 struct SweepSmem {
-    uint32_t slots, zb, tv, cx, cy, order, mbar, flags, total;
+    uint32_t slots, zb, tv, cx, cy, xv, order, mbar, flags, total;
 };
 __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, int zrows, int Bt, int W,
                                                 int esz) {
@@ -139,6 +145,7 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     s.tv = o; o += 7u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs, parts inputs
     s.cx = o; o += 64u * esz;
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
+    s.xv = o; o += ((uint32_t)(6 * Bt * 64 + (zrows + 1) * Bt * 2) * esz + 15u) & ~15u;   // incoming transfer
     s.order = o; o += ((uint32_t)(6 * zrows + 8) * 4 + 15u) & ~15u;   // load order table
     s.mbar = o; o += kMaxRing * 8;
     s.flags = o; o += 16;
@@ -265,6 +272,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     unsigned char* slots = smem + L.slots;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.mbar);
     C* zb = reinterpret_cast<C*>(smem + L.zb);       // [zrows][BT][W]
+    C* xv = reinterpret_cast<C*>(smem + L.xv);       // incoming transfer: [6][BT][64] vectors, [rows][BT][2] values
     C* v0 = reinterpret_cast<C*>(smem + L.tv);       // [BT][64] vectors: in/out of both chains, separator rhs
     C* vin_d = v0;
     C* vin_u = v0 + BT * 64;
@@ -484,16 +492,105 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 put(rr[u], bb[u], cc[u], cmul(CT<C>::from(f), cmul(sx[u], sy[u])));
             }
         }
+        // The previous strip solve's transfer x[to1] - x[to0] on this chunk's rows and the
+        // separator row below, from its chain solution y, the group solutions y2 of the
+        // chunk's two separators and the level-2 values x2 around their groups (the
+        // composites XF of factor.cu):
+        //   chunk row k:   x_k = y_k - GT[c,:] y2_{p-1} - GB[c,:] y2_p + XF[k][c] . x2
+        //   separator row: x = y2_p - GT2_p[c,:] x2a - GB2_p[c,:] x2b
+        // Tasks (row, column) go to 8-lane groups; the six factor rows of a group's first
+        // task are read before the dependency wait (they do not depend on it), the six
+        // vectors are staged in shared memory after it.
+        const StripDev& ps = A.pst;
+        const int Wp = ps.W, SLp = spld(Wp);
+        const int4 cm0 = A.g.cmeta[2 * p], cm1 = A.g.cmeta[2 * p + 1];
+        const int gA = cm0.z, gB = cm0.w;
+        const bool fa0 = gA > 0, fa1 = gA >= 0 && gA < NG - 1, fb0 = gB > 0, fb1 = gB >= 0 && gB < NG - 1;
+        const int lg = tid & 7, grp = tid >> 3, ngrp = ptid >> 3;
+        const int ntask = A.has_prev ? nrow * 2 : 0;
+        // the six rows of task t (unused ones zero), and the signs / switches they go with
+        const bool on[6] = {has_above, has_below, fa0, fa1, fb0, fb1};
+        auto task_rows = [&](int task, C (&rw)[6][8]) {
+            const int kk = task >> 1, i = task & 1;
+            const int col = 2 * A.sp.pdir + i, c = ps.xc[col];
+            const C* rp[6];
+            if (kk < m) {
+                const int k = r0 + kk;
+                const int64_t ro = ps.fac + (int64_t)k * ps.bs + (int64_t)c * SLp;
+                const int64_t xo = ps.xf + ((int64_t)k * 4 + col) * 4 * SLp;
+                const C* XFp = reinterpret_cast<const C*>(A.XF);
+                rp[0] = reinterpret_cast<const C*>(A.GT) + ro;
+                rp[1] = reinterpret_cast<const C*>(A.GB) + ro;
+                for (int v = 2; v < 6; ++v) rp[v] = NG > 1 ? XFp + xo + (v - 2) * SLp : nullptr;
+            } else {   // the separator row below: only its level-2 spikes
+                const int64_t o2 = ps.red + (int64_t)p * ps.bs + (int64_t)c * SLp;
+                rp[0] = rp[1] = rp[2] = rp[3] = nullptr;
+                rp[4] = NG > 1 ? reinterpret_cast<const C*>(A.GT2) + o2 : nullptr;
+                rp[5] = NG > 1 ? reinterpret_cast<const C*>(A.GB2) + o2 : nullptr;
+            }
+#pragma unroll
+            for (int v = 0; v < 6; ++v)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int a = lg + 8 * q;
+                    rw[v][q] = (rp[v] && on[v] && a < Wp) ? rp[v][a] : CT<C>::zero();
+                }
+        };
+        C rw0[6][8];
+        if (ntask > 0) task_rows(imin(grp, ntask - 1), rw0);
         pdl_wait();
-        if (A.sp.tin) {
-            asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");   // compute warps: source part written
+        if (A.has_prev) {
+            const C* Yp = reinterpret_cast<const C*>(A.pybuf);
+            // vectors: y2 above (row r0-1), y2 below (row r1), x2 around the group above, below
+            const int vrow[6] = {r0 - 1, r1, cm1.x, cm1.y, cm1.z, cm1.w};
+            for (int o = tid; o < 6 * nb * 64; o += ptid) {   // zero beyond Wp: the products read all 64
+                const int v = o / (nb * 64), b = (o / 64) % nb, c = o % 64;
+                xv[(v * BT + b) * 64 + c] = (on[v] && c < Wp)
+                                                ? Yp[((int64_t)(b0 + b) * A.g.Ny + vrow[v]) * A.Wmax + c]
+                                                : CT<C>::zero();
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");
+            C* xt = xv + 6 * BT * 64;                       // [row][BT][2]
+            const R sg[6] = {(R)-1, (R)-1, (R)1, (R)1, (R)1, (R)1};   // signs of the six terms (chunk rows)
+            for (int t0 = 0; t0 < ntask; t0 += ngrp) {   // uniform trip count: every lane shuffles
+                const bool live = t0 + grp < ntask;
+                const int task = imin(t0 + grp, ntask - 1);
+                const int kk = task >> 1, i = task & 1;
+                const int c = ps.xc[2 * A.sp.pdir + i];
+                if (t0 > 0) task_rows(task, rw0);   // the first task's rows were read before the wait
+                const bool srow = kk >= m;           // the separator row: x = y2_p - level-2 terms
+                for (int b = 0; b < nb; ++b) {
+                    const C y = lg == 0 ? (srow ? xv[(1 * BT + b) * 64 + c]
+                                                : Yp[((int64_t)(b0 + b) * A.g.Ny + r0 + kk) * A.Wmax + c])
+                                        : CT<C>::zero();
+                    C acc = CT<C>::zero();
+#pragma unroll
+                    for (int v = 0; v < 6; ++v) {
+                        C d = CT<C>::zero();
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int a = imin(lg + 8 * q, 63);
+                            d = cfma(rw0[v][q], xv[(v * BT + b) * 64 + a], d);
+                        }
+                        acc = cadd(acc, cscale(d, srow ? (R)-1 : sg[v]));
+                    }
+#pragma unroll
+                    for (int o = 1; o <= 4; o <<= 1) {
+                        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                    }
+                    if (live && lg == 0) xt[(kk * BT + b) * 2 + i] = cadd(y, acc);
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");
+            // tcoef (x[to1] - x[to0]) enters this strip on columns t0, t0+1 (Eqs. solve_upward,
+            // solve_downward), scaled to the symmetric form like the source
             for (int o = tid; o < nrow * nb * 2; o += ptid) {
                 const int i = o & 1, b = (o >> 1) % nb, r = (o >> 1) / nb;
                 const int c = A.sp.t0 + i - cofs;
                 if (c < 0 || c >= W) continue;
-                const double2 tv = A.sp.tin[(int64_t)(b0 + b) * A.g.Ny + r0 + r];
-                const C add = cmul(CT<C>::from(make_double2(A.sp.tcoef * tv.x, A.sp.tcoef * tv.y)),
-                                   cmul(ct[A.st.ctab + c], ct[A.g.ct_sy + r0 + r]));
+                const C tv = csub(xt[(r * BT + b) * 2 + 1], xt[(r * BT + b) * 2]);
+                const C add = cmul(cscale(tv, (R)A.sp.tcoef), cmul(ct[A.st.ctab + c], ct[A.g.ct_sy + r0 + r]));
                 const C* cur = r < m ? &zb[(r * BT + b) * W + c] : &rsep[b * 64 + c];
                 put(r, b, c, cadd(*cur, add));
             }
@@ -839,237 +936,18 @@ __device__ __forceinline__ C spike_dot2(const C* __restrict__ ra, const C (&xa)[
     return s;
 }
 
-// Shared memory of k_sweep_transfer (bytes), identical on host and device: the
-// separator values xs [2][Bt][64], then, when it fits, the staged level-2
-// spike blocks GT2_q, GB2_q of both sides (W rows of spld(W)) and per side and
-// RHS three rows of we = even(W) entries (y_q and the level-2 values above and
-// below the group), then three barriers and the transfer columns [rows][Bt][2].
-struct XferPlan {
-    bool stage;
-    uint32_t blk_bytes, vrow_bytes, xs, p1, mbar, xt, total;
-};
-__host__ __device__ inline XferPlan xfer_plan(int W, bool grouped, int Bt, int esz, int maxrows, uint32_t budget) {
-    XferPlan f;
-    f.blk_bytes = (uint32_t)(W * spld(W) * esz);
-    f.vrow_bytes = (uint32_t)(((W + 1) & ~1) * esz);
-    const uint32_t p1 = (grouped ? 4 * f.blk_bytes : 0u) + 2u * Bt * 3 * f.vrow_bytes;
-    const uint32_t xsb = (uint32_t)(2 * Bt * 64 * esz), xtb = (uint32_t)(maxrows * Bt * 2 * esz);
-    f.stage = xsb + p1 + 32 + xtb <= budget;
-    f.xs = 0;
-    f.p1 = xsb;
-    f.mbar = f.p1 + (f.stage ? p1 : 0u);
-    f.xt = f.mbar + 32;
-    f.total = f.xt + xtb;
-    return f;
-}
-
-// One CTA per (chunk, RHS tile), after the chain kernel; the part of the
-// strip solve the next strip waits for:
-//  1. the final values of the separators above and below the chunk: the chain
-//     kernel's values, for grouped separators corrected by the level-2 spikes,
-//     x_q = y_q - GT2_q x2_{gi-1} - GB2_q x2_{gi}  (8 lanes per entry; the
-//     blocks are staged in shared memory by TMA bulk copies when they fit);
-//     the separator below is written to xsep for the output kernel;
-//  2. the transfer difference x_k(to1) - x_k(to0), x_k = y_k - GT_p(k) x_above -
-//     GB_p(k) x_below, for every chunk row and the separator row below.
-// The output columns are left to k_sweep_output, which needs no ordering with
-// the strips that follow.
-template <typename C>
-__global__ void __launch_bounds__(256) k_sweep_transfer(SweepArgs A, const C* __restrict__ GT,
-                                                        const C* __restrict__ GB, const C* __restrict__ GT2,
-                                                        const C* __restrict__ GB2) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    pdl_trigger();
-    const int p = blockIdx.x;
-    const int b0 = blockIdx.y * A.Bt;
-    const int nb = imin(A.Bt, A.B - b0);
-    const int W = A.st.W, SL = spld(W);
-    const int esz = (int)sizeof(C);
-    const int P = A.g.P, NG = A.g.G;
-    const int4 m0 = A.g.cmeta[2 * p], m1 = A.g.cmeta[2 * p + 1];
-    const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
-    const bool tr = A.sp.tout != nullptr;
-    const XferPlan F = xfer_plan(W, NG > 1, A.Bt, esz, A.zrows, kXferBudget);
-    C* xs = reinterpret_cast<C*>(smem + F.xs);       // [2][Bt][64]: separator above, below
-    unsigned char* p1 = smem + F.p1;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + F.mbar);
-    C* xt = reinterpret_cast<C*>(smem + F.xt);       // [m][Bt][2]
-    const bool above = p > 0, below = p < P - 1;
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = l & 7;
-    const int grp = tid >> 3, ngrp = blockDim.x >> 3;
-    const int64_t bs = A.st.bs;
-    // per side: separator q and its row, its group (>= 0: corrected by level-2
-    // spikes) and the rows of the level-2 separators around that group
-    const int sq[2] = {p - 1, p}, srow[2] = {r0 - 1, r1};
-    const int sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
-    auto p1blk = [&](int side, int k) { return p1 + (size_t)(side * 2 + k) * F.blk_bytes; };   // k: GT2, GB2
-    auto p1row = [&](int side, int b, int k) {   // k: y_q, x2 above, x2 below
-        return p1 + 4 * (size_t)F.blk_bytes * (NG > 1) + ((size_t)(side * A.Bt + b) * 3 + k) * F.vrow_bytes;
-    };
-    __shared__ int fail;
-    if (tid == 0) {
-        fail = 0;
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    const bool stage = F.stage && (above || below);
-    // warp 0 stages step 1: the level-2 spike blocks (factor data) at once on
-    // barrier 0, the chain kernel's rows after the wait on barrier 1
-    if (stage && w == 0) {
-        uint32_t total = 0;
-        for (int side = 0; side < 2; ++side) {
-            if (side == 0 ? !above : !below) continue;
-            total += F.blk_bytes * ((sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
-        }
-        if (l == 0) mbar_expect_tx(&mbar[0], total);
-        __syncwarp();
-        if (l < 4) {
-            const int side = l >> 1, k = l & 1, gi = sg[side];
-            const bool on = side == 0 ? above : below;
-            const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
-            if (on && k == 0 && gi > 0) bulk_g2s(p1blk(side, 0), GT2 + o2, F.blk_bytes, &mbar[0]);
-            if (on && k == 1 && gi >= 0 && gi < NG - 1) bulk_g2s(p1blk(side, 1), GB2 + o2, F.blk_bytes, &mbar[0]);
-        }
-    }
-    // the spike rows of this group's first transfer task (factor data, independent of
-    // the chain kernel): in registers before the wait
-    const int ntask = tr ? m * 2 : 0;
-    C pa[8], pb[8];
-    {
-        const int task = imin(grp, imax(ntask - 1, 0));
-        const int c = (task & 1) ? A.sp.to1 : A.sp.to0;
-        const int64_t ro = A.st.fac + (int64_t)(r0 + (task >> 1)) * bs + (int64_t)imin(imax(c, 0), W - 1) * SL;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int a = g + 8 * i;
-            pa[i] = (tr && above && a < W) ? GT[ro + a] : CT<C>::zero();
-            pb[i] = (tr && below && a < W) ? GB[ro + a] : CT<C>::zero();
-        }
-    }
-    pdl_wait();
-    if (stage && w == 0) {
-        uint32_t total = 0;
-        for (int side = 0; side < 2; ++side) {
-            if (side == 0 ? !above : !below) continue;
-            total += (uint32_t)nb * F.vrow_bytes * (1 + (sg[side] > 0) + (sg[side] >= 0 && sg[side] < NG - 1));
-        }
-        if (l == 0) mbar_expect_tx(&mbar[1], total);
-        __syncwarp();
-        for (int ci = l; ci < 2 * 3 * nb; ci += 32) {
-            const int side = ci / (3 * nb), b = (ci / 3) % nb, kind = ci % 3;
-            if (side == 0 ? !above : !below) continue;
-            const int gi = sg[side];
-            if (kind == 0) bulk_g2s(p1row(side, b, 0), yrow<C>(A, b0 + b, srow[side]), F.vrow_bytes, &mbar[1]);
-            else if (kind == 1 && gi > 0)
-                bulk_g2s(p1row(side, b, 1), yrow<C>(A, b0 + b, sra[side]), F.vrow_bytes, &mbar[1]);
-            else if (kind == 2 && gi >= 0 && gi < NG - 1)
-                bulk_g2s(p1row(side, b, 2), yrow<C>(A, b0 + b, srb[side]), F.vrow_bytes, &mbar[1]);
-        }
-    }
-    // ---- 1. separator values
-    if (stage && !(mbar_wait(&mbar[0], 0u) && mbar_wait(&mbar[1], 0u))) fail = 1;
-    __syncthreads();
-    if (fail) {   // a bounded wait gave up: report, let the copies land (bounded), leave
-        if (tid == 0) {
-            atomicExch(A.status, 7);
-            mbar_wait(&mbar[0], 0u);
-            mbar_wait(&mbar[1], 0u);
-        }
-        __syncthreads();
-        return;
-    }
-    for (int side = 0; side < 2; ++side) {
-        if (side == 0 ? !above : !below) continue;
-        const int gi = sg[side];
-        const bool up = gi > 0, dn = gi >= 0 && gi < NG - 1;
-        const int64_t o2 = A.st.red + (int64_t)sq[side] * bs;
-        const C* T2 = F.stage ? reinterpret_cast<const C*>(p1blk(side, 0)) : GT2 + o2;
-        const C* B2 = F.stage ? reinterpret_cast<const C*>(p1blk(side, 1)) : GB2 + o2;
-        for (int b = 0; b < nb; ++b) {
-            const C* y = F.stage ? reinterpret_cast<const C*>(p1row(side, b, 0)) : yrow<C>(A, b0 + b, srow[side]);
-            C* xo = xs + (side * A.Bt + b) * 64;
-            if (gi < 0) {
-                for (int c = tid; c < W; c += blockDim.x) xo[c] = y[c];
-                continue;
-            }
-            C xa[8], xb[8];
-            lane_vec(xa, F.stage ? reinterpret_cast<const C*>(p1row(side, b, 1)) : yrow<C>(A, b0 + b, sra[side]),
-                     up, g, W);
-            lane_vec(xb, F.stage ? reinterpret_cast<const C*>(p1row(side, b, 2)) : yrow<C>(A, b0 + b, srb[side]),
-                     dn, g, W);
-            for (int base = w * 4; base < W; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
-                const int c = base + (l >> 3);
-                const int cc = imin(c, W - 1);
-                const C sum = spike_dot2(T2 + (int64_t)cc * SL, xa, up, B2 + (int64_t)cc * SL, xb, dn, g, W);
-                if (c < W && g == 0) xo[c] = csub(y[c], sum);
-            }
-        }
-    }
-    __syncthreads();
-    // the separator below is final: to the output kernel, and its transfer difference
-    if (below) {
-        C* xsep = reinterpret_cast<C*>(A.xsep);
-        for (int o = tid; o < nb * W; o += blockDim.x) {
-            const int b = o / W, c = o % W;
-            xsep[((int64_t)(b0 + b) * imax(P - 1, 1) + p) * A.Wmax + c] = xs[(A.Bt + b) * 64 + c];
-        }
-        if (tr && tid < nb) {
-            const C* xb = xs + (A.Bt + tid) * 64;
-            A.sp.tout[(int64_t)(b0 + tid) * A.g.Ny + r1] = csub(to_d2(xb[A.sp.to1]), to_d2(xb[A.sp.to0]));
-        }
-    }
-    if (!tr) return;
-    // ---- 2. transfer columns of the chunk rows: tasks (row, to0 / to1), one per 8-lane group
-    for (int b = 0; b < nb; ++b) {
-        C xa[8], xb[8];
-        lane_vec(xa, xs + b * 64, above, g, W);
-        lane_vec(xb, xs + (A.Bt + b) * 64, below, g, W);
-        for (int t0 = 0; t0 < ntask; t0 += ngrp) {   // uniform trip count: every lane shuffles
-            const bool live = t0 + grp < ntask;
-            const int task = imin(t0 + grp, ntask - 1);
-            const int kk = task >> 1, c = (task & 1) ? A.sp.to1 : A.sp.to0;
-            const int64_t ro = A.st.fac + (int64_t)(r0 + kk) * bs + (int64_t)c * SL;
-            const C y = live && g == 0 ? yrow<C>(A, b0 + b, r0 + kk)[c] : CT<C>::zero();
-            C sum;
-            if (t0 == 0) {   // the prefetched rows
-                C s0 = CT<C>::zero(), s1 = CT<C>::zero();
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    s0 = cfma(pa[i], xa[i], s0);
-                    s1 = cfma(pb[i], xb[i], s1);
-                }
-                sum = cadd(s0, s1);
-#pragma unroll
-                for (int o = 1; o <= 4; o <<= 1) {
-                    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
-                    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
-                }
-            } else {
-                sum = spike_dot2(GT + ro, xa, above, GB + ro, xb, below, g, W);
-            }
-            if (live && g == 0) xt[(kk * A.Bt + b) * 2 + (task & 1)] = csub(y, sum);
-        }
-    }
-    __syncthreads();
-    for (int o = tid; o < m * nb; o += blockDim.x) {
-        const int kk = o / nb, b = o % nb;
-        A.sp.tout[(int64_t)(b0 + b) * A.g.Ny + r0 + kk] =
-            csub(to_d2(xt[(kk * A.Bt + b) * 2 + 1]), to_d2(xt[(kk * A.Bt + b) * 2]));
-    }
-}
-
 // Output columns of many finished strip solves in one launch (grid: chunks x
-// strips x RHS tiles; throughput, not latency): row k of chunk p gets
-// x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p from the strip's chain solution y
-// and its final separator values, the separator row below the chunk its final
-// value; x (plus the base field) goes to the strip's output columns.  Tasks
-// (row, column) go to 8-lane groups, two per group at a time with all their
-// loads in flight together.
+// strips x RHS tiles; throughput, not latency).  The final values of the chunk's
+// two separators first: the chain kernel's values, for grouped separators
+// corrected by the level-2 spikes, x_q = y2_q - GT2_q x2_{gi-1} - GB2_q x2_{gi}.
+// Then row k of chunk p gets x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p, the
+// separator row below the chunk its final value; x (plus the base field) goes to
+// the strip's output columns.  8 lanes per value; the row tasks two per group at a
+// time with all their loads in flight together.
 template <typename C>
 __global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __restrict__ GT,
-                                                      const C* __restrict__ GB) {
+                                                         const C* __restrict__ GB, const C* __restrict__ GT2,
+                                                         const C* __restrict__ GB2) {
     __shared__ C xsv[2][4][64];   // separator above / below, per RHS (Bt <= 4)
     const int p = blockIdx.x;
     const int j = O.jlo + blockIdx.y;
@@ -1077,21 +955,40 @@ __global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __r
     const int nb = imin(O.Bt, O.B - b0);
     const StripDev st = O.g.strips[j];
     const int W = st.W, SL = spld(W);
-    const int P = O.g.P, Q1 = imax(P - 1, 1);
+    const int P = O.g.P, NG = O.g.G;
     const int off = st.lo - st.lpml;
     const int olo = imax(st.olo[O.dir] - off, 0), ohi = imin(st.ohi[O.dir] - off, W - 1);
     const int nout = ohi - olo + 1;
     if (nout <= 0) return;
-    const int4 m0 = O.g.cmeta[2 * p];
+    const int4 m0 = O.g.cmeta[2 * p], m1 = O.g.cmeta[2 * p + 1];
     const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
     const C* Y = reinterpret_cast<const C*>(O.ybuf) + (int64_t)j * O.ystride;
-    const C* XS = reinterpret_cast<const C*>(O.xsep) + (int64_t)j * O.xstride;
     const bool above = p > 0, below = p < P - 1;
-    const int tid = threadIdx.x, g = tid & 7, grp = tid >> 3, ngrp = blockDim.x >> 3;
-    for (int o = tid; o < 2 * nb * 64; o += blockDim.x) {
-        const int side = o / (nb * 64), b = (o / 64) % nb, c = o % 64;
-        const bool on = (side == 0 ? above : below) && c < W;
-        xsv[side][b][c] = on ? XS[((int64_t)(b0 + b) * Q1 + (side == 0 ? p - 1 : p)) * O.Wmax + c] : CT<C>::zero();
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = tid & 7, grp = tid >> 3, ngrp = blockDim.x >> 3;
+    auto yr = [&](int b, int k) { return Y + ((int64_t)(b0 + b) * O.g.Ny + k) * O.Wmax; };
+    // ---- final separator values
+    const int srow[2] = {r0 - 1, r1}, sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
+    for (int side = 0; side < 2; ++side) {
+        const bool on = side == 0 ? above : below;
+        const int gi = on ? sg[side] : -1;
+        for (int b = 0; b < nb; ++b) {
+            const C* y = yr(b, on ? srow[side] : r0);
+            if (gi < 0) {   // no separator, a level-2 separator or a single group: already final
+                for (int c = tid; c < 64; c += blockDim.x) xsv[side][b][c] = (on && c < W) ? y[c] : CT<C>::zero();
+                continue;
+            }
+            const bool up = gi > 0, dn = gi < NG - 1;
+            const int64_t o2 = st.red + (int64_t)(side == 0 ? p - 1 : p) * st.bs;
+            C xa[8], xb[8];
+            lane_vec(xa, yr(b, up ? sra[side] : r0), up, g, W);
+            lane_vec(xb, yr(b, dn ? srb[side] : r0), dn, g, W);
+            for (int base = w * 4; base < 64; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
+                const int c = base + (l >> 3);
+                const int cc = imin(c, W - 1);
+                const C sum = spike_dot2(GT2 + o2 + (int64_t)cc * SL, xa, up, GB2 + o2 + (int64_t)cc * SL, xb, dn, g, W);
+                if (g == 0) xsv[side][b][c] = c < W ? csub(y[c], sum) : CT<C>::zero();
+            }
+        }
     }
     __syncthreads();
     auto at = [&](int b, int k, int c) { return ((int64_t)(b0 + b) * O.g.Ny + k) * O.g.Nx + off + c; };
@@ -1127,7 +1024,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __r
                     sa[u][i] = (above && a < W) ? GT[ro + a] : CT<C>::zero();
                     sb[u][i] = (below && a < W) ? GB[ro + a] : CT<C>::zero();
                 }
-                y[u] = Y[((int64_t)(b0 + b) * O.g.Ny + k) * O.Wmax + c[u]];
+                y[u] = yr(b, k)[c[u]];
                 bv[u] = O.base ? O.base[at(b, k, c[u])] : make_double2(0.0, 0.0);
             }
 #pragma unroll
@@ -1172,7 +1069,13 @@ static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& s
     A.P2U = g.G > 1 ? pool[9] : nullptr;
     A.ybuf = wk.ybuf;
     A.parts = wk.parts;
-    A.xsep = wk.xsep;
+    A.has_prev = 0;
+    A.pybuf = wk.pybuf;
+    A.GT = pool[1];
+    A.GB = pool[2];
+    A.GT2 = pool[6];
+    A.GB2 = pool[7];
+    A.XF = pool[10];
     A.counters = wk.counters;
     A.status = wk.status;
     return A;
@@ -1193,8 +1096,9 @@ static bool plan(const StripDev& st, int zrows, int B, int& Bt, int& ring, size_
 }
 
 template <typename C>
-cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const SweepStep& step,
-                               const SweepWork& wk, void* const* pool, cudaStream_t s, KernelTimer* tm) {
+cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const StripDev* pst,
+                               const SweepStep& step, const SweepWork& wk, void* const* pool, cudaStream_t s,
+                               KernelTimer* tm) {
     int Bt, ring;
     size_t smem;
     if (!plan<C>(st, wk.zrows, wk.B, Bt, ring, smem)) return cudaErrorInvalidConfiguration;
@@ -1210,8 +1114,12 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
         attr_set = true;
     }
     SweepArgs A = make_args<C>(g, st, step, wk, pool, Bt, ring);
+    if (pst && step.prev >= 0) {
+        A.has_prev = 1;
+        A.pst = *pst;
+    }
     const int ntile = (wk.B + Bt - 1) / Bt;
-    // both kernels with programmatic stream serialisation (see pdl_wait)
+    // consecutive strip solves with programmatic stream serialisation (see pdl_wait)
     cudaLaunchAttribute pdl[1];
     pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     pdl[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1243,22 +1151,6 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
         err = cudaLaunchKernelEx(&cfg, kfn, A);
     }
     if (err != cudaSuccess) return err;
-    {
-        const XferPlan F = xfer_plan(st.W, g.G > 1, Bt, (int)sizeof(C), wk.zrows, kXferBudget);
-        static bool xattr = false;
-        if (!xattr) {
-            err = cudaFuncSetAttribute(k_sweep_transfer<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kXferBudget);
-            if (err != cudaSuccess) return err;
-            xattr = true;
-        }
-        if (F.total > kXferBudget) return cudaErrorInvalidConfiguration;
-        const cudaLaunchConfig_t cfg = config(dim3(g.P, ntile), 256, F.total);
-        TimedLaunch t(tm, "sweep_transfer", s);
-        err = cudaLaunchKernelEx(&cfg, k_sweep_transfer<C>, A, (const C*)pool[1], (const C*)pool[2],
-                                 (const C*)pool[6], (const C*)pool[7]);
-        if (err != cudaSuccess) return err;
-    }
     return cudaGetLastError();
 }
 
@@ -1266,17 +1158,19 @@ template <typename C>
 cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm) {
     if (O.nstrip <= 0) return cudaSuccess;
     TimedLaunch t(tm, "sweep_output", s);
-    k_sweep_output<C><<<dim3(O.g.P, O.nstrip, (O.B + O.Bt - 1) / O.Bt), 256, 0, s>>>(O, (const C*)pool[1],
-                                                                                      (const C*)pool[2]);
+    k_sweep_output<C><<<dim3(O.g.P, O.nstrip, (O.B + O.Bt - 1) / O.Bt), 256, 0, s>>>(
+        O, (const C*)pool[1], (const C*)pool[2], (const C*)pool[6], (const C*)pool[7]);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_outputs<float2>(const OutArgs&, void* const*, cudaStream_t, KernelTimer*);
 template cudaError_t launch_outputs<double2>(const OutArgs&, void* const*, cudaStream_t, KernelTimer*);
 
-template cudaError_t launch_strip_solve<float2>(const Geom&, int, const StripDev&, const SweepStep&,
-                                                const SweepWork&, void* const*, cudaStream_t, KernelTimer*);
-template cudaError_t launch_strip_solve<double2>(const Geom&, int, const StripDev&, const SweepStep&,
-                                                 const SweepWork&, void* const*, cudaStream_t, KernelTimer*);
+template cudaError_t launch_strip_solve<float2>(const Geom&, int, const StripDev&, const StripDev*,
+                                                const SweepStep&, const SweepWork&, void* const*, cudaStream_t,
+                                                KernelTimer*);
+template cudaError_t launch_strip_solve<double2>(const Geom&, int, const StripDev&, const StripDev*,
+                                                 const SweepStep&, const SweepWork&, void* const*, cudaStream_t,
+                                                 KernelTimer*);
 
 }  // namespace helm
