@@ -134,7 +134,7 @@ __device__ __forceinline__ C* yrow(const SweepArgs& A, int b, int k) {
 
 // Shared-memory carve-up (bytes), identical on host and device.
 struct SweepSmem {
-    uint32_t slots, zb, tv, cx, cy, xv, order, mbar, flags, total;
+    uint32_t slots, zb, tv, cx, cy, xv, order, l2, mbar, flags, total;
 };
 __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, int zrows, int Bt, int W,
                                                 int esz) {
@@ -147,6 +147,7 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
     s.xv = o; o += ((uint32_t)(6 * Bt * 64 + (zrows + 1) * Bt * 2) * esz + 15u) & ~15u;   // incoming transfer
     s.order = o; o += ((uint32_t)(6 * zrows + 8) * 4 + 15u) & ~15u;   // load order table
+    s.l2 = o; o += 64 * 4;                                               // level-2 separators (first 64)
     s.mbar = o; o += kMaxRing * 8;
     s.flags = o; o += 16;
     s.total = o;
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
     C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
     int* order = reinterpret_cast<int*>(smem + L.order);
+    int* l2s = reinterpret_cast<int*>(smem + L.l2);  // level-2 separator indices gq1[i], i < 64
     volatile int* flags = reinterpret_cast<int*>(smem + L.flags);
     const int p = blockIdx.x, tile = blockIdx.y;
     const int b0 = tile * BT;
@@ -426,9 +428,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             if (up2) order[G++] = enc(kP2U, q0 - 1);
             ngroup = G - nchunk;
             if (NG > 1) {
-                int sl[64];   // level-2 slots, loads in flight together
-                for (int i = 0; i < imin(n2, 64); ++i) sl[i] = A.g.gq1[i];
-                G += chain_order(order + G, n2, [&](int i) { return i < 64 ? sl[i] : A.g.gq1[i]; });
+                for (int i = 0; i < imin(n2, 64); ++i) l2s[i] = A.g.gq1[i];
+                G += chain_order(order + G, n2, [&](int i) { return i < 64 ? l2s[i] : A.g.gq1[i]; });
             }
         }
         nload = G;
@@ -768,12 +769,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     int* cnt = A.counters + (int64_t)tile * (NG + 1);
     auto arrive = [&](int* ctr, int expect) -> bool {   // after a barrier; true on the last arrival
         if (tid == 0) {
-            __threadfence();
-            const bool last = atomicAdd(ctr, 1) == expect;
-            if (last) {
-                *ctr = 0;
-                __threadfence();
-            }
+            // release: this CTA's writes (ordered before by the barrier); acquire: the
+            // writes every earlier arrival released
+            int old;
+            asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+            const bool last = old == expect;
+            if (last) *ctr = 0;   // next used by a later launch
             flags[0] = last ? 1 : 0;
         }
         __syncthreads();
@@ -849,7 +850,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 const int o = o0 + u * ptid;
                 if (o < tot) {
                     const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-                    const int64_t pb = pidx(b, lvl == 1 ? q0 + i : A.g.gq1[i], 0) + c;
+                    const int64_t pb = pidx(b, lvl == 1 ? q0 + i : (i < 64 ? l2s[i] : A.g.gq1[i]), 0) + c;
                     v[u] = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
                     if (lvl == 2)
                         v[u] = cadd(v[u], cadd(__ldcg(parts + pb + 2 * A.Wmax), __ldcg(parts + pb + 3 * A.Wmax)));
@@ -876,7 +877,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         if (!chain(n)) return;
         for (int o = tid; o < n * nb * W; o += blockDim.x) {
             const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-            yrow<C>(A, b0 + b, A.g.r1[lvl == 1 ? q0 + i : A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
+            yrow<C>(A, b0 + b, A.g.r1[lvl == 1 ? q0 + i : (i < 64 ? l2s[i] : A.g.gq1[i])])[c] =
+                zb[(i * BT + b) * W + c];
         }
         if (lvl == 2 || NG == 1) return;
         // the group's parts of the level-2 right-hand sides:
