@@ -70,6 +70,9 @@ struct helm_dd {
     std::vector<cd> gx_int, gx_half, gy_int, gy_half, gz_int, gz_half;
     // device
     cudaStream_t stream = nullptr, own_stream = nullptr;
+    // the output passes run beside the strip solves: a low-priority stream and its events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
     Geom geom{};
     double* d_c = nullptr;
     double* d_k2 = nullptr;
@@ -261,6 +264,13 @@ helm_status ensure_device(helm_dd* h) {
     if (h->dev_ready) return HELM_OK;
     if (!h->own_stream) CK(h, cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
     if (!h->stream) h->stream = h->own_stream;
+    if (!h->side) {
+        int lo = 0, hi = 0;
+        CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));   // lo: the lowest priority
+        CK(h, cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo));
+        CK(h, cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming));
+    }
     const int64_t nint = (int64_t)h->c.size();
     CK(h, cudaMalloc(&h->d_c, nint * sizeof(double)));
     CK(h, cudaMalloc(&h->d_k2, nvol(h) * sizeof(double)));
@@ -646,11 +656,28 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
             return launch_strip_solve<float2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, h->stream, &h->timer);
         return launch_strip_solve<double2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, h->stream, &h->timer);
     };
-    auto outputs = [&](int dir, int nstrip, double2* dst, const double2* base) -> cudaError_t {
-        OutArgs O{h->geom, dir, 0, nstrip, bf.Y, ystride, ws, B, B > 1 ? 4 : 1, dst, base};
-        if (mixed) return launch_outputs<float2>(O, h->d_pool, h->stream, &h->timer);
-        return launch_outputs<double2>(O, h->d_pool, h->stream, &h->timer);
+    const int kOutBatch = 8;    // strips per output launch
+    const int kOutCTAs = 56;    // CTAs of an output launch beside the strip solves
+    // Output columns of strips jlo .. jlo+n-1, once their solves are done: on the side
+    // stream, so that they run on the SMs the strip solves leave idle; join() makes the
+    // main stream wait for every output pass issued so far.
+    // Passes issued while strip solves still follow run on a third of the SMs (the strip
+    // solves take about two thirds); the last pass of a sweep runs on the whole GPU.
+    auto outputs = [&](int dir, int jlo, int n, double2* dst, const double2* base, bool last) -> cudaError_t {
+        if (n <= 0) return cudaSuccess;
+        OutArgs O{h->geom, dir, jlo, n, bf.Y, ystride, ws, B, B > 1 ? 4 : 1, dst, base, last ? 0 : kOutCTAs};
+        cudaError_t e = cudaEventRecord(h->ev_main, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_main, 0);
+        if (e != cudaSuccess) return e;
+        if (mixed) return launch_outputs<float2>(O, h->d_pool, h->side, &h->timer);
+        return launch_outputs<double2>(O, h->d_pool, h->side, &h->timer);
     };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(h->ev_side, h->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_side, 0);
+        return e;
+    };
+
     // forward sweep j = 1..J (Eq. solve_upward): A^(j) v^(j) = 1_{D^(j)} f - 2 delta(x-b_j) d_x v^(j-1),
     // the transfer on the first two columns of strip j taken from the solve of strip j-1
     for (int j = 0; j < J; ++j) {
@@ -663,8 +690,11 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         sp.t0 = beta[j];
         sp.tcoef = -ih2;
         CK(h, strip_solve(j, sp));
+        if ((j + 1) % kOutBatch == 0 || j == J - 1)
+            CK(h, outputs(0, j + 1 - ((j % kOutBatch) + 1), (j % kOutBatch) + 1, (J == 1) ? out : V, nullptr,
+                          j == J - 1));
     }
-    CK(h, outputs(0, J, (J == 1) ? out : V, nullptr));
+    CK(h, join());
     if (J == 1) return HELM_OK;
     // residual g = f - A v
     if ((s = dev_stencil(h, V, in, G, B)) != HELM_OK) return s;
@@ -680,8 +710,10 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         sp.t0 = beta[j + 1] + 1;
         sp.tcoef = ih2;
         CK(h, strip_solve(j, sp));
+        const int done = J - 1 - j;   // strips solved so far in this sweep: j .. J-2
+        if (done % kOutBatch == 0 || j == 0) CK(h, outputs(1, j, (done - 1) % kOutBatch + 1, out, V, j == 0));
     }
-    CK(h, outputs(1, J - 1, out, V));
+    CK(h, join());
     // D~^(J) keeps v (w = 0 there)
     CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
     return HELM_OK;
@@ -1087,6 +1119,9 @@ void helm_dd_destroy(helm_dd* h) {
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
                     &h->ws_small, &h->ws_grad})
         ws_free(*w);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_main) cudaEventDestroy(h->ev_main);
+    if (h->ev_side) cudaEventDestroy(h->ev_side);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     cudaGetLastError();
     delete h;

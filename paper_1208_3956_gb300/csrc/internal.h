@@ -124,6 +124,7 @@ struct OutArgs {
     int Wmax, B, Bt;
     double2* dst;           // [B][Ny][Nx] output field
     const double2* base;    // optional field added on output
+    int maxcta;             // CTAs of the launch (0: one per work item)
 };
 template <typename C>
 cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm);

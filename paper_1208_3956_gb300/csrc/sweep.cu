@@ -18,7 +18,7 @@
 //     level-2 separators held at zero (twisted chain z_i = a_i - E_i z_outer,
 //     x_i = z_i - F_i x_inner) and adds the group's parts of the level-2
 //     right-hand sides; the last group to finish solves the level-2 system.
-// k_sweep_output (grid: chunks x strips x RHS tiles, once per sweep)
+// k_sweep_output (work items: chunks x strips x RHS tiles, grid-stride)
 //   final separator values (grouped separators: x_q = y_q - GT2_q x2_above -
 //   GB2_q x2_below), then x_k = y_k - GT_p(k) x_{p-1} - GB_p(k) x_p on the output
 //   columns of every strip, scattered (plus the base field) to the output field.
@@ -951,99 +951,104 @@ __global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __r
                                                          const C* __restrict__ GB, const C* __restrict__ GT2,
                                                          const C* __restrict__ GB2) {
     __shared__ C xsv[2][4][64];   // separator above / below, per RHS (Bt <= 4)
-    const int p = blockIdx.x;
-    const int j = O.jlo + blockIdx.y;
-    const int b0 = blockIdx.z * O.Bt;
-    const int nb = imin(O.Bt, O.B - b0);
-    const StripDev st = O.g.strips[j];
-    const int W = st.W, SL = spld(W);
-    const int P = O.g.P, NG = O.g.G;
-    const int off = st.lo - st.lpml;
-    const int olo = imax(st.olo[O.dir] - off, 0), ohi = imin(st.ohi[O.dir] - off, W - 1);
-    const int nout = ohi - olo + 1;
-    if (nout <= 0) return;
-    const int4 m0 = O.g.cmeta[2 * p], m1 = O.g.cmeta[2 * p + 1];
-    const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
-    const C* Y = reinterpret_cast<const C*>(O.ybuf) + (int64_t)j * O.ystride;
-    const bool above = p > 0, below = p < P - 1;
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = tid & 7, grp = tid >> 3, ngrp = blockDim.x >> 3;
-    auto yr = [&](int b, int k) { return Y + ((int64_t)(b0 + b) * O.g.Ny + k) * O.Wmax; };
-    // ---- final separator values
-    const int srow[2] = {r0 - 1, r1}, sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
-    for (int side = 0; side < 2; ++side) {
-        const bool on = side == 0 ? above : below;
-        const int gi = on ? sg[side] : -1;
+    const int ntile = (O.B + O.Bt - 1) / O.Bt;
+    const int nitem = O.g.P * O.nstrip * ntile;
+    for (int item = blockIdx.x; item < nitem; item += gridDim.x) {   // (chunk, strip, RHS tile)
+        __syncthreads();   // xsv of the previous item consumed
+        const int p = item % O.g.P;
+        const int j = O.jlo + (item / O.g.P) % O.nstrip;
+        const int b0 = (item / (O.g.P * O.nstrip)) * O.Bt;
+        const int nb = imin(O.Bt, O.B - b0);
+        const StripDev st = O.g.strips[j];
+        const int W = st.W, SL = spld(W);
+        const int P = O.g.P, NG = O.g.G;
+        const int off = st.lo - st.lpml;
+        const int olo = imax(st.olo[O.dir] - off, 0), ohi = imin(st.ohi[O.dir] - off, W - 1);
+        const int nout = ohi - olo + 1;
+        if (nout <= 0) continue;
+        const int4 m0 = O.g.cmeta[2 * p], m1 = O.g.cmeta[2 * p + 1];
+        const int r0 = m0.x, r1 = m0.y, m = r1 - r0;
+        const C* Y = reinterpret_cast<const C*>(O.ybuf) + (int64_t)j * O.ystride;
+        const bool above = p > 0, below = p < P - 1;
+        const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, g = tid & 7, grp = tid >> 3, ngrp = blockDim.x >> 3;
+        auto yr = [&](int b, int k) { return Y + ((int64_t)(b0 + b) * O.g.Ny + k) * O.Wmax; };
+        // ---- final separator values
+        const int srow[2] = {r0 - 1, r1}, sg[2] = {m0.z, m0.w}, sra[2] = {m1.x, m1.z}, srb[2] = {m1.y, m1.w};
+        for (int side = 0; side < 2; ++side) {
+            const bool on = side == 0 ? above : below;
+            const int gi = on ? sg[side] : -1;
+            for (int b = 0; b < nb; ++b) {
+                const C* y = yr(b, on ? srow[side] : r0);
+                if (gi < 0) {   // no separator, a level-2 separator or a single group: already final
+                    for (int c = tid; c < 64; c += blockDim.x) xsv[side][b][c] = (on && c < W) ? y[c] : CT<C>::zero();
+                    continue;
+                }
+                const bool up = gi > 0, dn = gi < NG - 1;
+                const int64_t o2 = st.red + (int64_t)(side == 0 ? p - 1 : p) * st.bs;
+                C xa[8], xb[8];
+                lane_vec(xa, yr(b, up ? sra[side] : r0), up, g, W);
+                lane_vec(xb, yr(b, dn ? srb[side] : r0), dn, g, W);
+                for (int base = w * 4; base < 64; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
+                    const int c = base + (l >> 3);
+                    const int cc = imin(c, W - 1);
+                    const C sum = spike_dot2(GT2 + o2 + (int64_t)cc * SL, xa, up, GB2 + o2 + (int64_t)cc * SL, xb, dn, g, W);
+                    if (g == 0) xsv[side][b][c] = c < W ? csub(y[c], sum) : CT<C>::zero();
+                }
+            }
+        }
+        __syncthreads();
+        auto at = [&](int b, int k, int c) { return ((int64_t)(b0 + b) * O.g.Ny + k) * O.g.Nx + off + c; };
+        if (below)   // the separator row below the chunk: its final value
+            for (int o = tid; o < nb * nout; o += blockDim.x) {
+                const int b = o / nout, c = olo + o % nout;
+                double2 v = to_d2(xsv[1][b][c]);
+                if (O.base) v = cadd(v, O.base[at(b, r1, c)]);
+                O.dst[at(b, r1, c)] = v;
+            }
+        const int ntask = m * nout;
         for (int b = 0; b < nb; ++b) {
-            const C* y = yr(b, on ? srow[side] : r0);
-            if (gi < 0) {   // no separator, a level-2 separator or a single group: already final
-                for (int c = tid; c < 64; c += blockDim.x) xsv[side][b][c] = (on && c < W) ? y[c] : CT<C>::zero();
-                continue;
-            }
-            const bool up = gi > 0, dn = gi < NG - 1;
-            const int64_t o2 = st.red + (int64_t)(side == 0 ? p - 1 : p) * st.bs;
             C xa[8], xb[8];
-            lane_vec(xa, yr(b, up ? sra[side] : r0), up, g, W);
-            lane_vec(xb, yr(b, dn ? srb[side] : r0), dn, g, W);
-            for (int base = w * 4; base < 64; base += (blockDim.x >> 5) * 4) {   // warp-uniform trip count
-                const int c = base + (l >> 3);
-                const int cc = imin(c, W - 1);
-                const C sum = spike_dot2(GT2 + o2 + (int64_t)cc * SL, xa, up, GB2 + o2 + (int64_t)cc * SL, xb, dn, g, W);
-                if (g == 0) xsv[side][b][c] = c < W ? csub(y[c], sum) : CT<C>::zero();
-            }
-        }
-    }
-    __syncthreads();
-    auto at = [&](int b, int k, int c) { return ((int64_t)(b0 + b) * O.g.Ny + k) * O.g.Nx + off + c; };
-    if (below)   // the separator row below the chunk: its final value
-        for (int o = tid; o < nb * nout; o += blockDim.x) {
-            const int b = o / nout, c = olo + o % nout;
-            double2 v = to_d2(xsv[1][b][c]);
-            if (O.base) v = cadd(v, O.base[at(b, r1, c)]);
-            O.dst[at(b, r1, c)] = v;
-        }
-    const int ntask = m * nout;
-    for (int b = 0; b < nb; ++b) {
-        C xa[8], xb[8];
-        lane_vec(xa, xsv[0][b], above, g, W);
-        lane_vec(xb, xsv[1][b], below, g, W);
-        for (int t0 = 0; t0 < ntask; t0 += 2 * ngrp) {   // uniform trip count: every lane shuffles
-            int kk[2], c[2];
-            bool live[2];
-            C sa[2][8], sb[2][8], y[2];
-            double2 bv[2];
+            lane_vec(xa, xsv[0][b], above, g, W);
+            lane_vec(xb, xsv[1][b], below, g, W);
+            for (int t0 = 0; t0 < ntask; t0 += 2 * ngrp) {   // uniform trip count: every lane shuffles
+                int kk[2], c[2];
+                bool live[2];
+                C sa[2][8], sb[2][8], y[2];
+                double2 bv[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {   // loads of both tasks first
-                const int t = t0 + u * ngrp + grp;
-                live[u] = t < ntask;
-                const int tc = imin(t, ntask - 1);
-                kk[u] = tc / nout;
-                c[u] = olo + tc % nout;
-                const int k = r0 + kk[u];
-                const int64_t ro = st.fac + (int64_t)k * st.bs + (int64_t)c[u] * SL;
+                for (int u = 0; u < 2; ++u) {   // loads of both tasks first
+                    const int t = t0 + u * ngrp + grp;
+                    live[u] = t < ntask;
+                    const int tc = imin(t, ntask - 1);
+                    kk[u] = tc / nout;
+                    c[u] = olo + tc % nout;
+                    const int k = r0 + kk[u];
+                    const int64_t ro = st.fac + (int64_t)k * st.bs + (int64_t)c[u] * SL;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int a = g + 8 * i;
-                    sa[u][i] = (above && a < W) ? GT[ro + a] : CT<C>::zero();
-                    sb[u][i] = (below && a < W) ? GB[ro + a] : CT<C>::zero();
+                    for (int i = 0; i < 8; ++i) {
+                        const int a = g + 8 * i;
+                        sa[u][i] = (above && a < W) ? GT[ro + a] : CT<C>::zero();
+                        sb[u][i] = (below && a < W) ? GB[ro + a] : CT<C>::zero();
+                    }
+                    y[u] = yr(b, k)[c[u]];
+                    bv[u] = O.base ? O.base[at(b, k, c[u])] : make_double2(0.0, 0.0);
                 }
-                y[u] = yr(b, k)[c[u]];
-                bv[u] = O.base ? O.base[at(b, k, c[u])] : make_double2(0.0, 0.0);
-            }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                C s0 = CT<C>::zero(), s1 = CT<C>::zero();
+                for (int u = 0; u < 2; ++u) {
+                    C s0 = CT<C>::zero(), s1 = CT<C>::zero();
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    s0 = cfma(sa[u][i], xa[i], s0);
-                    s1 = cfma(sb[u][i], xb[i], s1);
+                    for (int i = 0; i < 8; ++i) {
+                        s0 = cfma(sa[u][i], xa[i], s0);
+                        s1 = cfma(sb[u][i], xb[i], s1);
+                    }
+                    C sum = cadd(s0, s1);
+#pragma unroll
+                    for (int o = 1; o <= 4; o <<= 1) {
+                        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+                        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+                    }
+                    if (live[u] && g == 0) O.dst[at(b, r0 + kk[u], c[u])] = cadd(to_d2(csub(y[u], sum)), bv[u]);
                 }
-                C sum = cadd(s0, s1);
-#pragma unroll
-                for (int o = 1; o <= 4; o <<= 1) {
-                    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
-                    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
-                }
-                if (live[u] && g == 0) O.dst[at(b, r0 + kk[u], c[u])] = cadd(to_d2(csub(y[u], sum)), bv[u]);
             }
         }
     }
@@ -1160,8 +1165,10 @@ template <typename C>
 cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm) {
     if (O.nstrip <= 0) return cudaSuccess;
     TimedLaunch t(tm, "sweep_output", s);
-    k_sweep_output<C><<<dim3(O.g.P, O.nstrip, (O.B + O.Bt - 1) / O.Bt), 256, 0, s>>>(
-        O, (const C*)pool[1], (const C*)pool[2], (const C*)pool[6], (const C*)pool[7]);
+    const int nitem = O.g.P * O.nstrip * ((O.B + O.Bt - 1) / O.Bt);
+    const int grid = O.maxcta > 0 ? imin(nitem, O.maxcta) : nitem;
+    k_sweep_output<C><<<grid, 256, 0, s>>>(O, (const C*)pool[1], (const C*)pool[2], (const C*)pool[6],
+                                         (const C*)pool[7]);
     return cudaGetLastError();
 }
 
