@@ -170,8 +170,11 @@ helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc,
                              const int64_t* rec_idx, int nrec, const double* d,
                              double tol, double* misfit, double* grad_m);
 
-/* Run all device work of the handle on this cudaStream_t (NULL = the handle's
- * own stream).  The caller keeps ownership of the stream. */
+/* Order all device work of the handle on this cudaStream_t (NULL = the handle's
+ * own stream).  The output passes of a sweep run on an internal low-priority
+ * stream beside the strip solves; every call joins it back to this stream (an
+ * event wait) before the call's results are used.  The caller keeps ownership
+ * of the stream. */
 helm_status helm_dd_set_stream(helm_dd* h, void* stream);
 
 /* Per-kernel timing of the calls that follow: when enabled, each launch of the
