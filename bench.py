@@ -174,11 +174,12 @@ def run_reference(args):
     value = r["ndof"] / r["t_solve"] / 1e6
     line = {
         "impl": "reference", "metric": "RHS-solves/s to 1e-6 FP64 residual (Mdof*RHS/s)", "value": value,
-        "unit": "Mdof*RHS/s", "n_gpus": 0, "steps": r["steps"], "warmup": 0,
+        "unit": "Mdof*RHS/s", "n_gpus": world, "steps": r["steps"], "warmup": 0,
         "ms_per_step": r["t_solve"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128", "data": "synthetic (seeded smooth random medium)",
         "config": {"workload": WORKLOAD, "grid": "1023x1023 interior, 1055x1055 padded", "J": 64, "w_sub": 12,
-                   "w_outer": 16, "nrhs": 1, "tol": 1e-6, "restart": 20},
+                   "w_outer": 16, "nrhs_per_gpu": 1, "precision": "c128 oracle", "tol": 1e-6, "restart": 20,
+                   "iters": [r["iters"]], "rel_res": r["rel_res"]},
         "cpu_baseline": {"value": value, "unit": "Mdof*RHS/s", "cores": 1, "kind": "oracle",
                          "sample": f"{r['steps']} full oracle solve(s) of the workload (SuperLU strip solves, "
                                    f"single-threaded), factor {r['t_factor']:.1f}s excluded, "
