@@ -87,6 +87,14 @@ struct helm_dd {
     void* d_pool[11] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                         nullptr};
     int* d_status = nullptr;
+    // 3-D strips: s_x s_z per block entry (working precision) and its per-strip offsets,
+    // the offset of s_z in d_ct, the y-couplings -alpha_y(y_{k-1/2})/h^2 and the row
+    // stride of the strip right-hand-side / solution buffers
+    void* d_slab_sxz = nullptr;
+    std::vector<int64_t> slab_sxz_off;
+    int64_t ct_sz = 0;
+    std::vector<double2> slab_cy;
+    int slab_ld = 0;
     size_t esize = 16;
     bool factored = false;
     bool prepared = false;
@@ -315,6 +323,8 @@ helm_status prepare_geom(helm_dd* h) {
         s.ctab = (int64_t)ctv.size();
         for (int c = 0; c < s.W; ++c) ctv.push_back(1.0 / tabs[stab0 + s.tab + c]);
     }
+    h->ct_sz = (int64_t)ctv.size();   // s_z(z) (3-D strips)
+    for (int z = 0; z < (int)h->N[2]; ++z) ctv.push_back(1.0 / h->gz_int[z]);
     if (h->d_ct) cudaFree(h->d_ct);
     h->d_ct = nullptr;
     CK(h, cudaMalloc(&h->d_ct, ctv.size() * h->esize));
@@ -409,6 +419,109 @@ helm_status prepare_geom(helm_dd* h) {
     return HELM_OK;
 }
 
+
+// Output columns and transfer columns of strip j: the forward sweep keeps v^(j) on
+// D^(j), the backward w^(j) on D~^(j); the transfer leaves strip j on its last two
+// physical columns (forward, to the right neighbour) or its first two (backward).
+void set_strip_io(const helm_dd* h, StripDev& s, int j) {
+    s.olo[0] = h->beta[j] + 1;
+    s.ohi[0] = h->beta[j + 1];
+    s.olo[1] = j > 0 ? h->beta[j] + 2 : 0;
+    s.ohi[1] = h->beta[j + 1] + 1;
+    s.xc[1] = s.lpml + (s.hi - s.lo);
+    s.xc[0] = s.xc[1] - 1;
+    s.xc[2] = s.lpml;
+    s.xc[3] = s.lpml + 1;
+}
+
+// Algorithm 1 on the strips of a 3-D grid: one dense block of n = W N_z unknowns per
+// grid row y, X_k = S_k^{-1} stored for every row (slab3d.cu).
+helm_status factor_slabs(helm_dd* h) {
+    const int Ny = (int)h->N[1], Nz = (int)h->N[2];
+    int64_t fac = 0;
+    int nmax = 0, ldmax = 0;
+    for (size_t jj = 0; jj < h->strips.size(); ++jj) {
+        auto& s = h->strips[jj];
+        set_strip_io(h, s, (int)jj);
+        const int n = s.W * Nz;
+        s.nj = 0;
+        s.ld = (n + 3) & ~3;   // rows start 32-byte aligned, columns n.. zero
+        s.bs = (int64_t)n * s.ld;
+        s.fac = fac;
+        s.red = 0;
+        s.xf = 0;
+        fac += (int64_t)Ny * s.bs;
+        nmax = std::max(nmax, n);
+        ldmax = std::max(ldmax, s.ld);
+    }
+    if (nmax > 2048)
+        return fail(h, HELM_EINVAL, "a 3-D strip block has more than 2048 unknowns (W * N_z); use more strips");
+    for (auto& p : h->d_pool) { if (p) cudaFree(p); p = nullptr; }
+    h->factored = false;
+    CK(h, cudaMalloc(&h->d_pool[0], (size_t)fac * h->esize));
+    // s_x(c) s_z(z) per block entry, and the y-couplings
+    std::vector<cd> sxz;
+    h->slab_sxz_off.assign(h->strips.size(), 0);
+    for (size_t jj = 0; jj < h->strips.size(); ++jj) {
+        const auto& s = h->strips[jj];
+        h->slab_sxz_off[jj] = (int64_t)sxz.size();
+        for (int z = 0; z < Nz; ++z)
+            for (int c = 0; c < s.W; ++c) sxz.push_back(1.0 / (strip_alpha_at(h, s, 2 * c) * h->gz_int[z]));
+    }
+    const double ih2 = 1.0 / (h->h * h->h);
+    h->slab_cy.assign(Ny + 1, make_double2(0.0, 0.0));
+    for (int k = 0; k <= Ny; ++k) h->slab_cy[k] = to_d2h(-h->gy_half[k] * ih2);
+    if (h->d_slab_sxz) cudaFree(h->d_slab_sxz);
+    h->d_slab_sxz = nullptr;
+    CK(h, cudaMalloc(&h->d_slab_sxz, sxz.size() * h->esize));
+    if (h->esize == sizeof(float2)) {
+        std::vector<float2> f(sxz.size());
+        for (size_t i = 0; i < sxz.size(); ++i) f[i] = make_float2((float)sxz[i].real(), (float)sxz[i].imag());
+        CK(h, cudaMemcpy(h->d_slab_sxz, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<double2> f(sxz.size());
+        for (size_t i = 0; i < sxz.size(); ++i) f[i] = to_d2h(sxz[i]);
+        CK(h, cudaMemcpy(h->d_slab_sxz, f.data(), f.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    h->slab_ld = ldmax;
+    CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
+                          cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    // scratch of the block inversions
+    const size_t es = h->esize;
+    const size_t mbytes = (size_t)ldmax * nmax * es, multb = (size_t)2 * ldmax * es;
+    const size_t ibytes = (size_t)(2 * nmax + 2 + 2) * sizeof(int);
+    void* scratch = nullptr;
+    CK(h, cudaMalloc(&scratch, mbytes + multb + ibytes));
+    SlabScratch sc{};
+    sc.M = scratch;
+    sc.mult = (char*)scratch + mbytes;
+    sc.ldm = ldmax;
+    sc.perm = (int*)((char*)scratch + mbytes + multb);
+    sc.pinv = sc.perm + nmax;
+    sc.pivrow = sc.pinv + nmax;
+    sc.bar = (unsigned*)(sc.pivrow + 2);
+    cudaError_t e = cudaSuccess;
+    for (size_t jj = 0; jj < h->strips.size() && e == cudaSuccess; ++jj) {
+        if (h->prec == HELM_PREC_MIXED)
+            e = launch_slab_factor<float2>(h->geom, h->strips[jj], h->d_pool[0], sc, h->d_status, h->stream, &h->timer);
+        else
+            e = launch_slab_factor<double2>(h->geom, h->strips[jj], h->d_pool[0], sc, h->d_status, h->stream,
+                                            &h->timer);
+    }
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return fail_cuda(h, "3-D strip factor kernels", e);
+    if (st == 7) {
+        cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+        return fail(h, HELM_ETIMEOUT, "a bounded device wait in the 3-D strip factorisation gave up");
+    }
+    if (st != 0) return fail(h, HELM_ENUMERIC, "singular block in the strip factorisation");
+    h->factored = true;
+    return HELM_OK;
+}
 
 }  // namespace
 
@@ -516,28 +629,19 @@ helm_status helm_dd_factor(helm_dd* h) {
     if (!h) return HELM_EINVAL;
     helm_status ps = prepare_geom(h);
     if (ps != HELM_OK) return ps;
-    if (h->dim != 2) return fail(h, HELM_EINVAL, "strip factorisation is implemented for 2-D grids");
+    if (h->dim == 3) return factor_slabs(h);
     const int Ny = (int)h->N[1];
     int64_t fac = 0, red = 0, xf = 0;
     for (size_t jj = 0; jj < h->strips.size(); ++jj) {
         auto& s = h->strips[jj];
         const int j = (int)jj;
-        // output columns: the forward sweep keeps v^(j) on D^(j), the backward w^(j) on D~^(j)
-        s.olo[0] = h->beta[j] + 1;
-        s.ohi[0] = h->beta[j + 1];
-        s.olo[1] = j > 0 ? h->beta[j] + 2 : 0;
-        s.ohi[1] = h->beta[j + 1] + 1;
+        set_strip_io(h, s, j);
         s.nj = sweep_nj(s.W);
         s.ld = 4 * s.nj + 2;
         s.bs = (int64_t)s.W * s.ld;   // sweep layout; even, so blocks stay 16-byte aligned
         s.fac = fac;
         s.red = red;
         s.xf = xf;
-        // transfer columns (strip-local): forward to the right neighbour, backward to the left
-        s.xc[1] = s.lpml + (s.hi - s.lo);
-        s.xc[0] = s.xc[1] - 1;
-        s.xc[2] = s.lpml;
-        s.xc[3] = s.lpml + 1;
         fac += (int64_t)Ny * s.bs;
         red += (int64_t)std::max(h->P - 1, 1) * s.bs;
         xf += (int64_t)Ny * 16 * spld(s.W);
@@ -614,9 +718,14 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
     sz[1] = sz[0];
     sz[2] = (size_t)h->J * B * Ny * work_stride(h) * h->esize;
     sz[3] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
+    if (h->dim == 3) {   // right-hand sides and two strip solutions, [B][Ny][slab_ld] each
+        sz[2] = (size_t)3 * B * Ny * h->slab_ld * h->esize;
+        sz[3] = 256;
+    }
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
+helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
 
 // P applied to B device fields (Section 2.1): in -> out (distinct buffers).
 helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
@@ -633,6 +742,7 @@ helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
 
 // The double sweep itself on caller-provided buffers.
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf) {
+    if (h->dim == 3) return run_precond_slabs(h, in, out, B, bf);
     const int Ny = (int)h->N[1], Nx = (int)h->N[0];
     helm_status s;
     if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
@@ -716,6 +826,62 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     CK(h, join());
     // D~^(J) keeps v (w = 0 there)
     CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
+    return HELM_OK;
+}
+
+// The double sweep on the strips of a 3-D grid (same steps as run_precond; each strip
+// solve is the block substitution of slab3d.cu, its output written right after it).
+helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf) {
+    const int Ny = (int)h->N[1], Nx = (int)h->N[0], Nz = (int)h->N[2];
+    const int J = h->J, ld = h->slab_ld;
+    const auto& beta = h->beta;
+    const double ih2 = 1.0 / (h->h * h->h);
+    const bool mixed = h->prec == HELM_PREC_MIXED;
+    const size_t vb = (size_t)B * Ny * ld * h->esize;
+    char* rbuf = (char*)bf.Y;
+    char* ybuf[2] = {rbuf + vb, rbuf + 2 * vb};
+    double2* V = bf.V;
+    helm_status s;
+    auto solve = [&](int j, const SweepStep& sp, int slot) -> cudaError_t {
+        SlabWork wk{rbuf, ybuf[slot], sp.prev >= 0 ? ybuf[slot ^ 1] : nullptr,
+                    (const char*)h->d_slab_sxz + h->slab_sxz_off[j] * (int64_t)h->esize, h->ct_sz,
+                    h->slab_cy.data(), ld, B};
+        const StripDev* pst = sp.prev >= 0 ? &h->strips[sp.prev] : nullptr;
+        if (mixed) return launch_slab_solve<float2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);
+        return launch_slab_solve<double2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);
+    };
+    auto emit = [&](int j, int dir, int slot, double2* dst, const double2* base) -> cudaError_t {
+        if (mixed) return launch_slab_out<float2>(h->geom, h->strips[j], dir, ybuf[slot], ld, dst, base, B, h->stream, &h->timer);
+        return launch_slab_out<double2>(h->geom, h->strips[j], dir, ybuf[slot], ld, dst, base, B, h->stream, &h->timer);
+    };
+    for (int j = 0; j < J; ++j) {   // forward sweep (Eq. solve_upward)
+        SweepStep sp{};
+        sp.src = in;
+        sp.mlo = beta[j] + 1;
+        sp.mhi = beta[j + 1];
+        sp.prev = j > 0 ? j - 1 : -1;
+        sp.pdir = 0;
+        sp.t0 = beta[j];
+        sp.tcoef = -ih2;
+        CK(h, solve(j, sp, j & 1));
+        CK(h, emit(j, 0, j & 1, J == 1 ? out : V, nullptr));
+    }
+    if (J == 1) return HELM_OK;
+    if ((s = dev_stencil(h, V, in, bf.G, B)) != HELM_OK) return s;
+    for (int j = J - 2; j >= 0; --j) {   // backward sweep (Eq. solve_downward), w^(J) = 0
+        SweepStep sp{};
+        sp.src = bf.G;
+        sp.mlo = j > 0 ? beta[j] + 2 : 0;
+        sp.mhi = beta[j + 1] + 1;
+        sp.prev = (j + 1 <= J - 2) ? j + 1 : -1;
+        sp.pdir = 1;
+        sp.t0 = beta[j + 1] + 1;
+        sp.tcoef = ih2;
+        const int slot = (J - 2 - j) & 1;
+        CK(h, solve(j, sp, slot));
+        CK(h, emit(j, 1, slot, out, V));
+    }
+    CK(h, launch_copy_cols(V, out, B, Nx, Ny, Nz, beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
     return HELM_OK;
 }
 
@@ -1115,6 +1281,7 @@ void helm_dd_destroy(helm_dd* h) {
     cudaFree(h->d_status);
     for (auto p : h->d_pool) cudaFree(p);
     cudaFree(h->d_ct);
+    cudaFree(h->d_slab_sxz);
     cudaFree(h->d_counters);
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
                     &h->ws_small, &h->ws_grad})

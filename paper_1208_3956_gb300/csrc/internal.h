@@ -135,6 +135,45 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, co
                                const SweepStep& step, const SweepWork& wk, void* const* pool, cudaStream_t s,
                                KernelTimer* tm);
 
+// ---- slab3d.cu: strips of a 3-D grid (one dense block of n = W N_z unknowns per row y)
+// Scratch of the factorisation: the block being inverted (column-major, ldm >= n),
+// the exchanged pivot column (2 x ldm), the row exchanges and their inverse, the
+// published pivot rows (2) and the grid-barrier counter.
+struct SlabScratch {
+    void* M;
+    void* mult;
+    int ldm;
+    int* perm;
+    int* pinv;
+    int* pivrow;
+    unsigned* bar;
+};
+// One strip solve: right-hand sides and solution [B][Ny][ld], the previous strip
+// solve's solution (for the transfer), s_x s_z per block entry, s_z in the table ct.
+struct SlabWork {
+    void* rbuf;
+    void* ybuf;
+    const void* pybuf;
+    const void* sxz;          // this strip's s_x(c) s_z(z), working precision, n entries
+    int64_t ct_sz;            // offset of s_z(z) in Geom::ct
+    const double2* cy_host;   // host: -alpha_y(y_{k-1/2}) / h^2, k = 0 .. Ny
+    int ld;                   // row stride of rbuf / ybuf / pybuf (>= every strip's n)
+    int B;
+};
+// Factor blocks X_k = S_k^{-1} of strip st into pool + st.fac (row-major, leading
+// dimension st.ld, st.bs elements per block), k = 0 .. Ny-1.
+template <typename C>
+cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, const SlabScratch& sc, int* status,
+                               cudaStream_t s, KernelTimer* tm);
+// Right-hand side and block forward / back substitution of strip st (into wk.ybuf).
+template <typename C>
+cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev* pst, const SweepStep& sp,
+                              const SlabWork& wk, const void* pool, cudaStream_t s, KernelTimer* tm);
+// dst = [base +] the strip solution on padded columns st.olo[dir] .. st.ohi[dir].
+template <typename C>
+cudaError_t launch_slab_out(const Geom& g, const StripDev& st, int dir, const void* ybuf, int ld, double2* dst,
+                            const double2* base, int B, cudaStream_t s, KernelTimer* tm);
+
 // ---- field.cu: FP64 grid kernels
 cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, int nz, int w, double omega,
                       cudaStream_t s);

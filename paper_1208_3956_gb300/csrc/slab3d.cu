@@ -1,0 +1,564 @@
+// Three-dimensional strips (Section 2.2, Algorithm 1 and the sweeps of Section
+// 2.1 on a 3-D grid).  A strip is a slab of W x-columns by all N_z planes; at
+// grid row y = k its unknowns form one block of n = W N_z points, ordered
+// e = z W + c (strip-local column c fastest).  S^(j) A^(j) is block tridiagonal
+// along y with these dense-after-elimination blocks and diagonal couplings:
+//   D_k(e,e)     = [s_y s_z (a_x(c+1/2) + a_x(c-1/2))
+//                   + s_x s_z (a_y(k+1/2) + a_y(k-1/2))
+//                   + s_x s_y (a_z(z+1/2) + a_z(z-1/2))] / h^2 - s_x s_y s_z k^2
+//   D_k(e,e+1)   = -s_y s_z a_x(c+1/2) / h^2            (c+1 < W, same plane)
+//   D_k(e,e+W)   = -s_x s_y a_z(z+1/2) / h^2
+//   C_k(e)       = -s_x(c) s_z(z) a_y(k-1/2) / h^2      (couples rows k-1, k)
+// with s = 1/alpha at integer points and a = alpha at half points.
+//
+// Factorisation (Algorithm 1, top down): X_k = S_k^{-1},
+//   S_0 = D_0,  S_k = D_k - C_k X_{k-1} C_k,
+// each S_k inverted by Gauss-Jordan elimination with partial (row) pivoting on
+// the whole GPU (one cooperative launch per block).  Solve of a strip
+// (block forward and back substitution):
+//   y_k = X_k (r_k - C_k y_{k-1}),   k = 0 .. N_y-1
+//   x_k = y_k - X_k C_{k+1} x_{k+1}, k = N_y-2 .. 0
+// one launch per block row, each a matrix-vector product that streams X_k from
+// HBM: the X_k rows of a CTA are prefetched into L2 before the launch waits for
+// its predecessor (programmatic dependent launch), so the stream of factor bytes
+// runs on while the previous step finishes.
+#include "common.cuh"
+#include "strip_ops.cuh"
+#include "internal.h"
+
+namespace helm {
+namespace {
+
+constexpr uint32_t kBarPolls = 1u << 20;   // polls of a grid barrier before it gives up (about a second)
+constexpr int kGjThreads = 256;
+constexpr int kGjRowsPerThread = 8;        // n <= kGjThreads * kGjRowsPerThread
+constexpr int kGjMaxCols = 64;             // columns owned by one CTA
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename C> __device__ __forceinline__ C ldcg(const C* p);
+template <> __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
+
+// Barrier over all CTAs of a cooperative launch (co-resident by construction).
+// The counter rises by one per CTA and barrier; target = CTAs x barriers so far.
+// A wait that gives up records 7 in the status word and returns false.
+__device__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        unsigned v = ld_acquire_gpu(ctr);
+        for (uint32_t it = 0; v < target && it < kBarPolls; ++it) {
+            __nanosleep(32);
+            v = ld_acquire_gpu(ctr);
+        }
+        ok = v >= target;
+        if (!ok) atomicExch(status, 7);
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// ------------------------------------------------------------ block entries
+__device__ __forceinline__ double2 slab_sz(const Geom& g, int z) { return cinv(g.gz_int[z]); }
+
+__device__ double2 slab_diag(const Geom& g, const StripDev& st, int k, int c, int z) {
+    const double2 sx = strip_sx(g, st, c), sy = glob_sy(g, k), sz = slab_sz(g, z);
+    const double2 xs = cadd(strip_ax_half(g, st, c + 1), strip_ax_half(g, st, c));
+    const double2 ys = cadd(g.gy_half[k + 1], g.gy_half[k]);
+    const double2 zs = cadd(g.gz_half[z + 1], g.gz_half[z]);
+    double2 d = cadd(cadd(cmul(cmul(sy, sz), xs), cmul(cmul(sx, sz), ys)), cmul(cmul(sx, sy), zs));
+    d = cscale(d, g.inv_h2);
+    const double k2 = g.k2[((int64_t)z * g.Ny + k) * g.Nx + strip_k2_col(st, c)];
+    return csub(d, cscale(cmul(cmul(sx, sy), sz), k2));
+}
+// entry (e, e+1), e = z W + c, c + 1 < W
+__device__ double2 slab_xoff(const Geom& g, const StripDev& st, int k, int c, int z) {
+    return cscale(cmul(cmul(glob_sy(g, k), slab_sz(g, z)), strip_ax_half(g, st, c + 1)), -g.inv_h2);
+}
+// entry (e, e+W), z + 1 < N_z
+__device__ double2 slab_zoff(const Geom& g, const StripDev& st, int k, int c, int z) {
+    return cscale(cmul(cmul(strip_sx(g, st, c), glob_sy(g, k)), g.gz_half[z + 1]), -g.inv_h2);
+}
+// C_k(e), k >= 1
+__device__ double2 slab_coupling(const Geom& g, const StripDev& st, int k, int c, int z) {
+    return cscale(cmul(cmul(strip_sx(g, st, c), slab_sz(g, z)), g.gy_half[k]), -g.inv_h2);
+}
+// D_k(r, a) for any pair (zero off the stencil)
+__device__ double2 slab_dentry(const Geom& g, const StripDev& st, int k, int r, int a) {
+    const int W = st.W;
+    const int lo = imin(r, a), d = r > a ? r - a : a - r;
+    const int c = lo % W, z = lo / W;
+    if (d == 0) return slab_diag(g, st, k, c, z);
+    if (d == 1 && c + 1 < W) return slab_xoff(g, st, k, c, z);
+    if (d == W) return slab_zoff(g, st, k, c, z);
+    return make_double2(0.0, 0.0);
+}
+
+// M (column-major, ldm) = D_k - C_k Xp C_k, Xp = X_{k-1} in the row-major sweep
+// layout (leading dimension ld), or M = D_k for k = 0.  32 x 32 tiles.
+template <typename C>
+__global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, const C* __restrict__ Xp, int ld,
+                                                    C* __restrict__ M, int ldm) {
+    __shared__ C tile[32][33];
+    __shared__ C cr[32], cc[32];
+    const int n = st.W * g.Nz;
+    const int r0 = blockIdx.y * 32, a0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 32
+    if (Xp) {
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i, a = a0 + tx;
+            tile[i][tx] = (r < n && a < n) ? Xp[(int64_t)r * ld + a] : CT<C>::zero();
+        }
+        if (threadIdx.x < 64) {
+            const int e = (threadIdx.x < 32 ? r0 : a0) + tx;
+            const C v = e < n ? CT<C>::from(slab_coupling(g, st, k, e % st.W, e / st.W)) : CT<C>::zero();
+            (threadIdx.x < 32 ? cr : cc)[tx] = v;
+        }
+    }
+    __syncthreads();
+    // write column a0+i, rows r0+tx (coalesced along rows)
+    for (int i = ty; i < 32; i += 8) {
+        const int a = a0 + i, r = r0 + tx;
+        if (a >= n || r >= n) continue;
+        C v = CT<C>::from(slab_dentry(g, st, k, r, a));
+        if (Xp) v = csub(v, cmul(cmul(cr[tx], tile[tx][i]), cc[i]));
+        M[(int64_t)a * ldm + r] = v;
+    }
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of the n x n matrix M
+// (column-major, ldm), columns dealt round-robin to the CTAs of a cooperative
+// launch.  Step i: rows i and p (the largest |M(r,i)|, r >= i) are exchanged,
+// the pivot row is scaled by 1/M(p,i) with M(i,i) <- 1/pivot, and every other
+// row r loses m_r times it with M(r,i) <- -m_r/pivot (m_r = M(r,i) after the
+// exchange).  The owner of column i publishes p and the exchanged column m
+// (double-buffered by step parity) before the barrier of step i; it updates
+// column i+1 first, so the next pivot search starts as soon as possible.  The
+// result is (P M)^{-1} for the product P of the exchanges; pinv[c] = the
+// position of original row c after all exchanges, so M^{-1}(:, c) = result(:, pinv[c]).
+template <typename C>
+__global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int n, int ldm, int* __restrict__ perm,
+                                                         int* __restrict__ pinv, C* __restrict__ mult,
+                                                         int* __restrict__ pivrow, unsigned* __restrict__ bar,
+                                                         int* __restrict__ status) {
+    using R = typename CT<C>::R;
+    __shared__ C s_ai[kGjMaxCols], s_ap[kGjMaxCols];
+    __shared__ R s_best[kGjThreads / 32];
+    __shared__ int s_bidx[kGjThreads / 32];
+    __shared__ int s_p;
+    __shared__ int s_rows[kGjThreads * kGjRowsPerThread];
+    const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int ncol = b < n ? (n - 1 - b) / nb + 1 : 0;   // owned columns b, b+nb, ...
+
+    // pivot search and publication for column i (owned by this CTA, up to date)
+    auto publish = [&](int i) {
+        const C* col = M + (int64_t)i * ldm;
+        R best = (R)-1;
+        int bi = n;
+        for (int r = i + tid; r < n; r += kGjThreads) {
+            const R v = cabs2(col[r]);
+            if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((tid & 31) == 0) { s_best[tid >> 5] = best; s_bidx[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            R bb = s_best[0];
+            int bx = s_bidx[0];
+            for (int w = 1; w < kGjThreads / 32; ++w)
+                if (s_best[w] > bb || (s_best[w] == bb && s_bidx[w] < bx)) { bb = s_best[w]; bx = s_bidx[w]; }
+            if (!(bb > (R)0) || !(bb < (R)INFINITY) || bx >= n) {
+                atomicExch(status, 6);   // zero or non-finite pivot: the result is invalid
+                bx = i;
+            }
+            s_p = bx;
+            pivrow[i & 1] = bx;
+        }
+        __syncthreads();
+        const int p = s_p;
+        C* mu = mult + (int64_t)(i & 1) * ldm;
+        for (int r = tid; r < n; r += kGjThreads) mu[r] = col[r == i ? p : (r == p ? i : r)];
+    };
+
+    if (b == 0 && ncol > 0) publish(0);   // column 0 belongs to CTA 0
+    for (int i = 0; i < n; ++i) {
+        if (!grid_barrier(bar, (unsigned)(i + 1) * nb, status)) return;
+        const int p = __ldcg(pivrow + (i & 1));
+        const C* mu = mult + (int64_t)(i & 1) * ldm;
+        const C ip = cinv(ldcg(mu + i));
+        if (b == 0 && tid == 0) perm[i] = p;
+        C m_r[kGjRowsPerThread];
+#pragma unroll
+        for (int u = 0; u < kGjRowsPerThread; ++u) {
+            const int r = tid + u * kGjThreads;
+            m_r[u] = r < n ? ldcg(mu + r) : CT<C>::zero();
+        }
+        for (int lc = tid; lc < ncol; lc += kGjThreads) {
+            const C* col = M + (int64_t)(b + lc * nb) * ldm;
+            s_ai[lc] = col[i];
+            s_ap[lc] = col[p];
+        }
+        __syncthreads();
+        auto update = [&](int lc) {
+            const int c = b + lc * nb;
+            C* col = M + (int64_t)c * ldm;
+            const C t = c == i ? ip : cmul(s_ap[lc], ip);
+            const C ai = s_ai[lc];
+#pragma unroll
+            for (int u = 0; u < kGjRowsPerThread; ++u) {
+                const int r = tid + u * kGjThreads;
+                if (r >= n) continue;
+                const C base = c == i ? CT<C>::zero() : (r == p ? ai : col[r]);
+                col[r] = r == i ? t : csub(base, cmul(m_r[u], t));
+            }
+        };
+        const int cn = i + 1;
+        const int lcn = (cn < n && cn % nb == b) ? cn / nb : -1;
+        if (lcn >= 0) {
+            update(lcn);
+            __syncthreads();
+            publish(cn);
+        }
+        for (int lc = 0; lc < ncol; ++lc)
+            if (lc != lcn) update(lc);
+    }
+    // the exchanges, replayed: s_rows[r] = original row at position r
+    if (b == 0) {
+        __syncthreads();
+        for (int r = tid; r < n; r += kGjThreads) s_rows[r] = r;
+        __syncthreads();
+        if (tid == 0)
+            for (int i = 0; i < n; ++i) {
+                const int p = perm[i], t = s_rows[i];
+                s_rows[i] = s_rows[p];
+                s_rows[p] = t;
+            }
+        __syncthreads();
+        for (int r = tid; r < n; r += kGjThreads) pinv[s_rows[r]] = r;
+    }
+}
+
+// X (row-major sweep layout, ld, columns n..ld-1 zero) = M^{-1} from the
+// Gauss-Jordan result: X(a, c) = Mgj(a, pinv[c]) = M[pinv[c] * ldm + a].
+template <typename C>
+__global__ void __launch_bounds__(256) k_slab_store(const C* __restrict__ M, int n, int ldm,
+                                                    const int* __restrict__ pinv, C* __restrict__ X, int ld) {
+    __shared__ C tile[32][33];
+    const int a0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {   // column c0+i of X: rows a0+tx (contiguous in M)
+        const int c = c0 + i, a = a0 + tx;
+        tile[i][tx] = (c < n && a < n) ? M[(int64_t)pinv[c] * ldm + a] : CT<C>::zero();
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int a = a0 + i, c = c0 + tx;
+        if (a < n && c < ld) X[(int64_t)a * ld + c] = tile[tx][i];
+    }
+}
+
+// ------------------------------------------------------------------ sweeps
+// Right-hand side of a strip solve in the symmetric form (as the 2-D sweep):
+//   r(b,k,e) = s_x s_y s_z ([mlo <= gc <= mhi] src(b,z,k,gc)
+//                           + [gc == t0 or t0+1] tcoef (xp(to1) - xp(to0)))
+// xp: the previous strip solve's solution (strip pst, its transfer columns).
+template <typename C>
+__global__ void k_slab_rhs(Geom g, StripDev st, SweepStep sp, StripDev pst, const C* __restrict__ ct,
+                           int64_t ct_sz, const C* __restrict__ prevY, int pld, C* __restrict__ Rb, int ld, int B) {
+    const int W = st.W, Nz = g.Nz, Ny = g.Ny, n = W * Nz;
+    const int cofs = st.lo - st.lpml;
+    const int64_t tot = (int64_t)B * Ny * ld;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(o % ld);
+        const int k = (int)((o / ld) % Ny);
+        const int b = (int)(o / ((int64_t)ld * Ny));
+        if (e >= n) { Rb[o] = CT<C>::zero(); continue; }
+        const int c = e % W, z = e / W, gc = cofs + c;
+        const C s = cmul(cmul(ct[st.ctab + c], ct[g.ct_sy + k]), ct[ct_sz + z]);
+        double2 f = make_double2(0.0, 0.0);
+        if (gc >= sp.mlo && gc <= sp.mhi) f = sp.src[(((int64_t)b * Nz + z) * Ny + k) * g.Nx + gc];
+        C v = cmul(CT<C>::from(f), s);
+        if (prevY && (gc == sp.t0 || gc == sp.t0 + 1)) {
+            const C* py = prevY + ((int64_t)b * Ny + k) * pld + (int64_t)z * pst.W;
+            const C tv = csub(py[pst.xc[2 * sp.pdir + 1]], py[pst.xc[2 * sp.pdir]]);
+            v = cadd(v, cmul(cscale(tv, (typename CT<C>::R)sp.tcoef), s));
+        }
+        Rb[o] = v;
+    }
+}
+
+// One step of a strip solve: out = base + X (rhs - cy sxz .* prev) for NB right-hand
+// sides (null rhs / prev / base count as zero); one warp per row of X.
+template <typename C>
+struct SlabStepArgs {
+    const C* X;          // block k, row-major, leading dimension xld (a multiple of 4, columns n.. zero)
+    int n, xld, rpc;     // block size, leading dimension, rows per CTA
+    const C* rhs;        // row k of the right-hand sides (b-th at + b * bstride), or null
+    const C* prev;       // neighbouring row of the solution, or null
+    const C* base;       // added to the product, or null
+    C* out;
+    const C* sxz;        // s_x(c) s_z(z) per e
+    C cy;                // -a_y(half point between the two rows) / h^2
+    int64_t bstride;
+    int B;
+};
+
+template <typename C, int NB>
+__global__ void __launch_bounds__(384, 2) k_slab_step(SlabStepArgs<C> A) {
+    using R = typename CT<C>::R;
+    extern __shared__ __align__(16) unsigned char slab_smem[];
+    C* zs = reinterpret_cast<C*>(slab_smem);   // [NB][xld]
+    dep_trigger();
+    const int r0 = blockIdx.x * A.rpc, r1 = imin(r0 + A.rpc, A.n);
+    if (threadIdx.x == 0 && r1 > r0) {   // this CTA's rows of X: independent of the previous step
+        const char* src = reinterpret_cast<const char*>(A.X + (int64_t)r0 * A.xld);
+        const int64_t bytes = (int64_t)(r1 - r0) * A.xld * sizeof(C);
+        for (int64_t o = 0; o < bytes; o += 65536) prefetch_l2(src + o, (uint32_t)(bytes - o < 65536 ? bytes - o : 65536));
+    }
+    dep_wait();
+    const int b0 = blockIdx.y * NB;
+    const int nb = imin(NB, A.B - b0);
+    for (int o = threadIdx.x; o < NB * A.xld; o += blockDim.x) {
+        const int b = o / A.xld, e = o % A.xld;
+        C z = CT<C>::zero();
+        if (b < nb && e < A.n) {
+            const int64_t off = (int64_t)(b0 + b) * A.bstride + e;
+            if (A.rhs) z = ldcg(A.rhs + off);
+            if (A.prev) z = csub(z, cmul(cmul(A.cy, A.sxz[e]), ldcg(A.prev + off)));
+        }
+        zs[o] = z;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = r0 + warp; row < r1; row += nw) {
+        const C* xr = A.X + (int64_t)row * A.xld;
+        C acc[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] = CT<C>::zero();
+        if constexpr (sizeof(C) == 8) {
+            // two complex64 per 16-byte load; ld is a multiple of 4, columns n..ld-1 are zero
+#pragma unroll 4
+            for (int e = 2 * lane; e < A.xld; e += 64) {
+                const float4 q = __ldcg(reinterpret_cast<const float4*>(xr + e));
+                const C x0 = make_float2(q.x, q.y), x1 = make_float2(q.z, q.w);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    acc[b] = cfma(x0, zs[b * A.xld + e], acc[b]);
+                    acc[b] = cfma(x1, zs[b * A.xld + e + 1], acc[b]);
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int e = lane; e < A.xld; e += 32) {
+                const C x = ldcg(xr + e);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc[b] = cfma(x, zs[b * A.xld + e], acc[b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            R re = acc[b].x, im = acc[b].y;
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            acc[b].x = re;
+            acc[b].y = im;
+        }
+        if (lane < nb) {
+            C v = CT<C>::zero();
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (b == lane) v = acc[b];
+            const int64_t off = (int64_t)(b0 + lane) * A.bstride + row;
+            if (A.base) v = cadd(v, A.base[off]);
+            A.out[off] = v;
+        }
+    }
+}
+
+// dst(b,z,k,gc) = [base] + x(b,k,e) on padded columns olo..ohi of the strip
+template <typename C>
+__global__ void k_slab_out(Geom g, StripDev st, int dir, const C* __restrict__ Y, int ld, double2* __restrict__ dst,
+                           const double2* __restrict__ base, int B) {
+    const int olo = st.olo[dir], ohi = st.ohi[dir], nc = ohi - olo + 1;
+    const int cofs = st.lo - st.lpml;
+    const int64_t tot = (int64_t)B * g.Nz * g.Ny * nc;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o % nc);
+        int64_t t = o / nc;
+        const int k = (int)(t % g.Ny);
+        t /= g.Ny;
+        const int z = (int)(t % g.Nz);
+        const int b = (int)(t / g.Nz);
+        const int gc = olo + i, c = gc - cofs;
+        const double2 x = to_d2(Y[((int64_t)b * g.Ny + k) * ld + (int64_t)z * st.W + c]);
+        const int64_t idx = (((int64_t)b * g.Nz + z) * g.Ny + k) * g.Nx + gc;
+        dst[idx] = base ? cadd(base[idx], x) : x;
+    }
+}
+
+int grid_for(int64_t work, int threads) {
+    const int64_t blocks = (work + threads - 1) / threads;
+    return (int)(blocks < 1 ? 1 : (blocks > 152 * 16 ? 152 * 16 : blocks));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+template <typename C>
+cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, const SlabScratch& sc, int* status,
+                               cudaStream_t s, KernelTimer* tm) {
+    const int n = st.W * g.Nz;
+    if (n > kGjThreads * kGjRowsPerThread) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_invert<C>, kGjThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int nb = imin(nsm, n);
+    if ((n + nb - 1) / nb > kGjMaxCols) return cudaErrorInvalidConfiguration;
+    C* X = reinterpret_cast<C*>(pool) + st.fac;
+    C* M = reinterpret_cast<C*>(sc.M);
+    C* mult = reinterpret_cast<C*>(sc.mult);
+    const dim3 tiles((n + 31) / 32, (n + 31) / 32), tiles_st((st.ld + 31) / 32, (n + 31) / 32);
+    for (int k = 0; k < g.Ny; ++k) {
+        {
+            TimedLaunch t(tm, "slab_build", s);
+            k_slab_build<C><<<tiles, 256, 0, s>>>(g, st, k, k > 0 ? X + (int64_t)(k - 1) * st.bs : nullptr, st.ld,
+                                                   M, sc.ldm);
+        }
+        e = cudaMemsetAsync(sc.bar, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        {
+            TimedLaunch t(tm, "slab_gj_invert", s);
+            int nn = n, ldm = sc.ldm;
+            void* args[] = {&M, &nn, &ldm, (void*)&sc.perm, (void*)&sc.pinv, &mult, (void*)&sc.pivrow,
+                            (void*)&sc.bar, &status};
+            e = cudaLaunchCooperativeKernel((const void*)k_gj_invert<C>, dim3(nb), dim3(kGjThreads), args, 0, s);
+            if (e != cudaSuccess) return e;
+        }
+        {
+            TimedLaunch t(tm, "slab_store", s);
+            k_slab_store<C><<<tiles_st, 256, 0, s>>>(M, n, sc.ldm, sc.pinv, X + (int64_t)k * st.bs, st.ld);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename C>
+cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev* pst, const SweepStep& sp,
+                              const SlabWork& wk, const void* pool, cudaStream_t s, KernelTimer* tm) {
+    const int n = st.W * g.Nz, Ny = g.Ny, ld = wk.ld, B = wk.B;
+    const C* ct = reinterpret_cast<const C*>(g.ct);
+    C* Rb = reinterpret_cast<C*>(wk.rbuf);
+    C* Y = reinterpret_cast<C*>(wk.ybuf);
+    const C* X = reinterpret_cast<const C*>(pool) + st.fac;
+    const C* sxz = reinterpret_cast<const C*>(wk.sxz);
+    {
+        TimedLaunch t(tm, "slab_rhs", s);
+        const StripDev pd = pst ? *pst : st;
+        k_slab_rhs<C><<<grid_for((int64_t)B * Ny * ld, 256), 256, 0, s>>>(
+            g, st, sp, pd, ct, wk.ct_sz, pst ? reinterpret_cast<const C*>(wk.pybuf) : nullptr, ld, Rb, ld, B);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int NB = 4;
+    const int rpc = 12;
+    const int nbt = (B + NB - 1) / NB;
+    const bool one = B == 1;
+    const size_t smem = (size_t)(one ? 1 : NB) * st.ld * sizeof(C);
+    static bool attr_set = false;
+    if (!attr_set) {
+        for (auto fn : {k_slab_step<C, 1>, k_slab_step<C, NB>}) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return e;
+        }
+        attr_set = true;
+    }
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((n + rpc - 1) / rpc, one ? 1 : nbt);
+    cfg.blockDim = dim3(32 * rpc);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    void (*fn)(SlabStepArgs<C>) = one ? k_slab_step<C, 1> : k_slab_step<C, NB>;
+    const int64_t bstride = (int64_t)Ny * ld;
+    SlabStepArgs<C> A{};
+    A.n = n;
+    A.xld = st.ld;
+    A.rpc = rpc;
+    A.sxz = sxz;
+    A.bstride = bstride;
+    A.B = B;
+    TimedLaunch t(tm, "slab_step", s);
+    for (int k = 0; k < Ny; ++k) {   // y_k = X_k (r_k - C_k y_{k-1})
+        A.X = X + (int64_t)k * st.bs;
+        A.rhs = Rb + (int64_t)k * ld;
+        A.prev = k > 0 ? Y + (int64_t)(k - 1) * ld : nullptr;
+        A.base = nullptr;
+        A.out = Y + (int64_t)k * ld;
+        A.cy = CT<C>::from(wk.cy_host[k]);
+        e = cudaLaunchKernelEx(&cfg, fn, A);
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = Ny - 2; k >= 0; --k) {   // x_k = y_k - X_k C_{k+1} x_{k+1}
+        A.X = X + (int64_t)k * st.bs;
+        A.rhs = nullptr;
+        A.prev = Y + (int64_t)(k + 1) * ld;
+        A.base = Y + (int64_t)k * ld;
+        A.out = Y + (int64_t)k * ld;
+        A.cy = CT<C>::from(wk.cy_host[k + 1]);
+        e = cudaLaunchKernelEx(&cfg, fn, A);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t launch_slab_out(const Geom& g, const StripDev& st, int dir, const void* ybuf, int ld, double2* dst,
+                            const double2* base, int B, cudaStream_t s, KernelTimer* tm) {
+    TimedLaunch t(tm, "slab_out", s);
+    const int64_t work = (int64_t)B * g.Nz * g.Ny * (st.ohi[dir] - st.olo[dir] + 1);
+    k_slab_out<C><<<grid_for(work, 256), 256, 0, s>>>(g, st, dir, reinterpret_cast<const C*>(ybuf), ld, dst, base,
+                                                     B);
+    return cudaGetLastError();
+}
+
+#define HELM_SLAB_INST(C)                                                                                       \
+    template cudaError_t launch_slab_factor<C>(const Geom&, const StripDev&, void*, const SlabScratch&, int*,   \
+                                               cudaStream_t, KernelTimer*);                                    \
+    template cudaError_t launch_slab_solve<C>(const Geom&, const StripDev&, const StripDev*, const SweepStep&, \
+                                              const SlabWork&, const void*, cudaStream_t, KernelTimer*);       \
+    template cudaError_t launch_slab_out<C>(const Geom&, const StripDev&, int, const void*, int, double2*,     \
+                                            const double2*, int, cudaStream_t, KernelTimer*);
+HELM_SLAB_INST(float2)
+HELM_SLAB_INST(double2)
+#undef HELM_SLAB_INST
+
+}  // namespace helm
