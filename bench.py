@@ -8,7 +8,9 @@ device.  Metric: Mdof*RHS/s = padded unknowns x right-hand sides / solve time.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
 
 With the mixed-precision sweep (default) the line also carries "fp64_sweep": the same
-solve with complex128 factors and sweep (FP64 GMRES), and the mixed / FP64 ratio.
+solve with complex128 factors and sweep (FP64 GMRES), and the mixed / FP64 ratio; and, on
+one GPU, "slab3d": the 3-D workload (63^3 smooth random medium, padded 79^3, J = 8 slabs
+of dense W N_z blocks) with its own roofline for the slab strip-solve kernel.
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 
 Multi-GPU (torchrun, one process per GPU): every rank solves its own source
@@ -190,6 +192,57 @@ def run_reference(args):
     return 0
 
 
+def run_slab3d(helm, media, torch, stream, steps):
+    """The 3-D smooth random medium (63^3, padded 79^3, J = 8, 6-point added layers), mixed
+    precision, one point source; solve time with inputs resident, and the slab strip-solve
+    kernel's roofline (one launch = one strip solve: 2 N_y - 1 dense blocks of (W N_z)^2)."""
+    wl = media.WORKLOADS["smooth63_3d"]
+    c = media.medium("smooth63_3d")
+    omega = media.omega_for(c, wl.h, wl.ppw)
+    s3 = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed")
+    s3.set_stream(stream.cuda_stream)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    s3.factor()
+    e[1].record()
+    f = torch.as_tensor(media.point_sources(wl.n, wl.w_outer, wl.h, media.source_positions("smooth63_3d")[:1]),
+                        device="cuda")
+    s3.solve(f, tol=1e-6, restart=20, maxit=200)
+    k3 = max(3, steps // 2)
+    e[2].record()
+    for _ in range(k3):
+        _, info = s3.solve(f, tol=1e-6, restart=20, maxit=200)
+    e[3].record()
+    torch.cuda.synchronize()
+    t_ms = e[2].elapsed_time(e[3]) / k3
+    s3.set_timing(True)
+    for _ in range(k3):
+        s3.solve(f, tol=1e-6, restart=20, maxit=200)
+    stats = s3.kernel_stats()
+    s3.set_timing(False)
+    Ny, Nz = s3.N[1], s3.N[2]
+    ns = [w * Nz for w in s3.strip_widths()]
+    per = [(2 * Ny - 1) * n * n * 8 for n in ns] + [(2 * Ny - 1) * n * n * 8 for n in ns[:-1]]
+    alg = sum(per) / len(per)
+    sw = stats.get("slab_sweep", (0, 0.0))
+    achieved = alg / (sw[1] / sw[0] * 1e-3) / 1e9 if sw[0] else 0.0
+    peaks = load_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    out = {"workload": "smooth63_3d", "grid": "63^3 interior, 79^3 padded", "J": wl.J, "w_sub": wl.w_sub,
+           "w_outer": wl.w_outer, "precision": "mixed", "nrhs": 1,
+           "value": s3.ndof / (t_ms * 1e-3) / 1e6, "unit": "Mdof*RHS/s", "ms_per_solve": t_ms, "steps": k3,
+           "iters": [i["iters"] for i in info], "rel_res": max(i["rel_res"] for i in info),
+           "factor_ms": e[0].elapsed_time(e[1]),
+           "roofline": {"bound": "hbm", "kernel": "slab_sweep", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm,
+                        "traffic": captured_traffic("paper_1208_3956_gb300/csrc/slab3d.cu",
+                                                    "profiles/slab_sweep_smooth63_3d.md"),
+                        "alg_bytes_per_launch": alg},
+           "kernel_ms_per_step": {k: v[1] / k3 for k, v in stats.items()}}
+    s3.close()
+    return out
+
+
 def run_ours(args):
     rank, world, local = rank_env()
     if world > 1:
@@ -275,6 +328,11 @@ def run_ours(args):
                 "mixed_over_fp64": value / v64}
         s64.close()
 
+    slab3d = None
+    if world == 1 and not args.no_3d:
+        from paper_1208_3956_gb300 import media
+        slab3d = run_slab3d(helm, media, torch, stream, args.steps)
+
     line = None
     if rank == 0:
         peaks = load_peaks()
@@ -319,6 +377,8 @@ def run_ours(args):
         }
         if fp64:
             line["fp64_sweep"] = fp64
+        if slab3d:
+            line["slab3d"] = slab3d
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_oracle_solve_time(max_seconds=40.0, steps=1)
         line["cpu_baseline"] = {"value": r["ndof"] / r["t_solve"] / 1e6, "unit": "Mdof*RHS/s", "cores": 1,
@@ -345,9 +405,20 @@ def main():
     ap.add_argument("--chunks", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the complex128-sweep comparison")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D workload")
+    ap.add_argument("--only-3d", action="store_true",
+                    help="run only the 3-D workload and print its object (a profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_3d:
+        import torch
+        from paper_1208_3956_gb300 import helm, media
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps(run_slab3d(helm, media, torch, stream, args.steps)), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -845,7 +845,7 @@ helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B
     auto solve = [&](int j, const SweepStep& sp, int slot) -> cudaError_t {
         SlabWork wk{rbuf, ybuf[slot], sp.prev >= 0 ? ybuf[slot ^ 1] : nullptr,
                     (const char*)h->d_slab_sxz + h->slab_sxz_off[j] * (int64_t)h->esize, h->ct_sz,
-                    h->slab_cy.data(), ld, B};
+                    h->slab_cy.data(), ld, B, (unsigned*)h->d_counters, h->d_status};
         const StripDev* pst = sp.prev >= 0 ? &h->strips[sp.prev] : nullptr;
         if (mixed) return launch_slab_solve<float2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);
         return launch_slab_solve<double2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);

@@ -159,6 +159,8 @@ struct SlabWork {
     const double2* cy_host;   // host: -alpha_y(y_{k-1/2}) / h^2, k = 0 .. Ny
     int ld;                   // row stride of rbuf / ybuf / pybuf (>= every strip's n)
     int B;
+    unsigned* bar;            // grid-barrier counter of the strip-solve kernel
+    int* status;              // error word (7 = a bounded wait gave up)
 };
 // Factor blocks X_k = S_k^{-1} of strip st into pool + st.fac (row-major, leading
 // dimension st.ld, st.bs elements per block), k = 0 .. Ny-1.

@@ -18,10 +18,10 @@
 // (block forward and back substitution):
 //   y_k = X_k (r_k - C_k y_{k-1}),   k = 0 .. N_y-1
 //   x_k = y_k - X_k C_{k+1} x_{k+1}, k = N_y-2 .. 0
-// one launch per block row, each a matrix-vector product that streams X_k from
-// HBM: the X_k rows of a CTA are prefetched into L2 before the launch waits for
-// its predecessor (programmatic dependent launch), so the stream of factor bytes
-// runs on while the previous step finishes.
+// all 2 N_y - 1 steps in one cooperative launch (k_slab_sweep), each a
+// matrix-vector product that streams X_k from HBM through shared memory.
+#include <algorithm>
+
 #include "common.cuh"
 #include "strip_ops.cuh"
 #include "internal.h"
@@ -39,11 +39,6 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename C> __device__ __forceinline__ C ldcg(const C* p);
 template <> __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
@@ -149,12 +144,14 @@ __global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, 
 // column i+1 first, so the next pivot search starts as soon as possible.  The
 // result is (P M)^{-1} for the product P of the exchanges; pinv[c] = the
 // position of original row c after all exchanges, so M^{-1}(:, c) = result(:, pinv[c]).
+// cached != 0: a CTA keeps its columns in shared memory for the whole elimination.
 template <typename C>
 __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int n, int ldm, int* __restrict__ perm,
                                                          int* __restrict__ pinv, C* __restrict__ mult,
                                                          int* __restrict__ pivrow, unsigned* __restrict__ bar,
-                                                         int* __restrict__ status) {
+                                                         int* __restrict__ status, int cached) {
     using R = typename CT<C>::R;
+    extern __shared__ __align__(16) unsigned char gj_smem[];
     __shared__ C s_ai[kGjMaxCols], s_ap[kGjMaxCols];
     __shared__ R s_best[kGjThreads / 32];
     __shared__ int s_bidx[kGjThreads / 32];
@@ -162,10 +159,19 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
     __shared__ int s_rows[kGjThreads * kGjRowsPerThread];
     const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
     const int ncol = b < n ? (n - 1 - b) / nb + 1 : 0;   // owned columns b, b+nb, ...
+    C* cache = reinterpret_cast<C*>(gj_smem);            // [ncol][n] when cached
+    auto colp = [&](int lc) -> C* {
+        return cached ? cache + (int64_t)lc * n : M + (int64_t)(b + lc * nb) * ldm;
+    };
+    if (cached) {
+        for (int lc = 0; lc < ncol; ++lc)
+            for (int r = tid; r < n; r += kGjThreads) cache[(int64_t)lc * n + r] = M[(int64_t)(b + lc * nb) * ldm + r];
+        __syncthreads();
+    }
 
     // pivot search and publication for column i (owned by this CTA, up to date)
     auto publish = [&](int i) {
-        const C* col = M + (int64_t)i * ldm;
+        const C* col = colp(i / nb);   // i = b + (i / nb) nb
         R best = (R)-1;
         int bi = n;
         for (int r = i + tid; r < n; r += kGjThreads) {
@@ -211,14 +217,14 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
             m_r[u] = r < n ? ldcg(mu + r) : CT<C>::zero();
         }
         for (int lc = tid; lc < ncol; lc += kGjThreads) {
-            const C* col = M + (int64_t)(b + lc * nb) * ldm;
+            const C* col = colp(lc);
             s_ai[lc] = col[i];
             s_ap[lc] = col[p];
         }
         __syncthreads();
         auto update = [&](int lc) {
             const int c = b + lc * nb;
-            C* col = M + (int64_t)c * ldm;
+            C* col = colp(lc);
             const C t = c == i ? ip : cmul(s_ap[lc], ip);
             const C ai = s_ai[lc];
 #pragma unroll
@@ -238,6 +244,11 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
         }
         for (int lc = 0; lc < ncol; ++lc)
             if (lc != lcn) update(lc);
+    }
+    if (cached) {
+        __syncthreads();
+        for (int lc = 0; lc < ncol; ++lc)
+            for (int r = tid; r < n; r += kGjThreads) M[(int64_t)(b + lc * nb) * ldm + r] = cache[(int64_t)lc * n + r];
     }
     // the exchanges, replayed: s_rows[r] = original row at position r
     if (b == 0) {
@@ -304,92 +315,249 @@ __global__ void k_slab_rhs(Geom g, StripDev st, SweepStep sp, StripDev pst, cons
     }
 }
 
-// One step of a strip solve: out = base + X (rhs - cy sxz .* prev) for NB right-hand
-// sides (null rhs / prev / base count as zero); one warp per row of X.
+// A whole strip solve (2 N_y - 1 block steps) in one cooperative launch of at most
+// one CTA per SM.  CTA b owns rows [b rpc, (b+1) rpc) of every block; step s is
+//   forward  (s < N_y):      y_k = X_k (r_k - C_k y_{k-1}),       k = s
+//   backward (s >= N_y):     x_k = y_k - X_k (C_{k+1} x_{k+1}),    k = 2 N_y - 2 - s
+// in place in Y.  A producer warp streams the CTA's rows of X_k, step after step,
+// into a ring of row slots in shared memory (cp.async.bulk + mbarriers), with the
+// next step's rows prefetched into L2; it never waits for the vector, so the factor
+// stream runs ahead across the steps while the compute warps wait at the grid barrier
+// for the previous step's rows.  Compute warp w owns the column segment
+// [w seg, (w+1) seg) of every row: it loads its part of the step's input vector
+// z = r_k - C y_kp straight into registers, forms its partial products for all rows
+// of the step (four rows at a time), and the eight partials of a row are summed in
+// shared memory.  Every wait is bounded: on time-out the kernel records 7 in the
+// status word, waits (bounded) for its copies in flight and returns.
 template <typename C>
-struct SlabStepArgs {
-    const C* X;          // block k, row-major, leading dimension xld (a multiple of 4, columns n.. zero)
-    int n, xld, rpc;     // block size, leading dimension, rows per CTA
-    const C* rhs;        // row k of the right-hand sides (b-th at + b * bstride), or null
-    const C* prev;       // neighbouring row of the solution, or null
-    const C* base;       // added to the product, or null
-    C* out;
-    const C* sxz;        // s_x(c) s_z(z) per e
-    C cy;                // -a_y(half point between the two rows) / h^2
-    int64_t bstride;
-    int B;
+struct SlabSweepArgs {
+    const C* X;          // block 0 of the strip; block k at X + k * bs, row-major, leading dimension xld
+    int64_t bs;
+    int n, xld, Ny, rpc, ring;
+    const C* rhs;        // [B][Ny][ld] right-hand sides
+    C* Y;                // [B][Ny][ld] solution
+    int ld, B;           // row stride of rhs / Y; right-hand sides of this launch (<= NB)
+    const C* sxz;        // s_x(c) s_z(z) per block entry
+    const C* cyt;        // -alpha_y(y_{k-1/2}) / h^2, k = 0 .. Ny
+    unsigned* bar;       // step counter, zero at launch
+    int* status;
 };
 
-template <typename C, int NB>
-__global__ void __launch_bounds__(384, 2) k_slab_step(SlabStepArgs<C> A) {
-    using R = typename CT<C>::R;
-    extern __shared__ __align__(16) unsigned char slab_smem[];
-    C* zs = reinterpret_cast<C*>(slab_smem);   // [NB][xld]
-    dep_trigger();
-    const int r0 = blockIdx.x * A.rpc, r1 = imin(r0 + A.rpc, A.n);
-    if (threadIdx.x == 0 && r1 > r0) {   // this CTA's rows of X: independent of the previous step
-        const char* src = reinterpret_cast<const char*>(A.X + (int64_t)r0 * A.xld);
-        const int64_t bytes = (int64_t)(r1 - r0) * A.xld * sizeof(C);
-        for (int64_t o = 0; o < bytes; o += 65536) prefetch_l2(src + o, (uint32_t)(bytes - o < 65536 ? bytes - o : 65536));
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(uint64_t* m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ bool mb_wait(uint64_t* m, uint32_t parity) {
+    for (uint32_t it = 0; it < kBarPolls; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(m)), "r"(parity)
+            : "memory");
+        if (ok) return true;
     }
-    dep_wait();
-    const int b0 = blockIdx.y * NB;
-    const int nb = imin(NB, A.B - b0);
-    for (int o = threadIdx.x; o < NB * A.xld; o += blockDim.x) {
-        const int b = o / A.xld, e = o % A.xld;
-        C z = CT<C>::zero();
-        if (b < nb && e < A.n) {
-            const int64_t off = (int64_t)(b0 + b) * A.bstride + e;
-            if (A.rhs) z = ldcg(A.rhs + off);
-            if (A.prev) z = csub(z, cmul(cmul(A.cy, A.sxz[e]), ldcg(A.prev + off)));
-        }
-        zs[o] = z;
+    return false;
+}
+__device__ __forceinline__ void bulk_row(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(m))
+        : "memory");
+}
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+constexpr int kSweepThreads = 288;   // 8 compute warps + 1 producer warp
+constexpr int kSegU = 8;             // columns per lane: 8 warps x 32 lanes x 8 >= xld (n <= 2048)
+constexpr int kMaxRpc = 32;          // rows per CTA and step
+
+template <typename C, int NB>
+__global__ void __launch_bounds__(kSweepThreads, 1) k_slab_sweep(SlabSweepArgs<C> A) {
+    using R = typename CT<C>::R;
+    extern __shared__ __align__(128) unsigned char sweep_smem[];
+    const int R_ = A.ring, xld = A.xld;
+    C* ring = reinterpret_cast<C*>(sweep_smem);                       // [ring][xld]
+    C* part = ring + (int64_t)R_ * xld;                               // [8][kMaxRpc][NB] partial products
+    uint64_t* full = reinterpret_cast<uint64_t*>(part + 8 * kMaxRpc * NB);   // [ring]
+    uint64_t* empty = full + R_;                                      // [ring]
+    int* abort_flag = reinterpret_cast<int*>(empty + R_);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * A.rpc, nrow = imin(A.rpc, A.n - r0);
+    const int nsteps = 2 * A.Ny - 1;
+    const uint32_t rowbytes = (uint32_t)(xld * sizeof(C));
+    // ring slots go back to the producer at the end of a step (after the grid arrival) when
+    // the ring holds a whole step; otherwise each warp frees a group's slots as soon as it
+    // has used them
+    constexpr int RG = NB == 1 ? 4 : 2;
+    const bool defer = R_ >= A.rpc;
+    if (tid == 0) {
+        for (int i = 0; i < R_; ++i) { mb_init(&full[i], 1); mb_init(&empty[i], defer ? 1 : 8); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int row = r0 + warp; row < r1; row += nw) {
-        const C* xr = A.X + (int64_t)row * A.xld;
-        C acc[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) acc[b] = CT<C>::zero();
-        if constexpr (sizeof(C) == 8) {
-            // two complex64 per 16-byte load; ld is a multiple of 4, columns n..ld-1 are zero
-#pragma unroll 4
-            for (int e = 2 * lane; e < A.xld; e += 64) {
-                const float4 q = __ldcg(reinterpret_cast<const float4*>(xr + e));
-                const C x0 = make_float2(q.x, q.y), x1 = make_float2(q.z, q.w);
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    acc[b] = cfma(x0, zs[b * A.xld + e], acc[b]);
-                    acc[b] = cfma(x1, zs[b * A.xld + e + 1], acc[b]);
+
+    if (warp == 8) {   // producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            // the CTA's rows of block k(s) into L2, one step ahead of the ring copies: the
+            // ring holds about one step, the HBM stream then runs on across the barrier
+            auto prefetch = [&](int s) {
+                if (s >= nsteps) return;
+                const int k = s < A.Ny ? s : 2 * A.Ny - 2 - s;
+                const char* src = reinterpret_cast<const char*>(A.X + (int64_t)k * A.bs + (int64_t)r0 * xld);
+                const uint32_t bytes = (uint32_t)nrow * rowbytes;
+                for (uint32_t o = 0; o < bytes; o += 65536)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + o),
+                                 "r"(bytes - o < 65536 ? bytes - o : 65536)
+                                 : "memory");
+            };
+            prefetch(0);
+            for (int s = 0; s < nsteps && ok; ++s) {
+                prefetch(s + 1);
+                const int k = s < A.Ny ? s : 2 * A.Ny - 2 - s;
+                const C* src = A.X + (int64_t)k * A.bs + (int64_t)r0 * xld;
+                for (int i = 0; i < nrow; ++i, ++g) {
+                    const int slot = (int)(g % (uint32_t)R_);
+                    const uint32_t use = g / (uint32_t)R_;
+                    if (use > 0 && !mb_wait(&empty[slot], (use - 1) & 1)) { ok = false; break; }
+                    if (*(volatile int*)abort_flag) { ok = false; break; }
+                    mb_expect_tx(&full[slot], rowbytes);
+                    bulk_row(ring + (int64_t)slot * xld, src + (int64_t)i * xld, rowbytes, &full[slot]);
                 }
             }
-        } else {
-#pragma unroll 4
-            for (int e = lane; e < A.xld; e += 32) {
-                const C x = ldcg(xr + e);
+            if (!ok) atomicExch(A.status, 7);
+            // copies still in flight land before the CTA exits
+            const uint32_t lo = g > (uint32_t)R_ ? g - (uint32_t)R_ : 0;
+            for (uint32_t q = lo; q < g; ++q) mb_wait(&full[q % (uint32_t)R_], (q / (uint32_t)R_) & 1);
+        }
+        return;
+    }
+
+    // compute warps
+    const int e0 = warp * 32 * kSegU + lane;   // this lane's columns: e0 + 32 u, u < kSegU
+    uint32_t g0 = 0;   // issue index of this step's first row
+    for (int s = 0; s < nsteps; ++s, g0 += (uint32_t)nrow) {
+        const bool fwd = s < A.Ny;
+        const int k = fwd ? s : 2 * A.Ny - 2 - s;
+        const int kp = fwd ? k - 1 : k + 1;   // neighbouring row whose solution enters
+        if (s > 0) {   // every CTA's rows of the previous step are written
+            if (tid == 0) {
+                const unsigned target = (unsigned)s * gridDim.x;
+                unsigned v = ld_acquire_gpu(A.bar);
+                for (uint32_t it = 0; v < target && it < kBarPolls; ++it) {
+                    __nanosleep(20);
+                    v = ld_acquire_gpu(A.bar);
+                }
+                if (v < target) { atomicExch(A.status, 7); *(volatile int*)abort_flag = 1; }
+            }
+            compute_sync();
+            if (*(volatile int*)abort_flag) return;
+        }
+        // backward: y_k of the rows this CTA outputs (thread t < nrow B: row t / B, rhs t % B)
+        const int ob = tid % NB, oi = tid / NB;
+        const bool outs = tid < nrow * NB && ob < A.B;
+        C* yo = A.Y + ((int64_t)imin(ob, A.B - 1) * A.Ny + k) * A.ld + r0 + imin(oi, nrow - 1);
+        const C ybase = (outs && !fwd) ? *yo : CT<C>::zero();
+        // z = r_k - cy sxz .* y_kp on this lane's columns, in registers
+        const C cy = A.cyt[fwd ? k : k + 1];
+        C z[kSegU][NB];
 #pragma unroll
-                for (int b = 0; b < NB; ++b) acc[b] = cfma(x, zs[b * A.xld + e], acc[b]);
+        for (int u = 0; u < kSegU; ++u) {
+            const int e = e0 + 32 * u;
+            const bool ok = e < A.n;
+            const int ec = imin(e, A.n - 1);
+            const C sc = cmul(cy, ok ? A.sxz[ec] : CT<C>::zero());
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const bool okb = ok && b < A.B;
+                const int64_t rb = (int64_t)imin(b, A.B - 1) * A.Ny;
+                const C r = (okb && fwd) ? ldcg(A.rhs + (rb + k) * A.ld + ec) : CT<C>::zero();
+                const C y = (okb && kp >= 0) ? ldcg(A.Y + (rb + kp) * A.ld + ec) : CT<C>::zero();
+                z[u][b] = csub(r, cmul(sc, y));
             }
         }
+        // partial products of this warp's segment, RG rows at a time: the group's rows
+        // are awaited first, then their products interleaved (independent chains)
+        bool ok = true;
+        for (int i0 = 0; i0 < nrow && ok; i0 += RG) {
+            bool landed = true;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            R re = acc[b].x, im = acc[b].y;
-            for (int o = 16; o > 0; o >>= 1) {
-                re += __shfl_xor_sync(0xffffffffu, re, o);
-                im += __shfl_xor_sync(0xffffffffu, im, o);
+            for (int r = 0; r < RG; ++r) {
+                const uint32_t g = g0 + (uint32_t)(i0 + r);
+                if (i0 + r < nrow) landed &= mb_wait(&full[g % (uint32_t)R_], (g / (uint32_t)R_) & 1);
             }
-            acc[b].x = re;
-            acc[b].y = im;
-        }
-        if (lane < nb) {
-            C v = CT<C>::zero();
+            if (!__all_sync(0xffffffffu, landed)) { ok = false; break; }
+            const C* xr[RG];
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
-                if (b == lane) v = acc[b];
-            const int64_t off = (int64_t)(b0 + lane) * A.bstride + row;
-            if (A.base) v = cadd(v, A.base[off]);
-            A.out[off] = v;
+            for (int r = 0; r < RG; ++r)
+                xr[r] = ring + (int64_t)((g0 + (uint32_t)imin(i0 + r, nrow - 1)) % (uint32_t)R_) * xld;
+            C acc[RG][NB];
+#pragma unroll
+            for (int r = 0; r < RG; ++r)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc[r][b] = CT<C>::zero();
+#pragma unroll
+            for (int u = 0; u < kSegU; ++u) {
+                const int e = e0 + 32 * u;
+                C x[RG];
+#pragma unroll
+                for (int r = 0; r < RG; ++r) x[r] = e < xld ? xr[r][e] : CT<C>::zero();
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) acc[r][b] = cfma(x[r], z[u][b], acc[r][b]);
+            }
+            if (!defer) {
+                __syncwarp();
+                if (lane == 0)
+                    for (int r = 0; r < RG && i0 + r < nrow; ++r)
+                        mb_arrive(&empty[(g0 + (uint32_t)(i0 + r)) % (uint32_t)R_]);
+            }
+#pragma unroll
+            for (int r = 0; r < RG; ++r)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    R re = acc[r][b].x, im = acc[r][b].y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        re += __shfl_xor_sync(0xffffffffu, re, o);
+                        im += __shfl_xor_sync(0xffffffffu, im, o);
+                    }
+                    acc[r][b].x = re;
+                    acc[r][b].y = im;
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int r = 0; r < RG; ++r)
+                    if (i0 + r < nrow)
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) part[(warp * kMaxRpc + i0 + r) * NB + b] = acc[r][b];
+        }
+        if (!ok && lane == 0) { atomicExch(A.status, 7); *(volatile int*)abort_flag = 1; }
+        compute_sync();
+        if (*(volatile int*)abort_flag) return;
+        if (outs) {   // the eight partials of row oi, rhs ob
+            C v = ybase;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) v = cadd(v, part[(w * kMaxRpc + oi) * NB + ob]);
+            *yo = v;
+        }
+        compute_sync();
+        if (tid == 0) {
+            // this CTA's rows of step s are written (release: ordered after the barrier above);
+            // only then are the step's ring slots handed back, so that the refill traffic does
+            // not queue in front of the release
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(A.bar) : "memory");
+            if (defer)
+                for (int i = 0; i < nrow; ++i) mb_arrive(&empty[(g0 + (uint32_t)i) % (uint32_t)R_]);
         }
     }
 }
@@ -431,11 +599,23 @@ cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, co
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_invert<C>, kGjThreads, 0);
     if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
     const int nb = imin(nsm, n);
     if ((n + nb - 1) / nb > kGjMaxCols) return cudaErrorInvalidConfiguration;
+    // the owned columns stay in shared memory when they fit
+    const size_t kCacheMax = 200 * 1024;
+    const size_t cache = (size_t)((n + nb - 1) / nb) * n * sizeof(C);
+    int cached = cache <= kCacheMax ? 1 : 0;
+    size_t dsmem = cached ? cache : 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_gj_invert<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheMax);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_invert<C>, kGjThreads, dsmem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     C* X = reinterpret_cast<C*>(pool) + st.fac;
     C* M = reinterpret_cast<C*>(sc.M);
     C* mult = reinterpret_cast<C*>(sc.mult);
@@ -452,8 +632,8 @@ cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, co
             TimedLaunch t(tm, "slab_gj_invert", s);
             int nn = n, ldm = sc.ldm;
             void* args[] = {&M, &nn, &ldm, (void*)&sc.perm, (void*)&sc.pinv, &mult, (void*)&sc.pivrow,
-                            (void*)&sc.bar, &status};
-            e = cudaLaunchCooperativeKernel((const void*)k_gj_invert<C>, dim3(nb), dim3(kGjThreads), args, 0, s);
+                            (void*)&sc.bar, &status, &cached};
+            e = cudaLaunchCooperativeKernel((const void*)k_gj_invert<C>, dim3(nb), dim3(kGjThreads), args, dsmem, s);
             if (e != cudaSuccess) return e;
         }
         {
@@ -484,57 +664,51 @@ cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev*
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     constexpr int NB = 4;
-    const int rpc = 12;
-    const int nbt = (B + NB - 1) / NB;
-    const bool one = B == 1;
-    const size_t smem = (size_t)(one ? 1 : NB) * st.ld * sizeof(C);
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int rpc = (n + nsm - 1) / nsm, ncta = (n + rpc - 1) / rpc;
+    if (rpc > kMaxRpc || st.ld > 8 * 32 * kSegU) return cudaErrorInvalidValue;
+    const size_t row = (size_t)st.ld * sizeof(C);
+    const size_t kSmemMax = 227 * 1024;
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto fn : {k_slab_step<C, 1>, k_slab_step<C, NB>}) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        for (auto fn : {k_slab_sweep<C, 1>, k_slab_sweep<C, NB>}) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
             if (e != cudaSuccess) return e;
         }
         attr_set = true;
     }
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaLaunchAttribute pdl[1];
-    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    pdl[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((n + rpc - 1) / rpc, one ? 1 : nbt);
-    cfg.blockDim = dim3(32 * rpc);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = pdl;
-    cfg.numAttrs = 1;
-    void (*fn)(SlabStepArgs<C>) = one ? k_slab_step<C, 1> : k_slab_step<C, NB>;
-    const int64_t bstride = (int64_t)Ny * ld;
-    SlabStepArgs<C> A{};
-    A.n = n;
-    A.xld = st.ld;
-    A.rpc = rpc;
-    A.sxz = sxz;
-    A.bstride = bstride;
-    A.B = B;
-    TimedLaunch t(tm, "slab_step", s);
-    for (int k = 0; k < Ny; ++k) {   // y_k = X_k (r_k - C_k y_{k-1})
-        A.X = X + (int64_t)k * st.bs;
-        A.rhs = Rb + (int64_t)k * ld;
-        A.prev = k > 0 ? Y + (int64_t)(k - 1) * ld : nullptr;
-        A.base = nullptr;
-        A.out = Y + (int64_t)k * ld;
-        A.cy = CT<C>::from(wk.cy_host[k]);
-        e = cudaLaunchKernelEx(&cfg, fn, A);
+    for (int b0 = 0; b0 < B; b0 += NB) {
+        const int nb = imin(NB, B - b0);
+        const int nbk = nb == 1 ? 1 : NB;
+        const size_t fixed = (size_t)8 * kMaxRpc * nbk * sizeof(C) + 128;
+        const int ring = (int)std::min<size_t>(64, (kSmemMax - fixed) / (row + 16));
+        if (ring < 4) return cudaErrorInvalidValue;   // a row group of the compute warps fits
+        const size_t smem = (size_t)ring * row + (size_t)8 * kMaxRpc * nbk * sizeof(C) + (size_t)ring * 16 + 16;
+        SlabSweepArgs<C> A{};
+        A.X = X;
+        A.bs = st.bs;
+        A.n = n;
+        A.xld = st.ld;
+        A.Ny = Ny;
+        A.rpc = rpc;
+        A.ring = ring;
+        A.rhs = Rb + (int64_t)b0 * Ny * ld;
+        A.Y = Y + (int64_t)b0 * Ny * ld;
+        A.ld = ld;
+        A.B = nb;
+        A.sxz = sxz;
+        A.cyt = ct + g.ct_cy;
+        A.bar = wk.bar;
+        A.status = wk.status;
+        e = cudaMemsetAsync(wk.bar, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
-    }
-    for (int k = Ny - 2; k >= 0; --k) {   // x_k = y_k - X_k C_{k+1} x_{k+1}
-        A.X = X + (int64_t)k * st.bs;
-        A.rhs = nullptr;
-        A.prev = Y + (int64_t)(k + 1) * ld;
-        A.base = Y + (int64_t)k * ld;
-        A.out = Y + (int64_t)k * ld;
-        A.cy = CT<C>::from(wk.cy_host[k + 1]);
-        e = cudaLaunchKernelEx(&cfg, fn, A);
+        TimedLaunch t(tm, "slab_sweep", s);
+        void* args[] = {&A};
+        e = cudaLaunchCooperativeKernel(nbk == 1 ? (const void*)k_slab_sweep<C, 1> : (const void*)k_slab_sweep<C, NB>,
+                                        dim3(ncta), dim3(kSweepThreads), args, smem, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
