@@ -115,7 +115,15 @@ int helm_dd_sep_groups(const helm_dd* h);
  * columns on internal sides, k held constant in x across an added layer) in its
  * complex-symmetric form S^(j) A^(j), and factor it as a block-tridiagonal
  * matrix along y.  Factors stay on the device.  Returns HELM_ENUMERIC on a
- * numerically singular block. */
+ * numerically singular block.
+ * 2-D grids: W x W blocks, partitioned along y (nested dissection) for the
+ * parallel sweep.  3-D grids: one dense block of n = W N_z unknowns (a slab of
+ * W x-columns by all z-planes) per grid row y, factored top down with every
+ * block inverted by Gauss-Jordan elimination with partial pivoting; its
+ * inversions and the strip solves of the sweep run as cooperative launches
+ * (all CTAs co-resident), and a bounded wait inside them that gives up returns
+ * HELM_ETIMEOUT.  HELM_EINVAL when a 3-D block exceeds 2048 unknowns (use more
+ * strips).  Factor memory: N_y n^2 complex entries per strip (8 or 16 bytes). */
 helm_status helm_dd_factor(helm_dd* h);
 
 /* out = P in for nrhs right-hand sides (Section 2.1, Eqs. solve_upward and

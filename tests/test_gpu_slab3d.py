@@ -121,3 +121,14 @@ def test_slab_full_size_smooth63_3d_mixed_solve_properties():
     assert 1 <= info[0]["iters"] <= 30
     assert rel(g.matvec(u), f) <= 1e-6 * 1.01
     g.close()
+
+
+def test_slab_block_size_limit_is_an_argument_error():
+    # one strip of 46 x-columns by 106 z-planes: 4876 unknowns per block > 2048
+    c = np.full((100, 8, 40), 1.0)
+    g = helm.HelmDD(c, 1.0 / 32, 20.0, 3, 2, 1, "mixed")
+    with pytest.raises(helm.HelmError) as e:
+        g.factor()
+    assert e.value.status == -1   # HELM_EINVAL
+    assert "2048" in str(e.value)
+    g.close()
