@@ -21,6 +21,8 @@
  * Pointers.  Every array argument may be a host pointer or a CUDA device pointer
  *            (detected per call).  Host arrays are copied in and out inside the
  *            call.  Buffers are borrowed for the duration of the call only.
+ *            Device complex128 fields must be 16-byte aligned (HELM_EINVAL
+ *            otherwise: the kernels read them with 16-byte accesses).
  * Sync.      Calls are synchronous on return.  A handle is not thread-safe;
  *            separate handles are independent.
  * Errors.    Every call returns a helm_status and never aborts or throws across

@@ -140,6 +140,9 @@ void ws_free(helm_dd::Ws& w) {
     w.bytes = 0;
 }
 
+// complex128 device fields are read with 16-byte accesses
+bool misaligned16(const void* p) { return ((uintptr_t)p & 15) != 0; }
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -900,6 +903,8 @@ helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int
     if (!h->factored) return fail(h, HELM_ESTATE, "apply_precond before factor");
     const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
     const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    if ((din && misaligned16(in)) || (dout && misaligned16(out)))
+        return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
     helm_status s;
     const double2* dinp = (const double2*)in;
     double2* doutp = (double2*)out;
@@ -929,6 +934,8 @@ helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs) 
     }
     const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
     const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    if ((din && misaligned16(in)) || (dout && misaligned16(out)))
+        return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
     helm_status s;
     const double2* dinp = (const double2*)in;
     double2* doutp = (double2*)out;
@@ -1131,6 +1138,8 @@ helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs, do
     const auto t0 = std::chrono::steady_clock::now();
     const size_t bytes = (size_t)nrhs * nvol(h) * sizeof(double2);
     const bool din = is_device_ptr(rhs), dout = is_device_ptr(u);
+    if ((din && misaligned16(rhs)) || (dout && misaligned16(u)))
+        return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
     helm_status s;
     const double2* F = (const double2*)rhs;
     double2* U = (double2*)u;
@@ -1168,18 +1177,23 @@ helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc, const
         if (rec_idx[i] < 0 || rec_idx[i] >= NV) return fail(h, HELM_EINVAL, "receiver index out of range");
     const size_t vb = (size_t)nsrc * NV * sizeof(double2);
     helm_status s;
-    // ws_grad holds F/Q, U, MU, gpad, gint, receivers, gathered values
+    // ws_grad holds F/Q, U, MU, gpad, gint, receivers, gathered values, each starting on a
+    // 256-byte boundary (the complex128 arrays need 16-byte alignment whatever the counts)
     const int64_t nint = h->n[0] * h->n[1] * h->n[2];
-    const size_t need = 3 * vb + (size_t)NV * sizeof(double) + (size_t)nint * sizeof(double) +
-                        (size_t)nrec * sizeof(int64_t) + (size_t)nsrc * nrec * sizeof(double2) + 256;
-    if ((s = ws_reserve(h, h->ws_grad, need)) != HELM_OK) return s;
-    double2* FQ = (double2*)h->ws_grad.p;
-    double2* U = FQ + (size_t)nsrc * NV;
-    double2* MU = U + (size_t)nsrc * NV;
-    double* gpad = (double*)(MU + (size_t)nsrc * NV);
-    double* gint = gpad + NV;
-    int64_t* drec = (int64_t*)(gint + nint);
-    double2* gath = (double2*)(drec + nrec);
+    const size_t part[7] = {vb, vb, vb, (size_t)NV * sizeof(double), (size_t)nint * sizeof(double),
+                            (size_t)nrec * sizeof(int64_t), (size_t)nsrc * nrec * sizeof(double2)};
+    size_t off[8];
+    off[0] = 0;
+    for (int i = 0; i < 7; ++i) off[i + 1] = off[i] + ((part[i] + 255) & ~(size_t)255);
+    if ((s = ws_reserve(h, h->ws_grad, off[7])) != HELM_OK) return s;
+    char* wb = (char*)h->ws_grad.p;
+    double2* FQ = (double2*)(wb + off[0]);
+    double2* U = (double2*)(wb + off[1]);
+    double2* MU = (double2*)(wb + off[2]);
+    double* gpad = (double*)(wb + off[3]);
+    double* gint = (double*)(wb + off[4]);
+    int64_t* drec = (int64_t*)(wb + off[5]);
+    double2* gath = (double2*)(wb + off[6]);
     // sources: discrete deltas 1/h^dim
     const double amp = 1.0 / pow(h->h, h->dim);
     CK(h, cudaMemsetAsync(FQ, 0, vb, h->stream));
@@ -1341,6 +1355,8 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
     if (!h->factored) return fail(h, HELM_ESTATE, "apply_precond_noalloc before factor");
     if (!is_device_ptr(in) || !is_device_ptr(out))
         return fail(h, HELM_EINVAL, "apply_precond_noalloc takes device pointers only (host staging would allocate)");
+    if (misaligned16(in) || misaligned16(out))
+        return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
     if ((const void*)in == (const void*)out)
         return fail(h, HELM_EINVAL, "apply_precond_noalloc needs distinct input and output buffers");
     size_t sz[kPrecondBufs];

@@ -274,3 +274,18 @@ def test_full_size_smooth1023_mixed_solve_properties():
     b = g64.interfaces()
     cols = sorted({b[j] + 1 for j in range(1, wl.J)} | {b[j] + 2 for j in range(1, wl.J)})
     assert np.linalg.norm(np.delete(res, cols, axis=-1)) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_misaligned_device_field_is_an_argument_error():
+    import ctypes
+    import torch
+    g = helm.HelmDD(media.smooth_medium((20, 16), 2.0, 1.0, 2.0, 1), 1.0 / 24, 30.0, 3, 2, 2, "mixed").factor()
+    n = g.ndof
+    buf = torch.zeros(2 * n + 2, dtype=torch.float64, device="cuda")   # complex128 field 8 bytes off
+    out = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    p_in = ctypes.c_void_p(buf.data_ptr() + 8)
+    p_out = ctypes.c_void_p(out.data_ptr())
+    assert g.lib.helm_dd_apply_precond(g._h, p_in, p_out, 1) == -1   # HELM_EINVAL, nothing launched
+    assert b"16-byte" in g.lib.helm_dd_last_error(g._h)
+    assert g.lib.helm_dd_matvec(g._h, p_in, p_out, 1) == -1
+    g.close()

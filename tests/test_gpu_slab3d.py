@@ -132,3 +132,24 @@ def test_slab_block_size_limit_is_an_argument_error():
     assert e.value.status == -1   # HELM_EINVAL
     assert "2048" in str(e.value)
     g.close()
+
+
+def test_slab_gradient_matches_oracle():
+    from oracle.helm_oracle import misfit_and_gradient, receiver_data
+    n = (14, 10, 12)
+    w = 3
+    h = 1.0 / 24
+    c0 = media.smooth_medium(n, 2.0, 1.0, 2.0, 3)
+    c = c0 * (1 + 0.1 * media.smooth_medium(n, 2.0, 0.0, 1.0, 4))
+    omega = media.omega_for(c0, h, 8.0)
+    cref = 2.5
+    src = [media.padded_index((x, 0, z), n, w) for x, z in ((3, 4), (10, 7))]
+    rec = [media.padded_index((x, 0, z), n, w) for x in range(0, 14, 3) for z in range(0, 12, 4)]
+    d = receiver_data(c0, h, omega, w, src, rec, c_ref=cref)
+    Jo, go = misfit_and_gradient(c, h, omega, w, src, rec, d, c_ref=cref)
+    for prec in ("fp64", "mixed"):
+        g = helm.HelmDD(c, h, omega, w, 3, 2, prec, c_ref=cref).factor()
+        Jg, gg = g.gradient(src, rec, d, tol=1e-9)
+        assert abs(Jg - Jo) <= 1e-3 * abs(Jo)
+        assert rel(gg, go) <= 1e-3
+        g.close()
