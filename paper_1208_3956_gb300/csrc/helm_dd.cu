@@ -492,8 +492,8 @@ helm_status factor_slabs(helm_dd* h) {
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     // scratch of the block inversions
     const size_t es = h->esize;
-    const size_t mbytes = (size_t)ldmax * nmax * es, multb = (size_t)2 * ldmax * es;
-    const size_t ibytes = (size_t)(2 * nmax + 2 + 2) * sizeof(int);
+    const size_t mbytes = (size_t)ldmax * nmax * es, multb = (size_t)nmax * ldmax * es;
+    const size_t ibytes = (size_t)(3 * nmax + 2) * sizeof(int);
     void* scratch = nullptr;
     CK(h, cudaMalloc(&scratch, mbytes + multb + ibytes));
     SlabScratch sc{};
@@ -503,7 +503,7 @@ helm_status factor_slabs(helm_dd* h) {
     sc.perm = (int*)((char*)scratch + mbytes + multb);
     sc.pinv = sc.perm + nmax;
     sc.pivrow = sc.pinv + nmax;
-    sc.bar = (unsigned*)(sc.pivrow + 2);
+    sc.bar = (unsigned*)(sc.pivrow + nmax);
     cudaError_t e = cudaSuccess;
     for (size_t jj = 0; jj < h->strips.size() && e == cudaSuccess; ++jj) {
         if (h->prec == HELM_PREC_MIXED)

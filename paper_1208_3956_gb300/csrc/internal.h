@@ -137,8 +137,8 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, co
 
 // ---- slab3d.cu: strips of a 3-D grid (one dense block of n = W N_z unknowns per row y)
 // Scratch of the factorisation: the block being inverted (column-major, ldm >= n),
-// the exchanged pivot column (2 x ldm), the row exchanges and their inverse, the
-// published pivot rows (2) and the grid-barrier counter.
+// the published exchanged pivot columns (n x ldm, one per elimination step), the row
+// exchanges and their inverse, the published pivot rows (n) and the step counter.
 struct SlabScratch {
     void* M;
     void* mult;

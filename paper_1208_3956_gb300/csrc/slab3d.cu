@@ -44,26 +44,20 @@ template <typename C> __device__ __forceinline__ C ldcg(const C* p);
 template <> __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 template <> __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
 
-// Barrier over all CTAs of a cooperative launch (co-resident by construction).
-// The counter rises by one per CTA and barrier; target = CTAs x barriers so far.
-// A wait that gives up records 7 in the status word and returns false.
-__device__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        unsigned v = ld_acquire_gpu(ctr);
-        for (uint32_t it = 0; v < target && it < kBarPolls; ++it) {
-            __nanosleep(32);
-            v = ld_acquire_gpu(ctr);
-        }
-        ok = v >= target;
-        if (!ok) atomicExch(status, 7);
-        __threadfence();
+// One thread waits (bounded) until the counter reaches target; a wait that gives up
+// records 7 in the status word and returns false.
+__device__ bool wait_count(const unsigned* ctr, unsigned target, int* status) {
+    unsigned v = ld_acquire_gpu(ctr);
+    for (uint32_t it = 0; v < target && it < kBarPolls; ++it) {
+        __nanosleep(20);
+        v = ld_acquire_gpu(ctr);
     }
-    __syncthreads();
-    return ok != 0;
+    if (v >= target) return true;
+    atomicExch(status, 7);
+    return false;
+}
+__device__ __forceinline__ void add_release(unsigned* ctr) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
 }
 
 // ------------------------------------------------------------ block entries
@@ -139,9 +133,11 @@ __global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, 
 // launch.  Step i: rows i and p (the largest |M(r,i)|, r >= i) are exchanged,
 // the pivot row is scaled by 1/M(p,i) with M(i,i) <- 1/pivot, and every other
 // row r loses m_r times it with M(r,i) <- -m_r/pivot (m_r = M(r,i) after the
-// exchange).  The owner of column i publishes p and the exchanged column m
-// (double-buffered by step parity) before the barrier of step i; it updates
-// column i+1 first, so the next pivot search starts as soon as possible.  The
+// exchange).  The owner of column i publishes p and the exchanged column m (one
+// buffer per step, never reused, so a CTA may trail the others by any number of
+// steps) and raises the published-step counter bar[0] (release, zero at launch); a
+// CTA starts step i once that counter says so (acquire).  Only the owner of the next
+// column, which it updates first, is on the critical path.  The
 // result is (P M)^{-1} for the product P of the exchanges; pinv[c] = the
 // position of original row c after all exchanges, so M^{-1}(:, c) = result(:, pinv[c]).
 // cached != 0: a CTA keeps its columns in shared memory for the whole elimination.
@@ -155,7 +151,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
     __shared__ C s_ai[kGjMaxCols], s_ap[kGjMaxCols];
     __shared__ R s_best[kGjThreads / 32];
     __shared__ int s_bidx[kGjThreads / 32];
-    __shared__ int s_p;
+    __shared__ int s_p, s_ok;
     __shared__ int s_rows[kGjThreads * kGjRowsPerThread];
     const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
     const int ncol = b < n ? (n - 1 - b) / nb + 1 : 0;   // owned columns b, b+nb, ...
@@ -195,19 +191,23 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
                 bx = i;
             }
             s_p = bx;
-            pivrow[i & 1] = bx;
+            pivrow[i] = bx;
         }
         __syncthreads();
         const int p = s_p;
-        C* mu = mult + (int64_t)(i & 1) * ldm;
+        C* mu = mult + (int64_t)i * ldm;
         for (int r = tid; r < n; r += kGjThreads) mu[r] = col[r == i ? p : (r == p ? i : r)];
+        __syncthreads();
+        if (tid == 0) add_release(bar);   // step i published
     };
 
     if (b == 0 && ncol > 0) publish(0);   // column 0 belongs to CTA 0
     for (int i = 0; i < n; ++i) {
-        if (!grid_barrier(bar, (unsigned)(i + 1) * nb, status)) return;
-        const int p = __ldcg(pivrow + (i & 1));
-        const C* mu = mult + (int64_t)(i & 1) * ldm;
+        if (tid == 0) s_ok = wait_count(bar, (unsigned)(i + 1), status);
+        __syncthreads();
+        if (!s_ok) return;
+        const int p = __ldcg(pivrow + i);
+        const C* mu = mult + (int64_t)i * ldm;
         const C ip = cinv(ldcg(mu + i));
         if (b == 0 && tid == 0) perm[i] = p;
         C m_r[kGjRowsPerThread];
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gj_invert(C* __restrict__ M, int
         }
         for (int lc = 0; lc < ncol; ++lc)
             if (lc != lcn) update(lc);
+        __syncthreads();   // s_ai / s_ap are rewritten at the next step
     }
     if (cached) {
         __syncthreads();
@@ -626,7 +627,7 @@ cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, co
             k_slab_build<C><<<tiles, 256, 0, s>>>(g, st, k, k > 0 ? X + (int64_t)(k - 1) * st.bs : nullptr, st.ld,
                                                    M, sc.ldm);
         }
-        e = cudaMemsetAsync(sc.bar, 0, sizeof(unsigned), s);
+        e = cudaMemsetAsync(sc.bar, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         {
             TimedLaunch t(tm, "slab_gj_invert", s);

@@ -45,6 +45,26 @@ def test_noalloc_matches_apply_precond_on_two_calls(prec, chunks):
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_noalloc_matches_apply_precond_3d(prec):
+    # 3-D strips: right-hand sides and two strip solutions in the array, and the strip
+    # solve's step counter (a second call must find it reset)
+    torch = pytest.importorskip("torch")
+    n = (17, 13, 11)
+    c = media.smooth_medium(n, 2.0, 1.0, 2.0, 7)
+    h = 1.0 / 24
+    g = helm.HelmDD(c, h, media.omega_for(c, h, 8.0), 4, 3, 3, prec).factor()
+    for call, seed in enumerate((31, 32)):
+        f = torch.as_tensor(media.random_rhs((2,) + g.shape, seed), device="cuda")
+        ref = g.apply_precond(f)
+        out = torch.empty_like(f)
+        got = g.apply_precond_noalloc(f, out=out)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+        assert err <= TOL, (call, err)
+    g.close()
+
+
 def test_noalloc_rejects_oversize_batch_and_host_pointers():
     torch = pytest.importorskip("torch")
     g = _problem("mixed")
