@@ -196,7 +196,8 @@ int helm_dd_kernel_stats(helm_dd* h, char (*names)[48], int64_t* launches,
                          double* total_ms, int cap);
 
 /* Bytes of factor data one preconditioner application reads by the method's
- * own count (2 passes x sum over strip solves of N_y W_j^2 x element size). */
+ * own count (2 passes x sum over strip solves of N_y n_j^2 x element size, with
+ * n_j = W_j in 2-D and W_j N_z in 3-D). */
 double helm_dd_precond_factor_bytes(const helm_dd* h);
 
 /* Padded sizes N[0..2]; strip widths W_j (J entries) when W != NULL. */

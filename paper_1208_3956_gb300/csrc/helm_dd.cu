@@ -1259,7 +1259,8 @@ double helm_dd_precond_factor_bytes(const helm_dd* h) {
     if (!h) return 0.0;
     double b = 0.0;
     for (int j = 0; j < h->J; ++j) {
-        const double blk = (double)h->N[1] * h->strips[j].W * h->strips[j].W * h->esize;
+        const double n = (double)h->strips[j].W * h->N[2];   // unknowns of a block (N_z = 1 in 2-D)
+        const double blk = (double)h->N[1] * n * n * h->esize;
         b += 2.0 * blk * (j < h->J - 1 ? 2.0 : 1.0);
     }
     return b;

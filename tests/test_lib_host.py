@@ -53,6 +53,21 @@ def test_strip_geometry_matches_oracle(lib, name):
     s.close()
 
 
+def test_3d_geometry_and_factor_bytes(lib):
+    # slabs: a block holds W_j x-columns times all N_z planes
+    wl = media.WORKLOADS["smooth63_3d"]
+    c = media.medium("smooth63_3d")
+    s = helm.HelmDD(c, wl.h, media.omega_for(c, wl.h, wl.ppw), wl.w_outer, wl.w_sub, wl.J, "mixed")
+    p = HelmholtzDD(c, wl.h, media.omega_for(c, wl.h, wl.ppw), wl.w_outer, wl.w_sub, wl.J)
+    assert s.N == (79, 79, 79)
+    W = s.strip_widths()
+    assert W == [st.W for st in p.strips]
+    assert s.interfaces() == p.beta
+    ref = sum(2 * 79 * (w * 79) ** 2 * 8 * (2 if j < wl.J - 1 else 1) for j, w in enumerate(W))
+    assert s.precond_factor_bytes() == pytest.approx(ref)
+    s.close()
+
+
 def test_small_ragged_geometry(lib):
     c = np.full((29, 37), 1.5)
     s = helm.HelmDD(c, 0.05, 3.0, 5, 4, 3, "fp64")
