@@ -363,6 +363,58 @@ class HelmholtzDD:
         """GMRES on A P v = f, u = P v (Eq. left_preconditioned); returns (u, iters, relres)."""
         return fgmres(self.matvec, self.apply_precond, f, tol, restart, maxit)
 
+    # -- Section 2.3 ("Algorithm"), Algorithms 2-5: the reduced space ---------
+    def interface_columns(self) -> np.ndarray:
+        """The 2(J-1) grid lines beta_j+1, beta_j+2 (j = 1..J-1 in the paper's count)
+        that carry the residual f - A P f (Section 2.3)."""
+        cols = []
+        for j in range(1, self.J):
+            cols += [self.beta[j] + 1, self.beta[j] + 2]
+        return np.array(cols, dtype=int)
+
+    def reduce_rhs(self, f: np.ndarray):
+        """Algorithm 2: u~^(j) solves A^(j) u~^(j) = f restricted to
+        D~^(j) = {beta~_{j-1}+1 .. beta~_j}, beta~_j = beta_j + 1 (Eq. reduce_compute_ut);
+        u~ = u~^(j) on D~^(j); returns (phi, u~) with phi = f - A u~."""
+        f = np.asarray(f, dtype=complex)
+        beta, J = self.beta, self.J
+        ut = np.zeros_like(f)
+        for j in range(J):
+            st = self.strips[j]
+            lo_t = beta[j] + 2 if j > 0 else 0
+            hi_t = beta[j + 1] + 1 if j < J - 1 else self.N[0] - 1
+            dt = np.arange(lo_t, hi_t + 1)
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            r[..., dt - st.lo + st.lpml] = f[..., dt]
+            uj = self.strip_solve(j, r)
+            ut[..., dt] = uj[..., dt - st.lo + st.lpml]
+        return f - self.matvec(ut), ut
+
+    def apply_AP_reduced(self, y: np.ndarray) -> np.ndarray:
+        """Algorithm 3 on a field given on the interface lines only (y[..., i] is
+        line interface_columns()[i]): forward sweep, g = f - A v, backward sweep,
+        h = g - A w, output f - h (= A P f), restricted to the interface lines."""
+        cols = self.interface_columns()
+        shape = tuple(reversed(self.N))
+        f = np.zeros(y.shape[:-1] + (shape[-1],), dtype=complex)
+        f[..., cols] = y
+        _, _, g, w = self.apply_precond(f, return_parts=True)
+        h = g - self.matvec(w)
+        return (f - h)[..., cols]
+
+    def solve_reduced(self, f: np.ndarray, tol=1e-6, restart=20, maxit=200):
+        """Algorithm 5: phi from Algorithm 2; GMRES on A P xi = phi in the reduced space
+        (Eq. solve_A_reduced with psi = P xi); Algorithm 4: u = P xi + u~.
+        Returns (u, iterations, relative residual of the reduced system, history)."""
+        phi, ut = self.reduce_rhs(f)
+        cols = self.interface_columns()
+        if cols.size == 0:                       # J = 1: u~ = A^-1 f, phi = 0
+            return ut, 0, 0.0, []
+        xi, iters, rr, hist = fgmres(self.apply_AP_reduced, lambda v: v, phi[..., cols], tol, restart, maxit)
+        full = np.zeros_like(ut)
+        full[..., cols] = xi
+        return self.apply_precond(full) + ut, iters, rr, hist
+
 
 # ---------------------------------------------------------------------------
 # Right-preconditioned (flexible) GMRES with modified Gram-Schmidt and complex

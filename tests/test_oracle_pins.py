@@ -373,3 +373,64 @@ def test_gradient_matches_central_differences():
         fd = (jp - jm) / (2 * eps)
         an = float(np.sum(grad * dm))
         assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+
+
+# ---------------------------------------------------------------------------
+# Section 2.3 ("Algorithm"), Algorithms 2-5: the reduced space of the 2(J-1)
+# interface lines beta_j+1, beta_j+2
+# ---------------------------------------------------------------------------
+
+def _off_lines(o, field):
+    mask = np.ones(o.N[0], dtype=bool)
+    mask[o.interface_columns()] = False
+    return np.abs(field[..., mask]).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_reduced_rhs_lives_on_the_interface_lines(dim):
+    # Algorithm 2: phi = f - A u~ vanishes off the lines beta_j+1, beta_j+2, while f
+    # and u~ do not (the strip solves reproduce f inside every D~^(j))
+    o = _small_problem(dim=dim, J=3).factor()
+    f = media.random_rhs(tuple(reversed(o.N)), 11)
+    phi, ut = o.reduce_rhs(f)
+    assert o.interface_columns().size == 2 * (o.J - 1)
+    assert _off_lines(o, phi) <= 1e-12 * np.abs(f).max()
+    assert np.abs(phi[..., o.interface_columns()]).max() > 1e-3 * np.abs(f).max()
+
+
+def test_AP_keeps_interface_support_and_algorithm3_equals_A_P():
+    # the residual f - APf lives on the lines (Section 2.3), so AP maps the reduced
+    # space into itself; Algorithm 3's output f - h is A(v + w) = A P f
+    o = _small_problem(J=4).factor()
+    cols = o.interface_columns()
+    y = media.random_rhs(tuple(reversed(o.N))[:-1] + (cols.size,), 12)
+    f = np.zeros(tuple(reversed(o.N)), dtype=complex)
+    f[..., cols] = y
+    APf = o.matvec(o.apply_precond(f))
+    assert _off_lines(o, APf) <= 1e-12 * np.abs(APf).max()
+    assert np.abs(o.apply_AP_reduced(y) - APf[..., cols]).max() <= 1e-12 * np.abs(APf).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_reduced_solve_matches_the_direct_solve(dim):
+    # Algorithm 5 (Algorithms 2, 3 in GMRES, 4) against the plain definition u = A^-1 f
+    o = _small_problem(dim=dim, J=3).factor()
+    f = media.random_rhs(tuple(reversed(o.N)), 13)
+    u, iters, rr, _ = o.solve_reduced(f, tol=1e-10)
+    ud = o.direct_solve(f)
+    assert rr <= 1e-10
+    assert 1 <= iters <= 40
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) <= 1e-7
+    assert np.linalg.norm(f - o.matvec(u)) / np.linalg.norm(f) <= 1e-9
+
+
+def test_reduced_space_is_empty_for_one_strip():
+    # J = 1: no interfaces, u~ = A^-1 f and phi = 0, no GMRES iteration
+    o = _small_problem(J=1).factor()
+    f = media.random_rhs(tuple(reversed(o.N)), 14)
+    phi, ut = o.reduce_rhs(f)
+    assert np.abs(phi).max() <= 1e-12 * np.abs(f).max()
+    u, iters, _, _ = o.solve_reduced(f)
+    assert iters == 0
+    ud = o.direct_solve(f)
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) <= 1e-12
