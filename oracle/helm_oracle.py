@@ -10,7 +10,7 @@ it follows.  Arithmetic is complex128 throughout; matrices are assembled with
 scipy.sparse and factored with SuperLU.  Nothing here is blocked, fused or
 reordered beyond what the paper's definitions state.
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open (the design notes list each one too):
 
 * PML profile (Section 2.1 leaves sigma unspecified): quadratic
   ``sigma(d) = sigma0 * (d/L)^2`` with ``L = w*h`` and
