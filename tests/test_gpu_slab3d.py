@@ -8,6 +8,7 @@ Bars (written here, from the arithmetic):
   one strip (J = 1) ...... A (P f) = f to 1e-10 (P is the exact inverse)
   solve .................. true residual <= tol; solution within 1e-4 of the oracle's;
                            iterations within +-1
+  gradient ............... 1e-3 relative (misfit and dJ/dm against the oracle's direct solves)
 """
 import numpy as np
 import pytest
