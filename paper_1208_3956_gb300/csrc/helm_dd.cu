@@ -180,9 +180,6 @@ void build_tables(helm_dd* h) {
     po.h = h->h;
     po.omega = h->omega;
     po.sigma0 = pml_sigma0(h->c_ref, h->w_outer, h->h);
-    Pml ps = po;
-    ps.w = h->w_sub;
-    ps.sigma0 = pml_sigma0(h->c_ref, h->w_sub, h->h);
     auto axis = [&](int Np, std::vector<cd>& ai, std::vector<cd>& ah) {
         ai.resize(Np);
         ah.resize(Np + 1);
