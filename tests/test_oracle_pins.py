@@ -274,6 +274,21 @@ def test_wider_subdomain_pml_improves_preconditioner():
     assert rel[0] > rel[1] > rel[2], rel
 
 
+def test_wider_subdomain_pml_improves_preconditioner_3d():
+    """The same trend on a 3-D constant medium (Section 4, Table 3: thicker added layers,
+    fewer iterations); slabs of W x-columns by all z-planes."""
+    n, h = (23, 15, 15), 1.0 / 16
+    c = np.ones((n[2], n[1], n[0]))
+    omega = 2 * math.pi / (8 * h)
+    f = media.point_sources(n, 5, h, [(11, 7, 7)])[0]
+    rel = []
+    for ws in (1, 3, 5):
+        p = HelmholtzDD(c, h, omega, 5, ws, 3).factor()
+        rel.append(np.linalg.norm(f - p.matvec(p.apply_precond(f))) / np.linalg.norm(f))
+    assert rel[0] > rel[1] > rel[2], rel
+    assert rel[2] < 0.05
+
+
 def test_iteration_band_of_table4():
     """Constant 2-D medium, layers of 10 points: iterations in the band of Table 4."""
     rows = np.loadtxt(os.path.join(GOLDEN, "table4_pml_iterations.txt"))
