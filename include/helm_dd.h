@@ -112,6 +112,14 @@ helm_status helm_dd_set_sep_groups(helm_dd* h, int G);
 /* G in use after helm_dd_factor (0 before). */
 int helm_dd_sep_groups(const helm_dd* h);
 
+/* Right-hand sides per internal panel of helm_dd_solve and helm_dd_gradient (the
+ * batching of Section 4's many-source runs, not the paper's own parameter): a
+ * call with more right-hand sides runs them panel after panel, so that the
+ * Krylov basis (2 restart + 2 complex128 fields per right-hand side) and the
+ * sweep buffers are held for one panel only.  0 (the default) takes as many as
+ * the free device memory holds.  Results do not depend on the panel width. */
+helm_status helm_dd_set_panel(helm_dd* h, int nrhs);
+
 /* Algorithm 1 (preparation): assemble every strip operator A^(j) on the grid of
  * Eq. grid_A_j (physical columns beta_{j-1}+1 .. beta_j+1 plus w_sub added PML
  * columns on internal sides, k held constant in x across an added layer) in its
@@ -119,7 +127,9 @@ int helm_dd_sep_groups(const helm_dd* h);
  * matrix along y.  Factors stay on the device.  Returns HELM_ENUMERIC on a
  * numerically singular block.
  * 2-D grids: W x W blocks, partitioned along y (nested dissection) for the
- * parallel sweep.  3-D grids: one dense block of n = W N_z unknowns (a slab of
+ * parallel sweep; a strip solve keeps a ring of at least four blocks in shared
+ * memory, so HELM_EINVAL when a strip is too wide for it (complex128: about 50
+ * columns; complex64: 64).  3-D grids: one dense block of n = W N_z unknowns (a slab of
  * W x-columns by all z-planes) per grid row y, factored top down with every
  * block inverted by Gauss-Jordan elimination with partial pivoting; its
  * inversions and the strip solves of the sweep run as cooperative launches
@@ -141,17 +151,20 @@ helm_status helm_dd_apply_precond(helm_dd* h, const double* in, double* out, int
  * device memory, programs near the memory limit where a late workspace
  * allocation could fail, and latency-critical loops where cudaMalloc/cudaFree
  * would stall the device.  The work buffers come from one 64 MiB file-scope
- * device array that every GPU loading the library holds until process exit.
+ * device array.  The array (and every kernel module the call launches) is
+ * loaded onto a device, and its 64 MiB taken, when a handle first uses that
+ * device (in helm_dd_factor, with the handle's other device memory); its
+ * device address is looked up there too, once per device with that device
+ * current.  It is held until the process exits.  The call itself allocates
+ * nothing.
  *   in, out   DEVICE pointers (complex128 fields as above), distinct; host
  *             pointers are rejected because staging them would allocate
  *   nrhs      number of fields; HELM_EINVAL (with the byte count in
  *             helm_dd_last_error) when 2*nrhs*N*16 bytes plus the strip
  *             buffers exceed the 64 MiB limit
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and each reuses what the previous
- * call left there, so calls that overlap on the GPU (other threads, other
- * handles, other streams) race and must be serialised by the caller.
+ * All calls share the one array and each reuses what the previous call left
+ * there, so calls that overlap on the GPU (other threads, other handles,
+ * other streams) race and must be serialised by the caller.
  * HELM_ESTATE before helm_dd_factor. */
 helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* in, double* out, int nrhs);
 
@@ -167,6 +180,48 @@ helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs);
 helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs,
                           double tol, int restart, int maxit, helm_rhs_info* info);
 
+/* ---- The reduced space (Section 2.3, "Algorithm"; Algorithms 2-5).
+ * Since f - A P f vanishes off the 2(J-1) grid lines x = beta_j+1, beta_j+2
+ * (j = 1..J-1), GMRES can run on fields given on those lines only.  A reduced
+ * array holds, per right-hand side, N[2] N[1] rows of L = 2(J-1) complex128
+ * values, interleaved: element (b, z, y, i) sits at complex offset
+ * ((b*N[2] + z)*N[1] + y)*L + i and is the field at padded column cols[i] of
+ * helm_dd_interface_lines.  Pointers may be host or device, as for fields. */
+
+/* L = 2(J-1); the padded columns of the interface lines (beta_j+1, beta_j+2 for
+ * j = 1..J-1, in that order) are written to cols[0..min(L, cap)-1]. */
+int helm_dd_interface_lines(const helm_dd* h, int* cols, int cap);
+
+/* Algorithm 2 (Eq. reduce_compute_ut): u~^(j) solves A^(j) u~^(j) = f restricted
+ * to D~^(j) = {beta_{j-1}+2 .. beta_j+1} (from column 0 for the first strip, to
+ * N[0]-1 for the last), u~ = u~^(j) on D~^(j); phi = f - A u~, which vanishes
+ * off the interface lines, is written in reduced form.  The J strip solves are
+ * independent.  ut (a full field per right-hand side) may be NULL; phi may be
+ * NULL when J = 1.  HELM_ESTATE before helm_dd_factor. */
+helm_status helm_dd_reduce_rhs(helm_dd* h, const double* f, double* phi, double* ut, int nrhs);
+
+/* Algorithm 3 on reduced arrays: out = R A P E in, with E the extension by zero
+ * to the padded grid and R the restriction to the interface lines (the forward
+ * sweep, the residual, the backward sweep and A applied to P E in; the result is
+ * supported on the interface lines up to rounding).  in and out distinct. */
+helm_status helm_dd_apply_AP_reduced(helm_dd* h, const double* in, double* out, int nrhs);
+
+/* Algorithm 5 in the reduced space: phi from Algorithm 2, GMRES(restart) on
+ * R A P E xi = phi (Eq. solve_A_reduced with psi = P E xi; vectors of N[2] N[1] L
+ * entries per right-hand side, x0 = 0), u = P E xi + u~ (Algorithm 4).  GMRES
+ * stops when the reduced residual would bring ||f - A u|| to tol ||f|| (in
+ * mixed precision at 1e-3 of its right-hand side at the tightest: the complex64
+ * operator is linear only up to its rounding); the true residual is then
+ * formed on the whole grid in FP64 and, where it is still above tol ||f||
+ * (complex64 strip solves leave small residuals off the lines, which the
+ * reduced space does not see), the same steps are repeated on it (defect
+ * correction, at most 8 passes).  info: GMRES iterations summed over the
+ * passes, the true relative residual, the batch time.  Right-hand sides run in
+ * panels (helm_dd_set_panel).  HELM_ENOTCONV (u and info written) when the
+ * tolerance is not reached within maxit iterations. */
+helm_status helm_dd_solve_reduced(helm_dd* h, const double* rhs, double* u, int nrhs, double tol, int restart,
+                                  int maxit, helm_rhs_info* info);
+
 /* Least-squares misfit J = 1/2 sum_s ||R u_s - d_s||^2 and its gradient with
  * respect to m = 1/c^2 on the interior grid (not in the paper: the adjoint of
  * A(m) = L - omega^2 diag(m)).  Sources are discrete deltas 1/h^dim at the
@@ -175,7 +230,11 @@ helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs,
  * S^-1 conj(R^T r_s)) share the factors; grad = omega^2 Re sum_s S mu_s u_s,
  * folded from the padded grid onto the interior through the clamp extension.
  * The PML profile is held fixed.  misfit and grad_m (interior size) are
- * written; tol is the GMRES tolerance of both solves. */
+ * written; tol is the GMRES tolerance of both solves.  grad_m may be NULL:
+ * then only the forward solves run and only the misfit is written.  Sources
+ * are processed in panels (helm_dd_set_panel; by default as many as the free
+ * device memory holds): a panel's forward fields are kept only until its
+ * adjoint solves are done. */
 helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc,
                              const int64_t* rec_idx, int nrec, const double* d,
                              double tol, double* misfit, double* grad_m);

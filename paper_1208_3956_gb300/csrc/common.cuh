@@ -134,6 +134,14 @@ struct Geom {
     // group of the separator above / below the chunk (-1: none, level 2, or G = 1),
     // ra / rb the rows of the level-2 separators above and below that group
     const int4* cmeta;
+    // entries of the paper-form stencil per axis (Section 2.2), three per grid index i:
+    //   {-a(i) a(i-1/2) / h^2, a(i) (a(i-1/2) + a(i+1/2)) / h^2, -a(i) a(i+1/2) / h^2}
+    // and, per axis, the index range [f0, f1) where they are exactly {-1, 2, -1} / h^2
+    // (outside every PML)
+    const double2* stc_x;
+    const double2* stc_y;
+    const double2* stc_z;
+    int fx0, fx1, fy0, fy1, fz0, fz1;
 };
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }

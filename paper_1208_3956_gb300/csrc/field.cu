@@ -41,45 +41,111 @@ cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, 
 }
 
 // ---------------------------------------------------------------- stencil
-// (A u)_p = sum_axes -a(i)[a(i+1/2)(u_{i+1}-u_i) - a(i-1/2)(u_i-u_{i-1})]/h^2 - k^2 u_p
-__device__ __forceinline__ double2 axis_term(double2 ai, double2 ap, double2 am, double2 u, double2 up,
-                                             double2 um) {
-    const double2 fwd = cmul(ap, csub(up, u));
-    const double2 bwd = cmul(am, csub(u, um));
-    return cneg(cmul(ai, csub(fwd, bwd)));
+// (A u)_p = sum_axes [cm(i) u_{i-1} + c0(i) u_i + cp(i) u_{i+1}] - k^2 u_p with the
+// per-axis entries of Geom::stc_* (Section 2.2, paper form; u = 0 beyond the grid).
+//
+// On GB300 the FP64 pipe, not HBM, bounds this kernel, so it is organised to issue
+// few FP64 instructions per point: a thread owns one x column of a tile of kRows
+// rows and marches along y with u(y-1), u(y), u(y+1) in registers (each value is
+// loaded once), takes its x neighbours from the adjacent lanes by shuffles, and
+// outside every PML (all entries exactly {-1, 2, -1}/h^2) evaluates
+//   (2 dim / h^2 - k^2) u - (sum of the 2 dim neighbours) / h^2
+// (13 FP64 instructions per point in 2-D, against 25 for the general complex form).
+constexpr int kStencilRows = 16;
+constexpr int kStencilThreads = 128;
+
+__device__ __forceinline__ double2 shfl_c(double2 v, int delta, bool up) {
+    double2 r;
+    r.x = up ? __shfl_up_sync(0xffffffffu, v.x, delta) : __shfl_down_sync(0xffffffffu, v.x, delta);
+    r.y = up ? __shfl_up_sync(0xffffffffu, v.y, delta) : __shfl_down_sync(0xffffffffu, v.y, delta);
+    return r;
 }
 
-__global__ void k_stencil(Geom g, const double2* __restrict__ u, const double2* __restrict__ f,
-                          double2* __restrict__ out, int B) {
+template <bool Z>
+__global__ void __launch_bounds__(kStencilThreads) k_stencil(Geom g, const double2* __restrict__ u,
+                                                             const double2* __restrict__ f,
+                                                             double2* __restrict__ out) {
     const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
+    const int x = blockIdx.x * kStencilThreads + threadIdx.x;
+    const bool on = x < Nx;
+    const int xc = on ? x : Nx - 1;
+    const int lane = threadIdx.x & 31;
+    const int y0 = blockIdx.y * kStencilRows, y1 = min(y0 + kStencilRows, Ny);
+    const int bz = blockIdx.z;
+    const int z = bz % Nz;
     const int64_t plane = (int64_t)Nx * Ny;
-    const int64_t vol = plane * Nz;
-    const int64_t tot = vol * B;
+    const int64_t pbase = (int64_t)bz * plane;          // field offset of plane (b, z)
+    const double* k2 = g.k2 + (int64_t)z * plane;
     const double2 zero = make_double2(0.0, 0.0);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i % vol;
-        const int x = (int)(p % Nx);
-        const int y = (int)((p / Nx) % Ny);
-        const int z = (int)(p / plane);
-        const double2 uc = u[i];
-        double2 acc = axis_term(g.gx_int[x], g.gx_half[x + 1], g.gx_half[x], uc,
-                                x + 1 < Nx ? u[i + 1] : zero, x > 0 ? u[i - 1] : zero);
-        acc = cadd(acc, axis_term(g.gy_int[y], g.gy_half[y + 1], g.gy_half[y], uc,
-                                  y + 1 < Ny ? u[i + Nx] : zero, y > 0 ? u[i - Nx] : zero));
-        if (Nz > 1)
-            acc = cadd(acc, axis_term(g.gz_int[z], g.gz_half[z + 1], g.gz_half[z], uc,
-                                      z + 1 < Nz ? u[i + plane] : zero, z > 0 ? u[i - plane] : zero));
-        acc = cscale(acc, g.inv_h2);
-        acc = csub(acc, cscale(uc, g.k2[p]));
-        out[i] = f ? csub(f[i], acc) : acc;
+    const double ih2 = g.inv_h2;
+    const double2 cxm = g.stc_x[3 * xc], cx0 = g.stc_x[3 * xc + 1], cxp = g.stc_x[3 * xc + 2];
+    const bool xplain = x >= g.fx0 && x < g.fx1;
+    double2 czm = zero, cz0 = zero, czp = zero;
+    bool zplain = true;
+    if (Z) {
+        czm = g.stc_z[3 * z];
+        cz0 = g.stc_z[3 * z + 1];
+        czp = g.stc_z[3 * z + 2];
+        zplain = z >= g.fz0 && z < g.fz1;
+    }
+    const double dplain = (Z ? 6.0 : 4.0) * ih2;
+    const double2* up = u + pbase + xc;
+    double2 um = (y0 > 0 && on) ? up[(int64_t)(y0 - 1) * Nx] : zero;
+    double2 uc = on ? up[(int64_t)y0 * Nx] : zero;
+    for (int y = y0; y < y1; ++y) {
+        const int64_t row = (int64_t)y * Nx;
+        const double2 un = (y + 1 < Ny && on) ? up[row + Nx] : zero;
+        // x neighbours: adjacent lanes, the warp's edge lanes from memory
+        double2 uxm = shfl_c(uc, 1, true), uxp = shfl_c(uc, 1, false);
+        if (lane == 0) uxm = (on && x > 0) ? up[row - 1] : zero;
+        if (lane == 31 || x == Nx - 1) uxp = (on && x + 1 < Nx) ? up[row + 1] : zero;
+        double2 uzm = zero, uzp = zero;
+        if (Z) {
+            uzm = (on && z > 0) ? up[row - plane] : zero;
+            uzp = (on && z + 1 < Nz) ? up[row + plane] : zero;
+        }
+        const double kk = on ? k2[row + xc] : 0.0;
+        double2 acc;
+        if (xplain && y >= g.fy0 && y < g.fy1 && zplain) {
+            double2 sn = cadd(cadd(uxm, uxp), cadd(um, un));
+            if (Z) sn = cadd(sn, cadd(uzm, uzp));
+            const double d = dplain - kk;
+            acc.x = fma(d, uc.x, -ih2 * sn.x);
+            acc.y = fma(d, uc.y, -ih2 * sn.y);
+        } else {
+            const double2 cym = g.stc_y[3 * y], cy0 = g.stc_y[3 * y + 1], cyp = g.stc_y[3 * y + 2];
+            double2 dg = cadd(cx0, cy0);
+            if (Z) dg = cadd(dg, cz0);
+            dg.x -= kk;
+            acc = cmul(dg, uc);
+            acc = cfma(cxm, uxm, acc);
+            acc = cfma(cxp, uxp, acc);
+            acc = cfma(cym, um, acc);
+            acc = cfma(cyp, un, acc);
+            if (Z) {
+                acc = cfma(czm, uzm, acc);
+                acc = cfma(czp, uzp, acc);
+            }
+        }
+        if (on) {
+            const int64_t i = pbase + row + x;
+            out[i] = f ? csub(f[i], acc) : acc;
+        }
+        um = uc;
+        uc = un;
     }
 }
 
 cudaError_t launch_stencil(const Geom& g, const double2* u, const double2* f, double2* out, int B,
                            cudaStream_t s, KernelTimer* tm) {
-    const int64_t tot = (int64_t)g.Nx * g.Ny * g.Nz * B;
+    const dim3 grid((g.Nx + kStencilThreads - 1) / kStencilThreads, (g.Ny + kStencilRows - 1) / kStencilRows,
+                    (unsigned)((int64_t)B * g.Nz));
+    if ((int64_t)B * g.Nz > 65535) return cudaErrorInvalidConfiguration;
     TimedLaunch t(tm, "stencil", s);
-    k_stencil<<<nblocks(tot, 256), 256, 0, s>>>(g, u, f, out, B);
+    if (g.Nz > 1)
+        k_stencil<true><<<grid, kStencilThreads, 0, s>>>(g, u, f, out);
+    else
+        k_stencil<false><<<grid, kStencilThreads, 0, s>>>(g, u, f, out);
     return cudaGetLastError();
 }
 
@@ -204,9 +270,9 @@ cudaError_t launch_scale(double2* dst, const double2* src, const double* scale, 
 }
 
 // ---------------------------------------------------------------- misfit gradient
-// gpad(p) = omega^2 Re sum_s S(p) mu_s(p) u_s(p),  S = prod_axes 1/alpha
+// gpad(p) += omega^2 Re sum_s S(p) mu_s(p) u_s(p),  S = prod_axes 1/alpha
 __global__ void k_grad_accum(Geom g, const double2* __restrict__ U, const double2* __restrict__ MU, int nsrc,
-                             double* __restrict__ gpad) {
+                             double* __restrict__ gpad) {   // adds to gpad
     const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
     const int64_t plane = (int64_t)Nx * Ny, vol = plane * Nz;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < vol; p += (int64_t)gridDim.x * blockDim.x) {
@@ -218,7 +284,7 @@ __global__ void k_grad_accum(Geom g, const double2* __restrict__ U, const double
             const double2 t = cmul(S, cmul(MU[(int64_t)s * vol + p], U[(int64_t)s * vol + p]));
             acc += t.x;
         }
-        gpad[p] = g.omega * g.omega * acc;
+        gpad[p] += g.omega * g.omega * acc;
     }
 }
 
@@ -268,6 +334,117 @@ cudaError_t launch_gather(const double2* U, int64_t ustride, const int64_t* idx,
                           cudaStream_t s) {
     k_gather<<<nblocks((int64_t)B * nidx, 256), 256, 0, s>>>(U, ustride, idx, nidx, B, out);
     return cudaGetLastError();
+}
+
+// dst[b * stride + idx[b][i]] = val[b][i] for i < n: point values of B fields (the host
+// merges repeated indices of a field, so every store of one index writes one value)
+__global__ void k_scatter(double2* __restrict__ dst, int64_t stride, const int64_t* __restrict__ idx,
+                          const double2* __restrict__ val, int n, int B) {
+    const int64_t tot = (int64_t)B * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x)
+        dst[(i / n) * stride + idx[i]] = val[i];
+}
+
+cudaError_t launch_scatter(double2* dst, int64_t stride, const int64_t* idx, const double2* val, int n, int B,
+                           cudaStream_t s) {
+    if (n <= 0 || B <= 0) return cudaSuccess;
+    k_scatter<<<nblocks((int64_t)B * n, 256), 256, 0, s>>>(dst, stride, idx, val, n, B);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- interface lines
+// The reduced space of Section 2.3 holds a field on L grid columns (the 2(J-1) lines
+// beta_j+1, beta_j+2): red[r * L + i] is column cols[i] of grid row r, r running over
+// the B * N_z * N_y rows of B fields.
+__global__ void k_gather_cols(const double2* __restrict__ full, double2* __restrict__ red,
+                              const int* __restrict__ cols, int L, int64_t rows, int Nx) {
+    const int64_t tot = rows * L;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x)
+        red[i] = full[(i / L) * Nx + cols[i % L]];
+}
+
+__global__ void k_scatter_cols(const double2* __restrict__ red, double2* __restrict__ full,
+                               const int* __restrict__ cols, int L, int64_t rows, int Nx) {
+    const int64_t tot = rows * L;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x)
+        full[(i / L) * Nx + cols[i % L]] = red[i];
+}
+
+// out[r * L + i] = f - (A u) at column cols[i] of row r (paper form, the entries of
+// Geom::stc_*), with f the full field f_full at that point or f_red[r * L + i]; when
+// both are null, out = A u there.
+__global__ void k_stencil_cols(Geom g, const double2* __restrict__ u, const double2* __restrict__ f_full,
+                               const double2* __restrict__ f_red, double2* __restrict__ out,
+                               const int* __restrict__ cols, int L, int B) {
+    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
+    const int64_t plane = (int64_t)Nx * Ny;
+    const int64_t rows = (int64_t)B * Nz * Ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * L;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / L;
+        const int x = cols[i % L];
+        const int y = (int)(r % Ny);
+        const int z = (int)((r / Ny) % Nz);
+        const int64_t p = r * Nx + x;
+        const double2 uc = u[p];
+        double2 dg = cadd(g.stc_x[3 * x + 1], g.stc_y[3 * y + 1]);
+        if (Nz > 1) dg = cadd(dg, g.stc_z[3 * z + 1]);
+        dg.x -= g.k2[(int64_t)z * plane + (int64_t)y * Nx + x];
+        double2 acc = cmul(dg, uc);
+        if (x > 0) acc = cfma(g.stc_x[3 * x], u[p - 1], acc);
+        if (x + 1 < Nx) acc = cfma(g.stc_x[3 * x + 2], u[p + 1], acc);
+        if (y > 0) acc = cfma(g.stc_y[3 * y], u[p - Nx], acc);
+        if (y + 1 < Ny) acc = cfma(g.stc_y[3 * y + 2], u[p + Nx], acc);
+        if (Nz > 1) {
+            if (z > 0) acc = cfma(g.stc_z[3 * z], u[p - plane], acc);
+            if (z + 1 < Nz) acc = cfma(g.stc_z[3 * z + 2], u[p + plane], acc);
+        }
+        if (f_full || f_red) acc = csub(f_full ? f_full[p] : f_red[i], acc);
+        out[i] = acc;
+    }
+}
+
+// dst += src over n entries
+__global__ void k_add(double2* __restrict__ dst, const double2* __restrict__ src, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = cadd(dst[i], src[i]);
+}
+
+cudaError_t launch_gather_cols(const double2* full, double2* red, const int* cols, int L, int64_t rows, int Nx,
+                               cudaStream_t s, KernelTimer* tm) {
+    if (L <= 0 || rows <= 0) return cudaSuccess;
+    TimedLaunch t(tm, "iface_gather", s);
+    k_gather_cols<<<nblocks(rows * L, 256), 256, 0, s>>>(full, red, cols, L, rows, Nx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_cols(const double2* red, double2* full, const int* cols, int L, int64_t rows, int Nx,
+                                cudaStream_t s, KernelTimer* tm) {
+    if (L <= 0 || rows <= 0) return cudaSuccess;
+    TimedLaunch t(tm, "iface_scatter", s);
+    k_scatter_cols<<<nblocks(rows * L, 256), 256, 0, s>>>(red, full, cols, L, rows, Nx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_cols(const Geom& g, const double2* u, const double2* f_full, const double2* f_red,
+                                double2* out, const int* cols, int L, int B, cudaStream_t s, KernelTimer* tm) {
+    const int64_t rows = (int64_t)B * g.Nz * g.Ny;
+    if (L <= 0 || rows <= 0) return cudaSuccess;
+    TimedLaunch t(tm, "iface_stencil", s);
+    k_stencil_cols<<<nblocks(rows * L, 256), 256, 0, s>>>(g, u, f_full, f_red, out, cols, L, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add(double2* dst, const double2* src, int64_t n, cudaStream_t s, KernelTimer* tm) {
+    TimedLaunch t(tm, "field_add", s);
+    k_add<<<nblocks(n, 256), 256, 0, s>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+// Loads this file's module onto the current device.
+cudaError_t preload_field_kernels() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, k_copy_cols);
 }
 
 }  // namespace helm

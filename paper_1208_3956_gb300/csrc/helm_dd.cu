@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <complex>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -59,6 +60,7 @@ struct helm_dd {
     int64_t N[3] = {1, 1, 1};
     double h = 1.0, omega = 1.0, c_ref = 0.0;
     int w_outer = 0, w_sub = 0, J = 1, P_req = 0, G_req = 0;
+    int panel = 0;   // right-hand sides per internal panel of solve / gradient (0: as many as fit)
     helm_prec prec = HELM_PREC_FP64;
     std::vector<double> c;
     // geometry
@@ -99,9 +101,13 @@ struct helm_dd {
     bool factored = false;
     bool prepared = false;
     bool dev_ready = false;
+    void* noalloc_base = nullptr;   // device address of the no-allocation scratch array
     // workspaces
     struct Ws { void* p = nullptr; size_t bytes = 0; };
-    Ws ws_V, ws_G, ws_Y, ws_parts, ws_io_in, ws_io_out, ws_kry, ws_small, ws_grad;
+    Ws ws_V, ws_G, ws_Y, ws_parts, ws_io_in, ws_io_out, ws_io_aux, ws_kry, ws_small, ws_grad, ws_red;
+    // interface lines of the reduced space (Section 2.3): padded columns beta_j+1, beta_j+2
+    std::vector<int> icols;
+    int* d_icols = nullptr;
     KernelTimer timer;
     std::string err;
 };
@@ -171,6 +177,11 @@ void build_geometry(helm_dd* h) {
         s.rpml = j < h->J - 1 ? h->w_sub : 0;
         s.W = s.lpml + (s.hi - s.lo + 1) + s.rpml;
         h->Wmax = std::max(h->Wmax, s.W);
+    }
+    h->icols.clear();
+    for (int j = 1; j < h->J; ++j) {
+        h->icols.push_back(h->beta[j] + 1);
+        h->icols.push_back(h->beta[j] + 2);
     }
 }
 
@@ -266,6 +277,49 @@ size_t counter_bytes(const helm_dd* h) { return (size_t)kMaxTiles * (h->G + 1) *
 
 double2 to_d2h(cd v) { return make_double2(v.real(), v.imag()); }
 
+}  // namespace
+
+// ------------------------------------------------------------------------
+// Scratch of the preconditioner application that allocates nothing.
+//
+// Some callers cannot let the library allocate device memory while they run:
+// programs that hand all device memory to their own pool allocator and forbid
+// any other allocation, programs running so close to the memory limit that a
+// late workspace allocation could fail mid-run, and latency-critical loops in
+// which cudaMalloc / cudaFree would stall the whole device.  For them the
+// work buffers of the double sweep come from one file-scope device array.  The
+// CUDA runtime loads it (and takes its memory) on a device when this file's
+// module is first used there, which ensure_device forces at a handle's first
+// device use; it is held until the process exits.
+// ------------------------------------------------------------------------
+static constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};   // device address of the array, per device
+
+// Device address of the scratch array on the current device.  The array's name
+// is only a host-side stand-in, so the address is looked up once per device
+// (with that device current) and cached.  Under lazy module loading the lookup
+// is what loads the array onto the device.
+cudaError_t noalloc_scratch(void** ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // First device use of a handle: stream, medium upload and k^2 (a1).  Creating
 // a handle touches no GPU, so its host-side geometry is usable without one.
 helm_status ensure_device(helm_dd* h) {
@@ -279,6 +333,13 @@ helm_status ensure_device(helm_dd* h) {
         CK(h, cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming));
         CK(h, cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming));
     }
+    // Everything a later call launches is loaded now, where allocation is expected:
+    // the no-allocation scratch array (its address cached per device) and the
+    // modules of the sweep, slab and grid kernels.
+    CK(h, noalloc_scratch(&h->noalloc_base));
+    CK(h, preload_sweep_kernels());
+    CK(h, preload_slab_kernels());
+    CK(h, preload_field_kernels());
     const int64_t nint = (int64_t)h->c.size();
     CK(h, cudaMalloc(&h->d_c, nint * sizeof(double)));
     CK(h, cudaMalloc(&h->d_k2, nvol(h) * sizeof(double)));
@@ -307,6 +368,31 @@ helm_status prepare_geom(helm_dd* h) {
     append(h->gy_half);
     append(h->gz_int);
     append(h->gz_half);
+    // stencil entries per axis: {-a(i) a(i-1/2), a(i) (a(i-1/2) + a(i+1/2)), -a(i) a(i+1/2)} / h^2,
+    // and the index range where they are exactly {-1, 2, -1} / h^2
+    const double ih2s = 1.0 / (h->h * h->h);
+    int frange[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int64_t stc_off[3] = {0, 0, 0};
+    auto stencil_axis = [&](int a, const std::vector<cd>& ai, const std::vector<cd>& ah) {
+        stc_off[a] = (int64_t)tabs.size();
+        const int Np = (int)ai.size();
+        int f0 = -1, f1 = -1;
+        for (int i = 0; i < Np; ++i) {
+            const cd cm = -ai[i] * ah[i] * ih2s, c0 = ai[i] * (ah[i] + ah[i + 1]) * ih2s, cp = -ai[i] * ah[i + 1] * ih2s;
+            tabs.push_back(cm);
+            tabs.push_back(c0);
+            tabs.push_back(cp);
+            const bool plain = cm == cd(-ih2s, 0.0) && cp == cd(-ih2s, 0.0) && c0 == cd(2.0 * ih2s, 0.0);
+            if (plain && f0 < 0) f0 = i;
+            if (plain && f0 >= 0 && f1 < 0 && i == Np - 1) f1 = Np;
+            if (!plain && f0 >= 0 && f1 < 0) f1 = i;
+        }
+        frange[a][0] = f0 < 0 ? 0 : f0;
+        frange[a][1] = f0 < 0 ? 0 : f1;
+    };
+    stencil_axis(0, h->gx_int, h->gx_half);
+    stencil_axis(1, h->gy_int, h->gy_half);
+    stencil_axis(2, h->gz_int, h->gz_half);
     const int64_t stab0 = (int64_t)tabs.size();
     const int Ny = (int)h->N[1];
     for (auto& s : h->strips) {
@@ -370,6 +456,12 @@ helm_status prepare_geom(helm_dd* h) {
     ints.insert(ints.end(), h->gq1.begin(), h->gq1.end());
     ints.insert(ints.end(), h->sepmap.begin(), h->sepmap.end());
     CK(h, cudaMemcpyAsync(h->d_ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (h->d_icols) cudaFree(h->d_icols);
+    h->d_icols = nullptr;
+    CK(h, cudaMalloc(&h->d_icols, std::max<size_t>(h->icols.size(), 1) * sizeof(int)));
+    if (!h->icols.empty())
+        CK(h, cudaMemcpyAsync(h->d_icols, h->icols.data(), h->icols.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              h->stream));
     Geom& g = h->geom;
     g.dim = h->dim;
     g.Nx = (int)h->N[0];
@@ -389,6 +481,12 @@ helm_status prepare_geom(helm_dd* h) {
     g.gz_int = h->d_tab + o; o += h->gz_int.size();
     g.gz_half = h->d_tab + o; o += h->gz_half.size();
     g.stab = h->d_tab + stab0;
+    g.stc_x = h->d_tab + stc_off[0];
+    g.stc_y = h->d_tab + stc_off[1];
+    g.stc_z = h->d_tab + stc_off[2];
+    g.fx0 = frange[0][0]; g.fx1 = frange[0][1];
+    g.fy0 = frange[1][0]; g.fy1 = frange[1][1];
+    g.fz0 = frange[2][0]; g.fz1 = frange[2][1];
     g.strips = h->d_strips;
     g.cmeta = reinterpret_cast<const int4*>(h->d_ints);
     g.r0 = h->d_ints + 8 * h->P;
@@ -427,7 +525,7 @@ void set_strip_io(const helm_dd* h, StripDev& s, int j) {
     s.olo[0] = h->beta[j] + 1;
     s.ohi[0] = h->beta[j + 1];
     s.olo[1] = j > 0 ? h->beta[j] + 2 : 0;
-    s.ohi[1] = h->beta[j + 1] + 1;
+    s.ohi[1] = j < h->J - 1 ? h->beta[j + 1] + 1 : (int)h->N[0] - 1;   // D~^(J) ends at the grid's edge
     s.xc[1] = s.lpml + (s.hi - s.lo);
     s.xc[0] = s.xc[1] - 1;
     s.xc[2] = s.lpml;
@@ -597,6 +695,12 @@ helm_status helm_dd_set_sep_groups(helm_dd* h, int G) {
 
 int helm_dd_sep_groups(const helm_dd* h) { return h && h->prepared ? h->G : 0; }
 
+helm_status helm_dd_set_panel(helm_dd* h, int nrhs) {
+    if (!h || nrhs < 0) return HELM_EINVAL;
+    h->panel = nrhs;
+    return HELM_OK;
+}
+
 helm_status helm_dd_set_stream(helm_dd* h, void* stream) {
     if (!h) return HELM_EINVAL;
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;   // null until first device use
@@ -645,6 +749,12 @@ helm_status helm_dd_factor(helm_dd* h) {
         fac += (int64_t)Ny * s.bs;
         red += (int64_t)std::max(h->P - 1, 1) * s.bs;
         xf += (int64_t)Ny * 16 * spld(s.W);
+        if (!strip_solve_fits(s, h->zrows, h->esize))
+            return fail(h, HELM_EINVAL, "strip " + std::to_string(j) + " (" + std::to_string(s.W) +
+                                            " columns) does not fit the strip solve's shared memory in " +
+                                            (h->esize == sizeof(float2) ? "complex64" : "complex128") +
+                                            " (complex128 strips hold at most about 50 columns): use more strips "
+                                            "or mixed precision");
     }
     for (auto& p : h->d_pool) { if (p) cudaFree(p); p = nullptr; }
     h->factored = false;
@@ -738,6 +848,38 @@ helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
     if ((s = ws_reserve(h, h->ws_parts, sz[3])) != HELM_OK) return s;
     PrecondBufs bf{(double2*)h->ws_V.p, (double2*)h->ws_G.p, h->ws_Y.p, h->ws_parts.p, h->d_counters};
     return run_precond(h, in, out, B, bf);
+}
+
+// The work buffers a call reserves grow but never shrink; when the free device memory
+// cannot hold `need` more bytes, drop them all so that the call's reservations start
+// from a clean slate (a workspace kept for a wider earlier call would otherwise hold
+// memory this call needs for others).
+void release_if_short(helm_dd* h, size_t need) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return; }
+    if (fr >= need) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_red}) ws_free(*w);
+}
+
+// Right-hand sides per internal panel of a solve or gradient: the handle's setting, or
+// as many as the free device memory holds.  Per right-hand side a panel needs the
+// FGMRES basis V_0..V_m, Z_0..Z_{m-1} and W (2m+2 fields), the preconditioner's
+// forward field and residual (2 fields), `extra` fields of the caller and the
+// strip chain solutions; the workspaces the handle already holds count as free.
+int panel_width(helm_dd* h, int nrhs, int m, int extra) {
+    if (h->panel > 0) return std::min(h->panel, nrhs);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return nrhs; }
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_grad}) fr += w->bytes;
+    size_t sz[kPrecondBufs];
+    precond_buf_bytes(h, 1, sz);
+    const size_t field = (size_t)nvol(h) * sizeof(double2);
+    const size_t per = (size_t)(2 * m + 2 + extra) * field + sz[0] + sz[1] + sz[2] + sz[3] + 4096;
+    const size_t fit = (size_t)(0.85 * (double)fr) / per;
+    const int Bp = (int)std::max<size_t>(1, std::min<size_t>((size_t)nrhs, fit));
+    release_if_short(h, (size_t)Bp * per);
+    return Bp;
 }
 
 // The double sweep itself on caller-provided buffers.
@@ -845,7 +987,7 @@ helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B
     auto solve = [&](int j, const SweepStep& sp, int slot) -> cudaError_t {
         SlabWork wk{rbuf, ybuf[slot], sp.prev >= 0 ? ybuf[slot ^ 1] : nullptr,
                     (const char*)h->d_slab_sxz + h->slab_sxz_off[j] * (int64_t)h->esize, h->ct_sz,
-                    h->slab_cy.data(), ld, B, (unsigned*)h->d_counters, h->d_status};
+                    h->slab_cy.data(), ld, B, (unsigned*)bf.counters, h->d_status};
         const StripDev* pst = sp.prev >= 0 ? &h->strips[sp.prev] : nullptr;
         if (mixed) return launch_slab_solve<float2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);
         return launch_slab_solve<double2>(h->geom, h->strips[j], pst, sp, wk, h->d_pool[0], h->stream, &h->timer);
@@ -955,24 +1097,42 @@ helm_status helm_dd_matvec(helm_dd* h, const double* in, double* out, int nrhs) 
 
 namespace {
 
-// Flexible GMRES(m), right preconditioned (Section 2.3, Eq. left_preconditioned;
-// Algorithm 5 in full space), batched over B columns with per-column masks.
-// Classical Gram-Schmidt with reorthogonalisation (CGS2) in FP64 on the device;
-// Hessenberg, Givens rotations and the small triangular solve on the host.
-helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double tol, int m, int maxit,
-                       std::vector<int>& iters, std::vector<double>& relres) {
-    const int64_t NV = nvol(h);
+// The operator a GMRES run works on, over vectors of n entries per right-hand side:
+// residual(x, f, out, B) writes out = f - M x (out = M x when f is null); precond(v, z, B)
+// writes z = P v, or is empty for plain GMRES (no preconditioner inside the operator's
+// Krylov loop, x += V y).
+struct KrylovOp {
+    int64_t n = 0;
+    std::function<helm_status(const double2*, const double2*, double2*, int)> residual;
+    std::function<helm_status(const double2*, double2*, int)> precond;
+    // stop on the Givens estimate without forming the final residual (the caller checks
+    // the true residual itself); for operators whose every application is expensive
+    bool trust_estimate = false;
+};
+
+// GMRES(m) on op (Section 2.3; Algorithm 5), batched over B columns with per-column
+// masks; with a preconditioner it is right-preconditioned flexible GMRES (Z_i = P V_i
+// stored, x += Z y), which admits the complex64 preconditioner.  Classical Gram-Schmidt
+// with reorthogonalisation (CGS2) in FP64 on the device; Hessenberg, Givens rotations and
+// the small triangular solve on the host.
+helm_status dev_gmres(helm_dd* h, const KrylovOp& op, const double2* F, double2* U, int B, double tol, int m,
+                      int maxit, std::vector<int>& iters, std::vector<double>& relres,
+                      const std::vector<double>* tol_per = nullptr) {
+    const int64_t NV = op.n;
+    // relative tolerance of column b (one for all, or one per column)
+    auto tolb = [&](int b) { return tol_per ? (*tol_per)[b] : tol; };
     const size_t vb = (size_t)B * NV * sizeof(double2);
+    const bool flex = (bool)op.precond;
     helm_status s;
-    // Krylov storage: V_0..V_m, Z_0..Z_{m-1}, W
-    if ((s = ws_reserve(h, h->ws_kry, (size_t)(2 * m + 2) * vb)) != HELM_OK) return s;
+    // Krylov storage: V_0..V_m, Z_0..Z_{m-1} (flexible only), W
+    if ((s = ws_reserve(h, h->ws_kry, (size_t)(flex ? 2 * m + 2 : m + 2) * vb)) != HELM_OK) return s;
     const int nblk = 304;
     const size_t small = (size_t)B * (m + 2) * nblk * sizeof(double2) + (size_t)4 * B * (m + 2) * sizeof(double2);
     if ((s = ws_reserve(h, h->ws_small, small)) != HELM_OK) return s;
     double2* V = (double2*)h->ws_kry.p;
     const int64_t vs = (int64_t)B * NV;   // stride between Krylov vectors (elements)
-    double2* Z = V + (int64_t)(m + 1) * vs;
-    double2* Wv = Z + (int64_t)m * vs;
+    double2* Z = flex ? V + (int64_t)(m + 1) * vs : V;
+    double2* Wv = flex ? Z + (int64_t)m * vs : V + (int64_t)(m + 1) * vs;
     double2* partial = (double2*)h->ws_small.p;
     double2* dres = partial + (size_t)B * (m + 2) * nblk;
     double2* dcoef = dres + (size_t)B * (m + 2);
@@ -1002,16 +1162,20 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
     std::vector<int> kend(B);
     std::vector<char> active(B);
     std::vector<double> beta;
+    std::vector<double> last_est(B, 0.0);
     int guard = 0;
+    bool first = true;
     while (true) {
-        // r = f - A x into V_0
-        if ((s = dev_stencil(h, U, F, V, B)) != HELM_OK) return s;
+        // r = f - M x into V_0 (r = f for the first cycle, where x = 0)
+        if (first) CK(h, cudaMemcpyAsync(V, F, vb, cudaMemcpyDeviceToDevice, h->stream));
+        else if ((s = op.residual(U, F, V, B)) != HELM_OK) return s;
+        first = false;
         if ((s = norms(V, beta)) != HELM_OK) return s;
         bool any = false;
         for (int b = 0; b < B; ++b) {
             if (!isfinite(beta[b])) return fail(h, HELM_ENUMERIC, "non-finite residual norm");
             relres[b] = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
-            if (bnorm[b] == 0.0 || beta[b] <= tol * bnorm[b]) conv[b] = 1;
+            if (bnorm[b] == 0.0 || beta[b] <= tolb(b) * bnorm[b]) conv[b] = 1;
             active[b] = !conv[b] && iters[b] < maxit;
             any = any || active[b];
             hscale[b] = active[b] ? 1.0 / beta[b] : 0.0;
@@ -1025,8 +1189,8 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
         for (int i = 0; i < m; ++i) {
             double2* Vi = V + (int64_t)i * vs;
             double2* Zi = Z + (int64_t)i * vs;
-            if ((s = dev_precond(h, Vi, Zi, B)) != HELM_OK) return s;
-            if ((s = dev_stencil(h, Zi, nullptr, Wv, B)) != HELM_OK) return s;
+            if (flex && (s = op.precond(Vi, Zi, B)) != HELM_OK) return s;
+            if ((s = op.residual(Zi, nullptr, Wv, B)) != HELM_OK) return s;
             // CGS2
             std::vector<cd> hcol((size_t)B * (i + 1), 0.0);
             for (int pass = 0; pass < 2; ++pass) {
@@ -1081,7 +1245,8 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
                 iters[b] += 1;
                 kend[b] = i + 1;
                 const double est = std::abs(gb[i + 1]);
-                if (est <= tol * bnorm[b] || iters[b] >= maxit || hn[b] == 0.0) active[b] = 0;
+                last_est[b] = est;
+                if (est <= tolb(b) * bnorm[b] || iters[b] >= maxit || hn[b] == 0.0) active[b] = 0;
                 hscale[b] = (active[b] && hn[b] > 0) ? 1.0 / hn[b] : 0.0;
                 still = still || active[b];
             }
@@ -1111,17 +1276,305 @@ helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double t
                                   h->stream));
             CK(h, launch_multi_axpy(U, Z, vs, dcoef, kmax, B, NV, h->stream, &h->timer));
         }
+        if (op.trust_estimate) {   // done when every column met its tolerance or maxit by the estimate
+            bool done = true;
+            for (int b = 0; b < B; ++b) {
+                if (conv[b]) continue;
+                if (kend[b] > 0) relres[b] = bnorm[b] > 0 ? last_est[b] / bnorm[b] : 0.0;
+                if (!(relres[b] <= tolb(b)) && iters[b] < maxit) done = false;
+            }
+            if (done) {
+                bool allconv = true;
+                for (int b = 0; b < B; ++b) allconv = allconv && relres[b] <= tolb(b);
+                return allconv ? HELM_OK : fail(h, HELM_ENOTCONV, "GMRES reached maxit before the tolerance");
+            }
+        }
     }
     // final true residual
-    if ((s = dev_stencil(h, U, F, Wv, B)) != HELM_OK) return s;
+    if ((s = op.residual(U, F, Wv, B)) != HELM_OK) return s;
     std::vector<double> rn;
     if ((s = norms(Wv, rn)) != HELM_OK) return s;
     bool allconv = true;
     for (int b = 0; b < B; ++b) {
         relres[b] = bnorm[b] > 0 ? rn[b] / bnorm[b] : 0.0;
-        if (!(relres[b] <= tol)) allconv = false;
+        if (!(relres[b] <= tolb(b))) allconv = false;
     }
     return allconv ? HELM_OK : fail(h, HELM_ENOTCONV, "GMRES reached maxit before the tolerance");
+}
+
+// Flexible GMRES in the full space (Algorithm 5 in its full-space form): A P v = f,
+// u = P v, over all padded unknowns.
+helm_status dev_fgmres(helm_dd* h, const double2* F, double2* U, int B, double tol, int m, int maxit,
+                       std::vector<int>& iters, std::vector<double>& relres) {
+    KrylovOp op;
+    op.n = nvol(h);
+    op.residual = [h](const double2* x, const double2* f, double2* out, int nb) {
+        return dev_stencil(h, x, f, out, nb);
+    };
+    op.precond = [h](const double2* v, double2* z, int nb) { return dev_precond(h, v, z, nb); };
+    return dev_gmres(h, op, F, U, B, tol, m, maxit, iters, relres);
+}
+
+
+// ------------------------------------------------------------------ reduced space
+// Section 2.3 ("Algorithm"), Algorithms 2-5: GMRES restricted to the 2(J-1) interface
+// lines beta_j+1, beta_j+2 (j = 1..J-1).  A reduced vector holds B fields of N_z N_y rows
+// of L = 2(J-1) values: entry (b, z, y, i) is column icols[i] of row (z, y) of field b.
+
+int64_t nred(const helm_dd* h) { return h->N[2] * h->N[1] * (int64_t)h->icols.size(); }
+
+// Algorithm 2, the strip solves (Eq. reduce_compute_ut): u~^(j) from f restricted to
+// D~^(j) = beta_{j-1}+2 .. beta_j+1 (0 .. for the first strip, .. N_x-1 for the last) with
+// no transfer; u~ = u~^(j) on D~^(j), written to Ut.  The solves are independent.
+helm_status run_local_solves(helm_dd* h, const double2* F, double2* Ut, int B, const PrecondBufs& bf) {
+    const int J = h->J, Nx = (int)h->N[0], Ny = (int)h->N[1];
+    const auto& beta = h->beta;
+    const bool mixed = h->prec == HELM_PREC_MIXED;
+    auto step_of = [&](int j) {
+        SweepStep sp{};
+        sp.src = F;
+        sp.mlo = j > 0 ? beta[j] + 2 : 0;
+        sp.mhi = j < J - 1 ? beta[j + 1] + 1 : Nx - 1;
+        sp.prev = -1;
+        sp.pdir = 0;
+        sp.t0 = 0;
+        sp.tcoef = 0.0;
+        return sp;
+    };
+    if (h->dim == 3) {
+        const int ld = h->slab_ld;
+        const size_t vb = (size_t)B * Ny * ld * h->esize;
+        char* rbuf = (char*)bf.Y;
+        char* ybuf = rbuf + vb;
+        for (int j = 0; j < J; ++j) {
+            const SweepStep sp = step_of(j);
+            SlabWork wk{rbuf, ybuf, nullptr, (const char*)h->d_slab_sxz + h->slab_sxz_off[j] * (int64_t)h->esize,
+                        h->ct_sz, h->slab_cy.data(), ld, B, (unsigned*)bf.counters, h->d_status};
+            cudaError_t e = mixed ? launch_slab_solve<float2>(h->geom, h->strips[j], nullptr, sp, wk, h->d_pool[0],
+                                                              h->stream, &h->timer)
+                                  : launch_slab_solve<double2>(h->geom, h->strips[j], nullptr, sp, wk, h->d_pool[0],
+                                                               h->stream, &h->timer);
+            if (e == cudaSuccess)
+                e = mixed ? launch_slab_out<float2>(h->geom, h->strips[j], 1, ybuf, ld, Ut, nullptr, B, h->stream,
+                                                    &h->timer)
+                          : launch_slab_out<double2>(h->geom, h->strips[j], 1, ybuf, ld, Ut, nullptr, B, h->stream,
+                                                     &h->timer);
+            if (e != cudaSuccess) return fail_cuda(h, "local strip solves", e);
+        }
+        return HELM_OK;
+    }
+    const int ws = work_stride(h);
+    const int64_t ystride = (int64_t)B * Ny * ws;
+    auto ybuf = [&](int j) { return (char*)bf.Y + j * ystride * (int64_t)h->esize; };
+    const int kOutBatch = 8;
+    for (int j = 0; j < J; ++j) {
+        const SweepStep sp = step_of(j);
+        SweepWork wk{ybuf(j), bf.parts, bf.counters, h->d_status, ws, B, h->zrows, nullptr};
+        cudaError_t e = mixed ? launch_strip_solve<float2>(h->geom, j, h->strips[j], nullptr, sp, wk, h->d_pool,
+                                                           h->stream, &h->timer)
+                              : launch_strip_solve<double2>(h->geom, j, h->strips[j], nullptr, sp, wk, h->d_pool,
+                                                            h->stream, &h->timer);
+        if (e != cudaSuccess) return fail_cuda(h, "local strip solves", e);
+        if ((j + 1) % kOutBatch == 0 || j == J - 1) {
+            const int n = (j % kOutBatch) + 1;
+            OutArgs O{h->geom, 1, j + 1 - n, n, bf.Y, ystride, ws, B, B > 1 ? 4 : 1, Ut, nullptr,
+                      j == J - 1 ? 0 : 56};
+            CK(h, cudaEventRecord(h->ev_main, h->stream));
+            CK(h, cudaStreamWaitEvent(h->side, h->ev_main, 0));
+            e = mixed ? launch_outputs<float2>(O, h->d_pool, h->side, &h->timer)
+                      : launch_outputs<double2>(O, h->d_pool, h->side, &h->timer);
+            if (e != cudaSuccess) return fail_cuda(h, "local strip outputs", e);
+        }
+    }
+    CK(h, cudaEventRecord(h->ev_side, h->side));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_side, 0));
+    return HELM_OK;
+}
+
+// Work buffers of the reduced-space routines for B fields: X (a reduced vector extended
+// by zero to the grid), Zf (P X), Ut (u~), Rr (the FP64 residual of the outer passes),
+// phi and xi (reduced); full fields first, each 256-byte aligned.
+struct RedBufs {
+    double2 *X, *Zf, *Ut, *Rr, *phi, *xi;
+};
+helm_status red_reserve(helm_dd* h, int B, RedBufs& rb) {
+    const size_t full = (size_t)B * nvol(h) * sizeof(double2), red = (size_t)B * std::max<int64_t>(nred(h), 1) * 16;
+    const size_t fa = align256(full), ra = align256(red);
+    helm_status s = ws_reserve(h, h->ws_red, 4 * fa + 2 * ra);
+    if (s != HELM_OK) return s;
+    char* p = (char*)h->ws_red.p;
+    rb.X = (double2*)p;
+    rb.Zf = (double2*)(p + fa);
+    rb.Ut = (double2*)(p + 2 * fa);
+    rb.Rr = (double2*)(p + 3 * fa);
+    rb.phi = (double2*)(p + 4 * fa);
+    rb.xi = (double2*)(p + 4 * fa + ra);
+    // X is zero off the interface lines from here on; only its interface columns are written
+    CK(h, cudaMemsetAsync(rb.X, 0, full, h->stream));
+    return HELM_OK;
+}
+
+// Algorithm 2: Ut = u~ and phi = (F - A u~) on the interface lines.
+helm_status dev_reduce(helm_dd* h, const double2* F, double2* phi, double2* Ut, int B) {
+    size_t sz[kPrecondBufs];
+    precond_buf_bytes(h, B, sz);
+    helm_status s;
+    if ((s = ws_reserve(h, h->ws_Y, sz[2])) != HELM_OK) return s;
+    if ((s = ws_reserve(h, h->ws_parts, sz[3])) != HELM_OK) return s;
+    PrecondBufs bf{nullptr, nullptr, h->ws_Y.p, h->ws_parts.p, h->d_counters};
+    if ((s = run_local_solves(h, F, Ut, B, bf)) != HELM_OK) return s;
+    CK(h, launch_stencil_cols(h->geom, Ut, F, nullptr, phi, h->d_icols, (int)h->icols.size(), B, h->stream,
+                              &h->timer));
+    return HELM_OK;
+}
+
+// Algorithm 3 on reduced vectors: out = f - R A P E x (out = R A P E x when f is null),
+// with E the extension by zero to the grid and R the restriction to the interface lines.
+KrylovOp reduced_op(helm_dd* h, const RedBufs& rb) {
+    KrylovOp op;
+    op.n = nred(h);
+    op.trust_estimate = true;   // dev_solve_reduced forms the true FP64 residual on the whole grid
+    const int L = (int)h->icols.size();
+    op.residual = [h, rb, L](const double2* x, const double2* f, double2* out, int nb) -> helm_status {
+        const int64_t rows = (int64_t)nb * h->N[2] * h->N[1];
+        CK(h, launch_scatter_cols(x, rb.X, h->d_icols, L, rows, (int)h->N[0], h->stream, &h->timer));
+        helm_status s = dev_precond(h, rb.X, rb.Zf, nb);
+        if (s != HELM_OK) return s;
+        CK(h, launch_stencil_cols(h->geom, rb.Zf, nullptr, f, out, h->d_icols, L, nb, h->stream, &h->timer));
+        return HELM_OK;
+    };
+    return op;
+}
+
+// Full-grid norms of B fields (FP64).
+helm_status field_norms(helm_dd* h, const double2* X, int B, int64_t n, std::vector<double>& nrm) {
+    helm_status s;
+    const int nblk = 304;
+    const size_t need = (size_t)B * nblk * sizeof(double2) + (size_t)B * sizeof(double2);
+    if ((s = ws_reserve(h, h->ws_small, std::max(need, h->ws_small.bytes))) != HELM_OK) return s;
+    double2* partial = (double2*)h->ws_small.p;
+    double2* dres = partial + (size_t)B * nblk;
+    CK(h, launch_multidot(X, 0, X, 1, B, n, partial, nblk, dres, h->stream, &h->timer));
+    std::vector<double2> hr(B);
+    CK(h, cudaMemcpyAsync(hr.data(), dres, B * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    nrm.resize(B);
+    for (int b = 0; b < B; ++b) nrm[b] = sqrt(std::max(hr[b].x, 0.0));
+    return HELM_OK;
+}
+
+// Algorithm 5 in the reduced space for B fields: phi from Algorithm 2, GMRES on
+// R A P E xi = phi (Eq. solve_A_reduced, psi = P E xi), u = P E xi + u~ (Algorithm 4).
+// Each pass stops GMRES when the reduced residual would bring ||f - A u|| to tol ||f||
+// (in mixed precision at 1e-3 of the pass's right-hand side at the tightest); the true
+// FP64 residual is then formed on the whole grid and, where it is still above tol ||f||
+// (complex64 strip solves leave residuals off the interface lines, which the reduced
+// space does not see), the pass is repeated on it (defect correction).
+helm_status dev_solve_reduced(helm_dd* h, const double2* F, double2* U, int B, double tol, int m, int maxit,
+                              std::vector<int>& iters, std::vector<double>& relres) {
+    const int64_t NV = nvol(h);
+    RedBufs rb;
+    helm_status s;
+    if ((s = red_reserve(h, B, rb)) != HELM_OK) return s;
+    iters.assign(B, 0);
+    relres.assign(B, 0.0);
+    std::vector<double> fn, pn, rn;
+    if ((s = field_norms(h, F, B, NV, fn)) != HELM_OK) return s;
+    for (int b = 0; b < B; ++b)
+        if (!std::isfinite(fn[b])) return fail(h, HELM_ENUMERIC, "non-finite right-hand side");
+    CK(h, cudaMemsetAsync(U, 0, (size_t)B * NV * sizeof(double2), h->stream));
+    const KrylovOp op = reduced_op(h, rb);
+    const double2* Rf = F;
+    const int kMaxPass = 8;
+    bool conv = false;
+    for (int pass = 0; pass < kMaxPass && !conv; ++pass) {
+        if ((s = dev_reduce(h, Rf, rb.phi, rb.Ut, B)) != HELM_OK) return s;
+        if (op.n > 0) {
+            if ((s = field_norms(h, rb.phi, B, op.n, pn)) != HELM_OK) return s;
+            // complex64 strip solves make the reduced operator linear only up to their
+            // rounding, below which GMRES stalls: in mixed precision every pass stops at
+            // 1e-3 of its right-hand side and the FP64 passes gain the remaining digits
+            const double floor_tol = h->prec == HELM_PREC_MIXED ? 1e-3 : 1e-14;
+            std::vector<double> tv(B);
+            for (int b = 0; b < B; ++b) {
+                const double target = (pass == 0 ? 1.0 : 0.5) * tol * fn[b];
+                tv[b] = pn[b] > 0 ? std::min(0.5, std::max(target / pn[b], floor_tol)) : 1.0;
+            }
+            std::vector<int> it;
+            std::vector<double> rr;
+            const int left = std::max(1, maxit - *std::max_element(iters.begin(), iters.end()));
+            s = dev_gmres(h, op, rb.phi, rb.xi, B, tol, m, left, it, rr, &tv);
+            if (s != HELM_OK && s != HELM_ENOTCONV) return s;
+            for (int b = 0; b < B; ++b) iters[b] += it[b];
+            // Algorithm 4: u += P E xi + u~
+            CK(h, launch_scatter_cols(rb.xi, rb.X, h->d_icols, (int)h->icols.size(), (int64_t)B * h->N[2] * h->N[1],
+                                      (int)h->N[0], h->stream, &h->timer));
+            if ((s = dev_precond(h, rb.X, rb.Zf, B)) != HELM_OK) return s;
+            CK(h, launch_add(U, rb.Zf, (int64_t)B * NV, h->stream, &h->timer));
+        }
+        CK(h, launch_add(U, rb.Ut, (int64_t)B * NV, h->stream, &h->timer));
+        // the true residual f - A u on the whole grid (FP64)
+        if ((s = dev_stencil(h, U, F, rb.Rr, B)) != HELM_OK) return s;
+        if ((s = field_norms(h, rb.Rr, B, NV, rn)) != HELM_OK) return s;
+        conv = true;
+        for (int b = 0; b < B; ++b) {
+            if (!std::isfinite(rn[b])) return fail(h, HELM_ENUMERIC, "non-finite residual norm");
+            relres[b] = fn[b] > 0 ? rn[b] / fn[b] : 0.0;
+            if (!(relres[b] <= tol)) conv = false;
+        }
+        if (*std::max_element(iters.begin(), iters.end()) >= maxit) break;
+        Rf = rb.Rr;
+    }
+    return conv ? HELM_OK : fail(h, HELM_ENOTCONV, "reduced-space GMRES did not reach the tolerance");
+}
+
+// Device view of a caller's input array (host arrays are copied into ws).
+helm_status stage_in(helm_dd* h, const double* p, size_t bytes, helm_dd::Ws& ws, const double2** out) {
+    if (is_device_ptr(p)) {
+        if (misaligned16(p)) return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
+        *out = (const double2*)p;
+        return HELM_OK;
+    }
+    helm_status s = ws_reserve(h, ws, bytes);
+    if (s != HELM_OK) return s;
+    CK(h, cudaMemcpyAsync(ws.p, p, bytes, cudaMemcpyHostToDevice, h->stream));
+    *out = (const double2*)ws.p;
+    return HELM_OK;
+}
+// Device buffer for a caller's output array: the array itself when it is on the device,
+// else ws (copied back by unstage_out).
+helm_status stage_out(helm_dd* h, double* p, size_t bytes, helm_dd::Ws& ws, double2** out) {
+    if (is_device_ptr(p)) {
+        if (misaligned16(p)) return fail(h, HELM_EINVAL, "device fields must be 16-byte aligned (complex128)");
+        *out = (double2*)p;
+        return HELM_OK;
+    }
+    helm_status s = ws_reserve(h, ws, bytes);
+    if (s != HELM_OK) return s;
+    *out = (double2*)ws.p;
+    return HELM_OK;
+}
+helm_status unstage_out(helm_dd* h, double* p, const double2* dev, size_t bytes) {
+    if ((const void*)p != (const void*)dev)
+        CK(h, cudaMemcpyAsync(p, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
+    return HELM_OK;
+}
+
+// Right-hand sides per panel of the reduced solve: per right-hand side four full fields
+// of its own, the preconditioner's two, the strip chain solutions, and m+4 reduced vectors.
+int panel_width_reduced(helm_dd* h, int nrhs, int m) {
+    if (h->panel > 0) return std::min(h->panel, nrhs);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return nrhs; }
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_red}) fr += w->bytes;
+    size_t sz[kPrecondBufs];
+    precond_buf_bytes(h, 1, sz);
+    const size_t field = (size_t)nvol(h) * sizeof(double2);
+    const size_t per = 4 * field + sz[0] + sz[1] + sz[2] + sz[3] + (size_t)(m + 4) * nred(h) * 16 + 4096;
+    const size_t fit = (size_t)(0.85 * (double)fr) / per;
+    const int Bp = (int)std::max<size_t>(1, std::min<size_t>((size_t)nrhs, fit));
+    release_if_short(h, (size_t)Bp * per);
+    return Bp;
 }
 
 }  // namespace
@@ -1149,10 +1602,18 @@ helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs, do
         if ((s = ws_reserve(h, h->ws_io_out, bytes)) != HELM_OK) return s;
         U = (double2*)h->ws_io_out.p;
     }
-    std::vector<int> iters;
-    std::vector<double> relres;
-    helm_status st = dev_fgmres(h, F, U, nrhs, tol, restart, maxit, iters, relres);
-    if (st != HELM_OK && st != HELM_ENOTCONV) return st;
+    std::vector<int> iters(nrhs), it_p;
+    std::vector<double> relres(nrhs), rr_p;
+    helm_status st = HELM_OK;
+    const int Bp = panel_width(h, nrhs, restart, din ? 0 : 2);
+    const int64_t NV = nvol(h);
+    for (int b0 = 0; b0 < nrhs; b0 += Bp) {   // right-hand sides in panels of Bp
+        const int nb = std::min(Bp, nrhs - b0);
+        helm_status sp = dev_fgmres(h, F + (int64_t)b0 * NV, U + (int64_t)b0 * NV, nb, tol, restart, maxit, it_p, rr_p);
+        if (sp != HELM_OK && sp != HELM_ENOTCONV) return sp;
+        if (sp == HELM_ENOTCONV) st = sp;
+        for (int b = 0; b < nb; ++b) { iters[b0 + b] = it_p[b]; relres[b0 + b] = rr_p[b]; }
+    }
     helm_status ds = check_device_status(h);
     if (ds != HELM_OK) return ds;
     if (!dout) CK(h, cudaMemcpyAsync(u, U, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -1163,26 +1624,114 @@ helm_status helm_dd_solve(helm_dd* h, const double* rhs, double* u, int nrhs, do
     return st;
 }
 
+int helm_dd_interface_lines(const helm_dd* h, int* cols, int cap) {
+    if (!h) return 0;
+    for (int i = 0; i < (int)h->icols.size() && i < cap && cols; ++i) cols[i] = h->icols[i];
+    return (int)h->icols.size();
+}
+
+helm_status helm_dd_reduce_rhs(helm_dd* h, const double* f, double* phi, double* ut, int nrhs) {
+    if (!h || !f || nrhs < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "reduce_rhs before factor");
+    const int64_t NR = nred(h);
+    if (NR > 0 && !phi) return HELM_EINVAL;
+    const size_t fb = (size_t)nrhs * nvol(h) * sizeof(double2), rbytes = (size_t)nrhs * NR * sizeof(double2);
+    helm_status s;
+    const double2* F;
+    double2* Phi = nullptr;
+    if ((s = stage_in(h, f, fb, h->ws_io_in, &F)) != HELM_OK) return s;
+    if (NR > 0 && (s = stage_out(h, phi, rbytes, h->ws_io_out, &Phi)) != HELM_OK) return s;
+    RedBufs rb;
+    if ((s = red_reserve(h, nrhs, rb)) != HELM_OK) return s;
+    if ((s = dev_reduce(h, F, Phi, rb.Ut, nrhs)) != HELM_OK) return s;
+    if ((s = check_device_status(h)) != HELM_OK) return s;
+    if (NR > 0 && (s = unstage_out(h, phi, Phi, rbytes)) != HELM_OK) return s;
+    if (ut) CK(h, cudaMemcpyAsync(ut, rb.Ut, fb, is_device_ptr(ut) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return HELM_OK;
+}
+
+helm_status helm_dd_apply_AP_reduced(helm_dd* h, const double* in, double* out, int nrhs) {
+    if (!h || !in || !out || nrhs < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "apply_AP_reduced before factor");
+    const int64_t NR = nred(h);
+    if (NR == 0) return HELM_OK;
+    const size_t rbytes = (size_t)nrhs * NR * sizeof(double2);
+    helm_status s;
+    const double2* X;
+    double2* Y;
+    if ((s = stage_in(h, in, rbytes, h->ws_io_in, &X)) != HELM_OK) return s;
+    if ((s = stage_out(h, out, rbytes, h->ws_io_out, &Y)) != HELM_OK) return s;
+    if ((const void*)X == (const void*)Y) return fail(h, HELM_EINVAL, "apply_AP_reduced needs distinct buffers");
+    RedBufs rb;
+    if ((s = red_reserve(h, nrhs, rb)) != HELM_OK) return s;
+    const KrylovOp op = reduced_op(h, rb);
+    if ((s = op.residual(X, nullptr, Y, nrhs)) != HELM_OK) return s;
+    if ((s = check_device_status(h)) != HELM_OK) return s;
+    if ((s = unstage_out(h, out, Y, rbytes)) != HELM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return HELM_OK;
+}
+
+helm_status helm_dd_solve_reduced(helm_dd* h, const double* rhs, double* u, int nrhs, double tol, int restart,
+                                  int maxit, helm_rhs_info* info) {
+    if (!h || !rhs || !u || nrhs < 1 || !(tol > 0) || restart < 1 || maxit < 1) return HELM_EINVAL;
+    if (!h->factored) return fail(h, HELM_ESTATE, "solve_reduced before factor");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t NV = nvol(h);
+    const size_t bytes = (size_t)nrhs * NV * sizeof(double2);
+    helm_status s;
+    const double2* F;
+    double2* U;
+    if ((s = stage_in(h, rhs, bytes, h->ws_io_in, &F)) != HELM_OK) return s;
+    if ((s = stage_out(h, u, bytes, h->ws_io_out, &U)) != HELM_OK) return s;
+    std::vector<int> iters(nrhs), it_p;
+    std::vector<double> relres(nrhs), rr_p;
+    helm_status st = HELM_OK;
+    const int Bp = panel_width_reduced(h, nrhs, restart);
+    for (int b0 = 0; b0 < nrhs; b0 += Bp) {   // right-hand sides in panels of Bp
+        const int nb = std::min(Bp, nrhs - b0);
+        helm_status sp = dev_solve_reduced(h, F + (int64_t)b0 * NV, U + (int64_t)b0 * NV, nb, tol, restart, maxit,
+                                           it_p, rr_p);
+        if (sp != HELM_OK && sp != HELM_ENOTCONV) return sp;
+        if (sp == HELM_ENOTCONV) st = sp;
+        for (int b = 0; b < nb; ++b) { iters[b0 + b] = it_p[b]; relres[b0 + b] = rr_p[b]; }
+    }
+    helm_status ds = check_device_status(h);
+    if (ds != HELM_OK) return ds;
+    if ((s = unstage_out(h, u, U, bytes)) != HELM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int b = 0; b < nrhs; ++b) info[b] = helm_rhs_info{iters[b], relres[b], ms};
+    return st;
+}
+
 helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc, const int64_t* rec_idx, int nrec,
                              const double* d, double tol, double* misfit, double* grad_m) {
-    if (!h || !src_idx || !rec_idx || !d || !misfit || !grad_m || nsrc < 1 || nrec < 1) return HELM_EINVAL;
+    if (!h || !src_idx || !rec_idx || !d || !misfit || nsrc < 1 || nrec < 1) return HELM_EINVAL;
     if (!h->factored) return fail(h, HELM_ESTATE, "gradient before factor");
     const int64_t NV = nvol(h);
     for (int i = 0; i < nsrc; ++i)
         if (src_idx[i] < 0 || src_idx[i] >= NV) return fail(h, HELM_EINVAL, "source index out of range");
     for (int i = 0; i < nrec; ++i)
         if (rec_idx[i] < 0 || rec_idx[i] >= NV) return fail(h, HELM_EINVAL, "receiver index out of range");
-    const size_t vb = (size_t)nsrc * NV * sizeof(double2);
+    const bool want_grad = grad_m != nullptr;
+    const int Bp = panel_width(h, nsrc, 20, want_grad ? 3 : 2);
+    const size_t vb = (size_t)Bp * NV * sizeof(double2);
     helm_status s;
-    // ws_grad holds F/Q, U, MU, gpad, gint, receivers, gathered values, each starting on a
-    // 256-byte boundary (the complex128 arrays need 16-byte alignment whatever the counts)
+    // ws_grad holds F/Q, U, MU (one panel each), gpad, gint, the receiver and scatter
+    // index / value arrays and the gathered values, each on a 256-byte boundary (the
+    // complex128 arrays need 16-byte alignment whatever the counts)
     const int64_t nint = h->n[0] * h->n[1] * h->n[2];
-    const size_t part[7] = {vb, vb, vb, (size_t)NV * sizeof(double), (size_t)nint * sizeof(double),
-                            (size_t)nrec * sizeof(int64_t), (size_t)nsrc * nrec * sizeof(double2)};
-    size_t off[8];
+    const size_t part[9] = {vb, vb, want_grad ? vb : 0, (size_t)NV * sizeof(double), (size_t)nint * sizeof(double),
+                            (size_t)nrec * sizeof(int64_t), (size_t)Bp * nrec * sizeof(int64_t),
+                            (size_t)Bp * nrec * sizeof(double2), (size_t)Bp * nrec * sizeof(double2)};
+    size_t off[10];
     off[0] = 0;
-    for (int i = 0; i < 7; ++i) off[i + 1] = off[i] + ((part[i] + 255) & ~(size_t)255);
-    if ((s = ws_reserve(h, h->ws_grad, off[7])) != HELM_OK) return s;
+    for (int i = 0; i < 9; ++i) off[i + 1] = off[i] + ((part[i] + 255) & ~(size_t)255);
+    if ((s = ws_reserve(h, h->ws_grad, off[9])) != HELM_OK) return s;
     char* wb = (char*)h->ws_grad.p;
     double2* FQ = (double2*)(wb + off[0]);
     double2* U = (double2*)(wb + off[1]);
@@ -1190,63 +1739,79 @@ helm_status helm_dd_gradient(helm_dd* h, const int64_t* src_idx, int nsrc, const
     double* gpad = (double*)(wb + off[3]);
     double* gint = (double*)(wb + off[4]);
     int64_t* drec = (int64_t*)(wb + off[5]);
-    double2* gath = (double2*)(wb + off[6]);
-    // sources: discrete deltas 1/h^dim
-    const double amp = 1.0 / pow(h->h, h->dim);
-    CK(h, cudaMemsetAsync(FQ, 0, vb, h->stream));
-    const double2 a2 = make_double2(amp, 0.0);
-    for (int i = 0; i < nsrc; ++i)
-        CK(h, cudaMemcpyAsync(FQ + (size_t)i * NV + src_idx[i], &a2, sizeof(double2), cudaMemcpyHostToDevice,
-                              h->stream));
+    int64_t* dsi = (int64_t*)(wb + off[6]);
+    double2* dsv = (double2*)(wb + off[7]);
+    double2* gath = (double2*)(wb + off[8]);
+    std::vector<double2> dd((size_t)nsrc * nrec);
+    if (is_device_ptr(d)) CK(h, cudaMemcpy(dd.data(), d, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    else memcpy(dd.data(), d, dd.size() * sizeof(double2));
+    CK(h, cudaMemcpyAsync(drec, rec_idx, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    if (want_grad) CK(h, cudaMemsetAsync(gpad, 0, (size_t)NV * sizeof(double), h->stream));
+    const double amp = 1.0 / pow(h->h, h->dim);   // sources: discrete deltas 1/h^dim
+    const int Nx = (int)h->N[0], Ny = (int)h->N[1];
+    std::vector<int64_t> si((size_t)Bp * nrec);
+    std::vector<double2> sv((size_t)Bp * nrec), ur((size_t)Bp * nrec);
     std::vector<int> iters;
     std::vector<double> relres;
-    helm_status st = dev_fgmres(h, FQ, U, nsrc, tol, 20, 400, iters, relres);
-    if (st != HELM_OK) return st;
-    // residual at receivers and the misfit
-    CK(h, cudaMemcpyAsync(drec, rec_idx, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_gather(U, NV, drec, nrec, nsrc, gath, h->stream));
-    std::vector<double2> ur((size_t)nsrc * nrec);
-    CK(h, cudaMemcpyAsync(ur.data(), gath, ur.size() * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    std::vector<double2> dd((size_t)nsrc * nrec);
-    const bool ddev = is_device_ptr(d);
-    if (ddev) CK(h, cudaMemcpy(dd.data(), d, dd.size() * sizeof(double2), cudaMemcpyDeviceToHost));
-    else memcpy(dd.data(), d, dd.size() * sizeof(double2));
     double J = 0.0;
-    // adjoint right-hand side q = S^-1 conj(R^T r), accumulated per index on the host
-    CK(h, cudaMemsetAsync(FQ, 0, vb, h->stream));
-    const int Nx = (int)h->N[0], Ny = (int)h->N[1];
-    for (int sidx = 0; sidx < nsrc; ++sidx) {
-        std::vector<std::pair<int64_t, cd>> acc;
-        for (int r = 0; r < nrec; ++r) {
-            const double2 u0 = ur[(size_t)sidx * nrec + r], d0 = dd[(size_t)sidx * nrec + r];
-            const cd res(u0.x - d0.x, u0.y - d0.y);
-            J += 0.5 * std::norm(res);
-            bool found = false;
-            for (auto& pr : acc)
-                if (pr.first == rec_idx[r]) { pr.second += res; found = true; }
-            if (!found) acc.push_back({rec_idx[r], res});
+    // Sources in panels of Bp (as many as the free device memory holds): the forward
+    // fields of one panel exist only until that panel's adjoint solves are done.
+    for (int s0 = 0; s0 < nsrc; s0 += Bp) {
+        const int nb = std::min(Bp, nsrc - s0);
+        CK(h, cudaMemsetAsync(FQ, 0, (size_t)nb * NV * sizeof(double2), h->stream));
+        for (int b = 0; b < nb; ++b) { si[b] = src_idx[s0 + b]; sv[b] = make_double2(amp, 0.0); }
+        CK(h, cudaMemcpyAsync(dsi, si.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(dsv, sv.data(), nb * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+        CK(h, launch_scatter(FQ, NV, dsi, dsv, 1, nb, h->stream));
+        helm_status st = dev_fgmres(h, FQ, U, nb, tol, 20, 400, iters, relres);
+        if (st != HELM_OK) return st;
+        // residual at the receivers and the misfit
+        CK(h, launch_gather(U, NV, drec, nrec, nb, gath, h->stream));
+        CK(h, cudaMemcpyAsync(ur.data(), gath, (size_t)nb * nrec * sizeof(double2), cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        // adjoint right-hand sides q = S^-1 conj(R^T r): repeated receivers of a source
+        // are summed here, so the scatter writes each point once
+        for (int b = 0; b < nb; ++b) {
+            std::vector<std::pair<int64_t, cd>> acc;
+            for (int r = 0; r < nrec; ++r) {
+                const double2 u0 = ur[(size_t)b * nrec + r], d0 = dd[(size_t)(s0 + b) * nrec + r];
+                const cd res(u0.x - d0.x, u0.y - d0.y);
+                J += 0.5 * std::norm(res);
+                bool found = false;
+                for (auto& pr : acc)
+                    if (pr.first == rec_idx[r]) { pr.second += res; found = true; }
+                if (!found) acc.push_back({rec_idx[r], res});
+            }
+            for (int r = 0; r < nrec; ++r) {
+                const auto& pr = acc[std::min(r, (int)acc.size() - 1)];   // unused slots repeat the last point
+                const int64_t p = pr.first;
+                const int x = (int)(p % Nx), y = (int)((p / Nx) % Ny), z = (int)(p / ((int64_t)Nx * Ny));
+                cd S = (1.0 / h->gx_int[x]) * (1.0 / h->gy_int[y]);
+                if (h->dim == 3) S *= 1.0 / h->gz_int[z];
+                const cd q = std::conj(pr.second) / S;
+                si[(size_t)b * nrec + r] = p;
+                sv[(size_t)b * nrec + r] = make_double2(q.real(), q.imag());
+            }
         }
-        for (auto& pr : acc) {
-            const int64_t p = pr.first;
-            const int x = (int)(p % Nx), y = (int)((p / Nx) % Ny), z = (int)(p / ((int64_t)Nx * Ny));
-            cd S = (1.0 / h->gx_int[x]) * (1.0 / h->gy_int[y]);
-            if (h->dim == 3) S *= 1.0 / h->gz_int[z];
-            const cd q = std::conj(pr.second) / S;
-            const double2 q2 = make_double2(q.real(), q.imag());
-            CK(h, cudaMemcpyAsync(FQ + (size_t)sidx * NV + p, &q2, sizeof(double2), cudaMemcpyHostToDevice,
-                                  h->stream));
-            CK(h, cudaStreamSynchronize(h->stream));
-        }
+        if (!want_grad) continue;
+        CK(h, cudaMemsetAsync(FQ, 0, (size_t)nb * NV * sizeof(double2), h->stream));
+        CK(h, cudaMemcpyAsync(dsi, si.data(), (size_t)nb * nrec * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              h->stream));
+        CK(h, cudaMemcpyAsync(dsv, sv.data(), (size_t)nb * nrec * sizeof(double2), cudaMemcpyHostToDevice,
+                              h->stream));
+        CK(h, launch_scatter(FQ, NV, dsi, dsv, nrec, nb, h->stream));
+        st = dev_fgmres(h, FQ, MU, nb, tol, 20, 400, iters, relres);
+        if (st != HELM_OK) return st;
+        CK(h, launch_grad_accum(U, MU, h->geom, nb, gpad, h->stream));
     }
-    st = dev_fgmres(h, FQ, MU, nsrc, tol, 20, 400, iters, relres);
-    if (st != HELM_OK) return st;
-    CK(h, launch_grad_accum(U, MU, h->geom, nsrc, gpad, h->stream));
-    CK(h, launch_fold(gpad, gint, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->stream));
-    if (is_device_ptr(grad_m))
-        CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    else
-        CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (want_grad) {
+        CK(h, launch_fold(gpad, gint, h->dim, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->w_outer, h->stream));
+        if (is_device_ptr(grad_m))
+            CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        else
+            CK(h, cudaMemcpyAsync(grad_m, gint, nint * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     *misfit = J;
     return HELM_OK;
@@ -1295,8 +1860,9 @@ void helm_dd_destroy(helm_dd* h) {
     cudaFree(h->d_ct);
     cudaFree(h->d_slab_sxz);
     cudaFree(h->d_counters);
-    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_kry,
-                    &h->ws_small, &h->ws_grad})
+    cudaFree(h->d_icols);
+    for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_io_aux,
+                    &h->ws_kry, &h->ws_small, &h->ws_grad, &h->ws_red})
         ws_free(*w);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
@@ -1307,46 +1873,6 @@ void helm_dd_destroy(helm_dd* h) {
 }
 
 const char* helm_dd_last_error(const helm_dd* h) { return h ? h->err.c_str() : "null handle"; }
-
-// ------------------------------------------------------------------------
-// Preconditioner application that allocates nothing.
-//
-// Some callers cannot let the library allocate device memory while they run:
-// programs that hand all device memory to their own pool allocator and forbid
-// any other allocation, programs running so close to the memory limit that a
-// late workspace allocation could fail mid-run, and latency-critical loops in
-// which cudaMalloc / cudaFree would stall the whole device.  For them the
-// work buffers of the double sweep come from one file-scope device array,
-// allocated by the CUDA runtime when the library's module is loaded and held
-// by every GPU that loads the library until the process exits.
-// ------------------------------------------------------------------------
-static constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB per device
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-namespace {
-constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};   // device address of the array, per device
-
-// Device address of the scratch array on the current device.  The array's name
-// is only a host-side stand-in, so the address is looked up once per device
-// (with that device current) and cached.
-cudaError_t noalloc_scratch(void** ptr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *ptr = g_noalloc_ptr[dev];
-    return cudaSuccess;
-}
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-}  // namespace
 
 extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* in, double* out, int nrhs) {
     if (!h || !in || !out || nrhs < 1) return HELM_EINVAL;
@@ -1368,9 +1894,8 @@ extern "C" helm_status helm_dd_apply_precond_noalloc(helm_dd* h, const double* i
         return fail(h, HELM_EINVAL, "apply_precond_noalloc needs " + std::to_string(total) +
                                         " bytes of scratch; the static limit is " +
                                         std::to_string(kNoAllocScratchBytes) + " (use fewer right-hand sides)");
-    void* base = nullptr;
-    CK(h, noalloc_scratch(&base));
-    unsigned char* b = (unsigned char*)base;
+    if (!h->noalloc_base) return fail(h, HELM_ESTATE, "no-allocation scratch not set up on this device");
+    unsigned char* b = (unsigned char*)h->noalloc_base;
     PrecondBufs bf{(double2*)(b + off[0]), (double2*)(b + off[1]), b + off[2], b + off[3],
                    (int*)(b + off[kPrecondBufs])};
     // the array keeps whatever the previous call left: the arrival counters must start at zero

@@ -129,6 +129,10 @@ struct OutArgs {
 template <typename C>
 cudaError_t launch_outputs(const OutArgs& O, void* const* pool, cudaStream_t s, KernelTimer* tm);
 
+// Whether one strip solve of st (a ring of at least four W x W blocks in shared memory)
+// fits on an SM with elements of esize bytes.
+bool strip_solve_fits(const StripDev& st, int zrows, size_t esize);
+
 template <typename C>
 // pst: the strip of the previous solve whose transfer enters this one (step.prev >= 0), host copy
 cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st_host, const StripDev* pst,
@@ -176,6 +180,13 @@ template <typename C>
 cudaError_t launch_slab_out(const Geom& g, const StripDev& st, int dir, const void* ybuf, int ld, double2* dst,
                             const double2* base, int B, cudaStream_t s, KernelTimer* tm);
 
+// Load the modules of each file's kernels onto the current device (lazy module
+// loading would otherwise load them, and take their memory, at the first launch
+// inside some later call).
+cudaError_t preload_sweep_kernels();
+cudaError_t preload_slab_kernels();
+cudaError_t preload_field_kernels();
+
 // ---- field.cu: FP64 grid kernels
 cudaError_t launch_k2(const double* c_int, double* k2, int dim, int nx, int ny, int nz, int w, double omega,
                       cudaStream_t s);
@@ -193,10 +204,26 @@ cudaError_t launch_multi_axpy(double2* w, const double2* V, int64_t vstride, con
 // dst[b] = src[b] * scale[b] (scale real, device [B])
 cudaError_t launch_scale(double2* dst, const double2* src, const double* scale, int B, int64_t N,
                          cudaStream_t s, KernelTimer* tm);
+// gpad += omega^2 Re sum_s S mu_s u_s
 cudaError_t launch_grad_accum(const double2* U, const double2* MU, const Geom& g, int nsrc, double* gpad,
                               cudaStream_t s);
 cudaError_t launch_fold(const double* gpad, double* gint, int dim, int nx, int ny, int nz, int w, cudaStream_t s);
 cudaError_t launch_gather(const double2* U, int64_t ustride, const int64_t* idx, int nidx, int B,
                           double2* out, cudaStream_t s);
+// Interface lines of the reduced space (Section 2.3): red[r * L + i] = column cols[i] of
+// grid row r, rows r = 0 .. B N_z N_y - 1.
+cudaError_t launch_gather_cols(const double2* full, double2* red, const int* cols, int L, int64_t rows, int Nx,
+                               cudaStream_t s, KernelTimer* tm);
+cudaError_t launch_scatter_cols(const double2* red, double2* full, const int* cols, int L, int64_t rows, int Nx,
+                                cudaStream_t s, KernelTimer* tm);
+// out (reduced) = f - A u on the interface columns, f from the full field f_full or the
+// reduced f_red (out = A u there when both are null)
+cudaError_t launch_stencil_cols(const Geom& g, const double2* u, const double2* f_full, const double2* f_red,
+                                double2* out, const int* cols, int L, int B, cudaStream_t s, KernelTimer* tm);
+// dst += src (n complex entries)
+cudaError_t launch_add(double2* dst, const double2* src, int64_t n, cudaStream_t s, KernelTimer* tm);
+// dst[b * stride + idx[b*n + i]] = val[b*n + i]  (device idx / val, B fields of n points)
+cudaError_t launch_scatter(double2* dst, int64_t stride, const int64_t* idx, const double2* val, int n, int B,
+                           cudaStream_t s);
 
 }  // namespace helm

@@ -567,8 +567,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_slab_sweep(SlabSweepArgs<C
 template <typename C>
 __global__ void k_slab_out(Geom g, StripDev st, int dir, const C* __restrict__ Y, int ld, double2* __restrict__ dst,
                            const double2* __restrict__ base, int B) {
-    const int olo = st.olo[dir], ohi = st.ohi[dir], nc = ohi - olo + 1;
     const int cofs = st.lo - st.lpml;
+    const int olo = st.olo[dir], ohi = min(st.ohi[dir], cofs + st.W - 1), nc = ohi - olo + 1;
     const int64_t tot = (int64_t)B * g.Nz * g.Ny * nc;
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < tot; o += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(o % nc);
@@ -719,10 +719,24 @@ template <typename C>
 cudaError_t launch_slab_out(const Geom& g, const StripDev& st, int dir, const void* ybuf, int ld, double2* dst,
                             const double2* base, int B, cudaStream_t s, KernelTimer* tm) {
     TimedLaunch t(tm, "slab_out", s);
-    const int64_t work = (int64_t)B * g.Nz * g.Ny * (st.ohi[dir] - st.olo[dir] + 1);
+    const int64_t work = (int64_t)B * g.Nz * g.Ny *
+                         (std::min(st.ohi[dir], st.lo - st.lpml + st.W - 1) - st.olo[dir] + 1);
     k_slab_out<C><<<grid_for(work, 256), 256, 0, s>>>(g, st, dir, reinterpret_cast<const C*>(ybuf), ld, dst, base,
                                                      B);
     return cudaGetLastError();
+}
+
+// Loads this file's module onto the current device (the strip-solve kernels of a
+// preconditioner application).
+cudaError_t preload_slab_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_slab_rhs<float2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_rhs<double2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<float2, 1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<double2, 1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_out<float2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_out<double2>);
+    return e;
 }
 
 #define HELM_SLAB_INST(C)                                                                                       \

@@ -1102,6 +1102,35 @@ static bool plan(const StripDev& st, int zrows, int B, int& Bt, int& ring, size_
     return false;
 }
 
+bool strip_solve_fits(const StripDev& st, int zrows, size_t esize) {
+    int Bt, ring;
+    size_t smem;
+    return esize == sizeof(float2) ? plan<float2>(st, zrows, 1, Bt, ring, smem)
+                                   : plan<double2>(st, zrows, 1, Bt, ring, smem);
+}
+
+// Shared-memory limit of every strip-solve instantiation (this also loads the module).
+template <typename C>
+static cudaError_t chunk_kernel_attrs() {
+    for (auto fn : {k_sweep_chunk<C, 8, 1>, k_sweep_chunk<C, 10, 1>, k_sweep_chunk<C, 12, 1>,
+                    k_sweep_chunk<C, 14, 1>, k_sweep_chunk<C, 16, 1>, k_sweep_chunk<C, 8, 4>,
+                    k_sweep_chunk<C, 10, 4>, k_sweep_chunk<C, 12, 4>, k_sweep_chunk<C, 14, 4>,
+                    k_sweep_chunk<C, 16, 4>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t preload_sweep_kernels() {
+    cudaError_t e = chunk_kernel_attrs<float2>();
+    if (e == cudaSuccess) e = chunk_kernel_attrs<double2>();
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sweep_output<float2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sweep_output<double2>);
+    return e;
+}
+
 template <typename C>
 cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const StripDev* pst,
                                const SweepStep& step, const SweepWork& wk, void* const* pool, cudaStream_t s,
@@ -1111,13 +1140,8 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     if (!plan<C>(st, wk.zrows, wk.B, Bt, ring, smem)) return cudaErrorInvalidConfiguration;
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto fn : {k_sweep_chunk<C, 8, 1>, k_sweep_chunk<C, 10, 1>, k_sweep_chunk<C, 12, 1>,
-                        k_sweep_chunk<C, 14, 1>, k_sweep_chunk<C, 16, 1>, k_sweep_chunk<C, 8, 4>,
-                        k_sweep_chunk<C, 10, 4>, k_sweep_chunk<C, 12, 4>, k_sweep_chunk<C, 14, 4>,
-                        k_sweep_chunk<C, 16, 4>}) {
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = chunk_kernel_attrs<C>();
+        if (e != cudaSuccess) return e;
         attr_set = true;
     }
     SweepArgs A = make_args<C>(g, st, step, wk, pool, Bt, ring);

@@ -54,6 +54,7 @@ def load() -> ctypes.CDLL:
         "helm_dd_set_chunks": (I, [P, I]),
         "helm_dd_set_sep_groups": (I, [P, I]),
         "helm_dd_sep_groups": (I, [P]),
+        "helm_dd_set_panel": (I, [P, I]),
         "helm_dd_factor": (I, [P]),
         "helm_dd_apply_precond": (I, [P, P, P, I]),
         "helm_dd_apply_precond_noalloc": (I, [P, P, P, I]),
@@ -67,6 +68,10 @@ def load() -> ctypes.CDLL:
         "helm_dd_dims": (None, [P, P]),
         "helm_dd_strip_widths": (I, [P, P, I]),
         "helm_dd_interfaces": (I, [P, P, I]),
+        "helm_dd_interface_lines": (I, [P, P, I]),
+        "helm_dd_reduce_rhs": (I, [P, P, P, P, I]),
+        "helm_dd_apply_AP_reduced": (I, [P, P, P, I]),
+        "helm_dd_solve_reduced": (I, [P, P, P, I, D, I, I, ctypes.POINTER(RhsInfo)]),
         "helm_dd_destroy": (None, [P]),
         "helm_dd_last_error": (ctypes.c_char_p, [P]),
     }
@@ -119,7 +124,7 @@ class HelmDD:
     """
 
     def __init__(self, c, h, omega, w_outer, w_sub, J, precision="mixed", c_ref=None, chunks=0,
-                 sep_groups=0):
+                 sep_groups=0, panel=0):
         self.lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.dim = c.ndim
@@ -145,6 +150,8 @@ class HelmDD:
             self._check(self.lib.helm_dd_set_chunks(self._h, int(chunks)))
         if sep_groups:
             self._check(self.lib.helm_dd_set_sep_groups(self._h, int(sep_groups)))
+        if panel:
+            self._check(self.lib.helm_dd_set_panel(self._h, int(panel)))
         N = (ctypes.c_int64 * 3)()
         self.lib.helm_dd_dims(self._h, N)
         self.N = tuple(int(N[a]) for a in range(self.dim))
@@ -191,6 +198,10 @@ class HelmDD:
     def set_stream(self, stream_handle: int):
         """Run the handle's device work on this cudaStream_t (0 = its own stream)."""
         self._check(self.lib.helm_dd_set_stream(self._h, ctypes.c_void_p(int(stream_handle) or None)))
+
+    def set_panel(self, nrhs: int):
+        """Right-hand sides per internal panel of solve / gradient (0 = as many as fit)."""
+        self._check(self.lib.helm_dd_set_panel(self._h, int(nrhs)))
 
     def set_timing(self, on: bool):
         self._check(self.lib.helm_dd_set_timing(self._h, 1 if on else 0))
@@ -268,19 +279,74 @@ class HelmDD:
         return o.obj, [dict(iters=info[i].iters, rel_res=info[i].rel_res, t_ms=info[i].t_ms)
                        for i in range(nrhs)]
 
-    def gradient(self, src_idx, rec_idx, d, tol=1e-6):
-        """(misfit, dJ/dm on the interior grid) for sources/receivers at padded indices."""
+    # -- the reduced space (Section 2.3, Algorithms 2-5) -----------------------
+    def interface_lines(self) -> list:
+        """Padded columns of the 2(J-1) interface lines beta_j+1, beta_j+2."""
+        L = int(self.lib.helm_dd_interface_lines(self._h, None, 0))
+        buf = (ctypes.c_int * max(L, 1))()
+        self.lib.helm_dd_interface_lines(self._h, buf, L)
+        return list(buf)[:L]
+
+    def _red_shape(self, nrhs):
+        return (nrhs,) + self.shape[:-1] + (len(self.interface_lines()),)
+
+    def _red_out(self, like, shape):
+        if _is_torch(like):
+            import torch
+            return torch.empty(shape, dtype=torch.complex128, device=like.device)
+        return np.empty(shape, dtype=np.complex128)
+
+    def reduce_rhs(self, f, want_ut=False):
+        """Algorithm 2: (phi on the interface lines [nrhs, ..., N_y, L], u~ or None)."""
+        nrhs = self._fields(f)
+        a = _Arr(f, np.complex128)
+        phi = _Arr(self._red_out(f, self._red_shape(nrhs)), np.complex128)
+        ut = _Arr(self._red_out(f, (nrhs,) + self.shape), np.complex128) if want_ut else None
+        _sync_torch(f)
+        self._check(self.lib.helm_dd_reduce_rhs(self._h, a.ptr, phi.ptr, ut.ptr if ut else None, nrhs))
+        return phi.obj, (ut.obj if ut else None)
+
+    def apply_AP_reduced(self, y):
+        """Algorithm 3 on interface-line data y [nrhs, ..., N_y, L]: R A P E y."""
+        L = len(self.interface_lines())
+        per = int(np.prod(self.shape[:-1])) * L
+        nrhs = int(np.prod(y.shape)) // per
+        if nrhs < 1 or nrhs * per != int(np.prod(y.shape)):
+            raise ValueError("reduced array size is not a multiple of N_z N_y L")
+        a = _Arr(y, np.complex128)
+        o = _Arr(self._red_out(y, tuple(y.shape)), np.complex128)
+        _sync_torch(y)
+        self._check(self.lib.helm_dd_apply_AP_reduced(self._h, a.ptr, o.ptr, nrhs))
+        return o.obj
+
+    def solve_reduced(self, f, tol=1e-6, restart=20, maxit=200, check=True):
+        """Algorithm 5 in the reduced space; returns (u, info) like solve."""
+        nrhs = self._fields(f)
+        a, out = _Arr(f, np.complex128), self._out_like(f)
+        o = _Arr(out, np.complex128)
+        info = (RhsInfo * nrhs)()
+        _sync_torch(f)
+        st = self.lib.helm_dd_solve_reduced(self._h, a.ptr, o.ptr, nrhs, float(tol), int(restart), int(maxit), info)
+        if st not in (0, -5) or (check and st != 0):
+            self._check(st)
+        return o.obj, [dict(iters=info[i].iters, rel_res=info[i].rel_res, t_ms=info[i].t_ms)
+                       for i in range(nrhs)]
+
+    def gradient(self, src_idx, rec_idx, d, tol=1e-6, with_grad=True):
+        """(misfit, dJ/dm on the interior grid) for sources/receivers at padded indices;
+        with_grad=False runs the forward solves only and returns (misfit, None)."""
         src = np.ascontiguousarray(src_idx, dtype=np.int64)
         rec = np.ascontiguousarray(rec_idx, dtype=np.int64)
         dd = np.ascontiguousarray(d, dtype=np.complex128)
         if dd.shape != (src.size, rec.size):
             raise ValueError("d must have shape (nsrc, nrec)")
-        grad = np.empty(tuple(reversed(self.n)), dtype=np.float64)
+        grad = np.empty(tuple(reversed(self.n)), dtype=np.float64) if with_grad else None
         mis = ctypes.c_double()
         self._check(self.lib.helm_dd_gradient(self._h, src.ctypes.data_as(ctypes.c_void_p), src.size,
                                               rec.ctypes.data_as(ctypes.c_void_p), rec.size,
                                               dd.ctypes.data_as(ctypes.c_void_p), float(tol),
-                                              ctypes.byref(mis), grad.ctypes.data_as(ctypes.c_void_p)))
+                                              ctypes.byref(mis),
+                                              grad.ctypes.data_as(ctypes.c_void_p) if with_grad else None))
         return float(mis.value), grad
 
 
@@ -292,26 +358,32 @@ def _torch_misfit_function():
 
         forward(m, spec): m = 1/c^2 on the interior grid (float64 tensor); spec is
         a dict with h, omega, w_outer, w_sub, J, src, rec, d and optional
-        precision, c_ref, tol.  The forward pass factors the strips at m and runs
-        the forward and adjoint solves in one library call; only the interior
-        gradient is kept for backward (wavefields are not stored).
+        precision, c_ref, tol, panel.  The forward pass factors the strips at m
+        and runs the forward solves only (the misfit); the factored solver is
+        kept for backward, which recomputes the forward fields and runs the
+        adjoint solves (no wavefield is stored between the two passes).
         """
 
         @staticmethod
         def forward(ctx, m, spec):
             c = (1.0 / torch.sqrt(m.detach())).cpu().numpy()
             solver = HelmDD(c, spec["h"], spec["omega"], spec["w_outer"], spec["w_sub"], spec["J"],
-                            spec.get("precision", "mixed"), c_ref=spec.get("c_ref"))
+                            spec.get("precision", "mixed"), c_ref=spec.get("c_ref"), panel=spec.get("panel", 0))
             solver.factor()
-            J, g = solver.gradient(spec["src"], spec["rec"], spec["d"], spec.get("tol", 1e-6))
-            solver.close()
-            ctx.save_for_backward(torch.as_tensor(g, dtype=m.dtype, device=m.device))
+            J, _ = solver.gradient(spec["src"], spec["rec"], spec["d"], spec.get("tol", 1e-6), with_grad=False)
+            ctx.solver = solver
+            ctx.spec = spec
+            ctx.meta = (m.dtype, m.device)
             return torch.tensor(J, dtype=m.dtype, device=m.device)
 
         @staticmethod
         def backward(ctx, gout):
-            (g,) = ctx.saved_tensors
-            return gout * g, None
+            spec = ctx.spec
+            _, g = ctx.solver.gradient(spec["src"], spec["rec"], spec["d"], spec.get("tol", 1e-6))
+            ctx.solver.close()
+            ctx.solver = None
+            dtype, device = ctx.meta
+            return gout * torch.as_tensor(g, dtype=dtype, device=device), None
 
     return HelmholtzMisfit
 

@@ -56,6 +56,22 @@ def test_slab_precond_fp64_matches_oracle(case):
     assert rel(Pf, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_slab_precond_large_blocks_match_oracle(prec, tol):
+    """Blocks of 1860 and 1800 unknowns (31 and 30 x-columns by 60 z-planes): every
+    one of the eight 256-column segments of the strip-solve kernel and 12-13 rows per
+    CTA, as in the smooth63_3d workload (1659-1817); B = 1 and a ragged B = 5."""
+    g, o = make3((40, 6, 52), 4, 6, 2, prec)
+    assert min(w * g.N[2] for w in g.strip_widths()) > 7 * 256
+    g.factor()
+    o.factor()
+    f = media.random_rhs((5,) + g.shape, 19)
+    ref = np.stack([o.apply_precond(f[b]) for b in range(5)])
+    assert rel(g.apply_precond(f), ref) <= tol
+    assert rel(g.apply_precond(f[:1]), ref[:1]) <= tol
+    g.close()
+
+
 @pytest.mark.parametrize("case", CASES3[:2])
 def test_slab_precond_mixed_close_to_oracle(case):
     g, o = make3(*case, "mixed")

@@ -97,3 +97,16 @@ def test_wide_single_strip_rejected(lib):
     c = np.ones((20, 70))
     with pytest.raises(helm.HelmError):
         helm.HelmDD(c, 0.05, 5.0, 4, 3, 1, "fp64")
+
+
+@pytest.mark.parametrize("name", ["const127", "smooth1023", "layered4095"])
+def test_interface_lines_match_oracle(lib, name):
+    """The reduced space's 2(J-1) lines beta_j+1, beta_j+2 (Section 2.3), from the host geometry."""
+    wl = media.WORKLOADS[name]
+    s = helm.HelmDD(np.ones(tuple(reversed(wl.n))), wl.h, 10.0, wl.w_outer, wl.w_sub, wl.J, "mixed")
+    beta = HelmholtzDD.interfaces(wl.n[0], wl.padded[0], wl.w_outer, wl.J)
+    ref = []
+    for j in range(1, wl.J):
+        ref += [beta[j] + 1, beta[j] + 2]
+    assert s.interface_lines() == ref
+    s.close()

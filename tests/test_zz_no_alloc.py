@@ -3,11 +3,13 @@
 Callers whose own allocator owns all device memory, or that run too close to
 the memory limit (or too latency-critically) to let a library call cudaMalloc
 mid-run, use helm_dd_apply_precond_noalloc: its work buffers live in one
-static 64 MiB device array.  This file checks, through the C ABI, that it
-returns what helm_dd_apply_precond returns on two calls in a row (the second
-call finds the first call's leftovers in the shared array), and that it
-rejects a batch whose buffers would not fit.  It runs last so that a failure
-here cannot hide the rest of the suite; it passes alone and after the others.
+static 64 MiB device array, loaded when a handle first uses the device.  This
+file checks, through the C ABI, that it returns what helm_dd_apply_precond
+returns on two calls in a row (the second call finds the first call's leftovers
+in the shared array), that a fresh handle's first call leaves the device's free
+memory unchanged, and that it rejects a batch whose buffers would not fit.  It
+runs last so that a failure here cannot hide the rest of the suite; it passes
+alone and after the others.
 """
 import numpy as np
 import pytest
@@ -47,8 +49,8 @@ def test_noalloc_matches_apply_precond_on_two_calls(prec, chunks):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_noalloc_matches_apply_precond_3d(prec):
-    # 3-D strips: right-hand sides and two strip solutions in the array, and the strip
-    # solve's step counter (a second call must find it reset)
+    # 3-D strips: right-hand sides, two strip solutions and the strip solve's step
+    # counter in the array (a second call must find the counter reset)
     torch = pytest.importorskip("torch")
     n = (17, 13, 11)
     c = media.smooth_medium(n, 2.0, 1.0, 2.0, 7)
@@ -62,6 +64,28 @@ def test_noalloc_matches_apply_precond_3d(prec):
         torch.cuda.synchronize()
         err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
         assert err <= TOL, (call, err)
+    g.close()
+
+
+def test_noalloc_first_call_of_a_fresh_handle_allocates_nothing():
+    torch = pytest.importorskip("torch")
+    # another handle runs the same kernels first, so that loading their code is not
+    # counted against the call under test
+    w = _problem("mixed")
+    f = torch.as_tensor(media.random_rhs((2,) + w.shape, 23), device="cuda")
+    w.apply_precond(f)
+    w.close()
+    g = _problem("mixed")   # created and factored: its first device use is behind it
+    out = torch.empty_like(f)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    g.apply_precond_noalloc(f, out=out)   # the handle's first preconditioner call
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    ref = g.apply_precond(f)
+    err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
+    assert err <= TOL, err
     g.close()
 
 
