@@ -184,7 +184,7 @@ class HelmholtzDD:
     """Discrete problem plus the double-sweep preconditioner (Sections 2.1-2.3)."""
 
     def __init__(self, c: np.ndarray, h: float, omega: float, w_outer: int,
-                 w_sub: int, J: int, c_ref: float | None = None):
+                 w_sub: int, J: int, c_ref: float | None = None, transmission: str = "pml"):
         c = np.asarray(c, dtype=float)
         if not np.all(np.isfinite(c)) or np.any(c <= 0):
             raise ValueError("speed must be positive and finite")
@@ -195,6 +195,9 @@ class HelmholtzDD:
         self.w_outer = int(w_outer)
         self.w_sub = int(w_sub)
         self.J = int(J)
+        if transmission not in ("pml", "robin"):
+            raise ValueError("transmission is 'pml' or 'robin'")
+        self.transmission = transmission
         self.N = tuple(k + 2 * self.w_outer for k in self.n)
         # c_ref fixes the PML strength; by default the maximum of the medium
         self.c_max = float(c.max()) if c_ref is None else float(c_ref)
@@ -228,6 +231,8 @@ class HelmholtzDD:
     def _strip(self, j: int) -> Strip:
         lo = self.beta[j] + 1
         hi = self.beta[j + 1] + 1 if j < self.J - 1 else self.N[0] - 1
+        if self.transmission == "robin":   # Section 4.4: no added PML, overlap of one column
+            return Strip(j, lo, hi, 0, 0)
         return Strip(j, lo, hi, self.w_sub if j > 0 else 0,
                      self.w_sub if j < self.J - 1 else 0)
 
@@ -272,10 +277,44 @@ class HelmholtzDD:
         return self.k2[..., cols]
 
     def strip_operator(self, j: int):
-        """(A^(j), S^(j)) on strip j's grid (Eq. grid_A_j)."""
+        """(A^(j), S^(j)) on strip j's grid (Eq. grid_A_j; with Robin transmission the
+        strip carries the ghost-eliminated Robin rows of robin_boundary_terms)."""
         st = self.strips[j]
         axes = [self.strip_x_alpha(st)] + list(self.axes[1:])
-        return helmholtz_operator(axes, self.strip_k2(st), self.h), symmetriser(axes)
+        Aj = helmholtz_operator(axes, self.strip_k2(st), self.h)
+        if self.transmission == "robin":
+            d = np.zeros(self.strip_k2(st).shape, dtype=complex)
+            for col, coef in self.robin_boundary_terms(j):
+                d[..., col] += coef
+            Aj = (Aj + sp.diags(d.ravel())).tocsr()
+        return Aj, symmetriser(axes)
+
+    # -- Section 4.4: Robin transmission conditions -------------------------
+    def robin_ab(self, col: int):
+        """(a, b) of the discrete Robin condition on a boundary half point next to padded
+        column col (the strip's boundary column), per grid row: with u_in the value at col
+        and u_out the one across the half point,
+            -+ d_x u + i k u  ~  a u_in + b u_out,   a = 1/h + i k/2,  b = -1/h + i k/2,
+        d_x u by the one-sided difference over the half point and u by the mean of the two
+        values; k = sqrt(k^2) at col."""
+        k = np.sqrt(self.k2[..., col])
+        return 1.0 / self.h + 0.5j * k, -1.0 / self.h + 0.5j * k
+
+    def robin_boundary_terms(self, j: int):
+        """The Robin rows of strip j: eliminating the ghost value u_out = (data - a u_in)/b
+        from the x-difference -(u_next - 2 u_in + u_out)/h^2 at the boundary column adds
+        (a/b)/h^2 to its diagonal and data/(b h^2) to its right-hand side.  Returns
+        (strip-local column, added diagonal per row) for the left boundary l^(j) (j > 0) and
+        the right boundary r^(j) (j < J-1)."""
+        st = self.strips[j]
+        out = []
+        if j > 0:
+            a, b = self.robin_ab(st.lo)
+            out.append((0, a / (b * self.h ** 2)))
+        if j < self.J - 1:
+            a, b = self.robin_ab(st.hi)
+            out.append((st.W - 1, a / (b * self.h ** 2)))
+        return out
 
     # -- Algorithm 1: preparation -------------------------------------------
     def factor(self):
@@ -300,6 +339,8 @@ class HelmholtzDD:
     # -- Section 2.1 (Eqs. solve_upward, solve_downward), Section 2.2 ------
     def apply_precond(self, f: np.ndarray, return_parts: bool = False):
         """P f = v + w: forward sweep, residual, backward sweep, compose."""
+        if self.transmission == "robin":
+            return self.apply_precond_robin(f, return_parts)
         f = np.asarray(f, dtype=complex)
         J, h = self.J, self.h
         beta = self.beta
@@ -340,6 +381,62 @@ class HelmholtzDD:
                 r[..., st.local(b + 2)] += t
             wj = self.strip_solve(j, r)
             w[..., dt] = wj[..., dt - st.lo + st.lpml]
+            w_next = wj
+        if return_parts:
+            return v + w, v, g, w
+        return v + w
+
+    def apply_precond_robin(self, f: np.ndarray, return_parts: bool = False):
+        """The double sweep with Robin transmission conditions (Section 4.4).
+
+        Right sweep, j = 1..J: v^(j) solves the Helmholtz equation on
+        ]l^(j), r^(j)[ (padded columns beta_{j-1}+1 .. beta_j+1, l^(j) = x_{beta_{j-1}+1/2},
+        r^(j) = x_{beta_j+3/2}: an overlap of one column) with f^(j) = f on
+        l^(j) < x < l^(j+1), d_x v + ik v = d_x v^(j-1) + ik v^(j-1) at l^(j) and
+        -d_x v + ik v = 0 at r^(j); v = v^(j) on l^(j) < x < l^(j+1).  Then g = f - A v,
+        and the left sweep is the left-right reflection with g as right-hand side:
+        j = J-1..1 (g vanishes on the last strip's part), -d_x w + ik w =
+        -d_x w^(j+1) + ik w^(j+1) at r^(j), d_x w + ik w = 0 at l^(j), w = w^(j) on
+        r^(j-1) < x < r^(j).  Output v + w.  The outer PML stays at the outer boundaries.
+        """
+        f = np.asarray(f, dtype=complex)
+        J, h = self.J, self.h
+        beta = self.beta
+        v = np.zeros_like(f)
+        v_prev = None
+        for j in range(J):                                  # right sweep
+            st = self.strips[j]
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            core = np.arange(beta[j] + 1, beta[j + 1] + 1)
+            r[..., core - st.lo] = f[..., core]
+            if j > 0:
+                # Robin data of v^(j-1) at l^(j): d_x v + ik v ~ a v_in + b v_out, with
+                # v_in at column beta_j+1 (inside strip j) and v_out at beta_j
+                pst = self.strips[j - 1]
+                a, b = self.robin_ab(st.lo)
+                data = a * v_prev[..., st.lo - pst.lo] + b * v_prev[..., st.lo - 1 - pst.lo]
+                r[..., 0] += data / (b * h ** 2)
+            vj = self.strip_solve(j, r)
+            v[..., core] = vj[..., core - st.lo]
+            v_prev = vj
+        g = f - self.matvec(v)
+        w = np.zeros_like(f)
+        w_next = None
+        for j in range(J - 2, -1, -1):                      # left sweep
+            st = self.strips[j]
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            lo_t = beta[j] + 2 if j > 0 else 0
+            dt = np.arange(lo_t, beta[j + 1] + 2)
+            r[..., dt - st.lo] = g[..., dt]
+            if j + 1 <= J - 2:
+                # Robin data of w^(j+1) at r^(j): -d_x w + ik w ~ a w_in + b w_out, with
+                # w_in at column beta_{j+1}+1 (inside strip j) and w_out at beta_{j+1}+2
+                nst = self.strips[j + 1]
+                a, b = self.robin_ab(st.hi)
+                data = a * w_next[..., st.hi - nst.lo] + b * w_next[..., st.hi + 1 - nst.lo]
+                r[..., st.W - 1] += data / (b * h ** 2)
+            wj = self.strip_solve(j, r)
+            w[..., dt] = wj[..., dt - st.lo]
             w_next = wj
         if return_parts:
             return v + w, v, g, w

@@ -449,3 +449,140 @@ def test_reduced_space_is_empty_for_one_strip():
     assert iters == 0
     ud = o.direct_solve(f)
     assert np.linalg.norm(u - ud) / np.linalg.norm(ud) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Section 4.4: Robin transmission conditions
+# ---------------------------------------------------------------------------
+
+def _robin_problem(n=(37, 19), J=3, w_outer=4, seed=8):
+    c = media.smooth_medium(n, 3.0, 1.0, 2.0, seed)
+    h = 1.0 / 24
+    omega = media.omega_for(c, h, 8.0)
+    return HelmholtzDD(c, h, omega, w_outer, 3, J, transmission="robin"), h
+
+
+def test_robin_strip_rows_match_explicit_ghost_system():
+    """The eliminated Robin rows of an interior strip against the explicit system: the
+    physical columns with the global stencil, plus one ghost column on each side whose
+    row is the discrete Robin condition a u_in + b u_ghost = data (Section 4.4, d_x u
+    one-sided over the half point, u the mean).  Dense solves on a tiny strip."""
+    p, h = _robin_problem()
+    p.factor()
+    j = 1
+    st = p.strips[j]
+    Ny, W = p.N[1], st.W
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((Ny, W)) + 1j * rng.standard_normal((Ny, W))
+    dl = rng.standard_normal(Ny) + 1j * rng.standard_normal(Ny)
+    dr = rng.standard_normal(Ny) + 1j * rng.standard_normal(Ny)
+    # explicit system: columns st.lo-1 (ghost) .. st.hi+1 (ghost), rows from the global A
+    cols = np.arange(st.lo - 1, st.hi + 2)
+    Wx = cols.size
+    A = p.A.tocsr()
+    Nx = p.N[0]
+    M = np.zeros((Ny * Wx, Ny * Wx), dtype=complex)
+    rhs = np.zeros(Ny * Wx, dtype=complex)
+    idx = lambda y, c: y * Wx + c
+    al, bl = p.robin_ab(st.lo)
+    ar, br = p.robin_ab(st.hi)
+    for y in range(Ny):
+        for ci, gc in enumerate(cols):
+            r = idx(y, ci)
+            if ci == 0:                     # left ghost: a u(lo) + b u(lo-1) = data
+                M[r, idx(y, 1)] = al[y]
+                M[r, r] = bl[y]
+                rhs[r] = dl[y]
+            elif ci == Wx - 1:              # right ghost: a u(hi) + b u(hi+1) = data
+                M[r, idx(y, Wx - 2)] = ar[y]
+                M[r, r] = br[y]
+                rhs[r] = dr[y]
+            else:
+                row = A.getrow(y * Nx + gc)
+                for q, v in zip(row.indices, row.data):
+                    yy, xx = divmod(q, Nx)
+                    M[r, idx(yy, xx - cols[0])] += v
+                rhs[r] = f[y, ci - 1]
+    ref = np.linalg.solve(M, rhs).reshape(Ny, Wx)[:, 1:-1]
+    r = f.copy()
+    r[:, 0] += dl / (bl * h ** 2)
+    r[:, -1] += dr / (br * h ** 2)
+    got = p.strip_solve(j, r)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_robin_one_strip_is_exact_and_preconditioner_linear():
+    p, _ = _robin_problem(J=1)
+    p.factor()
+    f = media.random_rhs(tuple(reversed(p.N)), 4)
+    assert np.linalg.norm(p.matvec(p.apply_precond(f)) - f) <= 1e-10 * np.linalg.norm(f)
+    q, _ = _robin_problem(J=4)
+    q.factor()
+    g1 = media.random_rhs(tuple(reversed(q.N)), 5)
+    g2 = media.random_rhs(tuple(reversed(q.N)), 6)
+    lhs = q.apply_precond(2.0 * g1 - 3j * g2)
+    rhs = 2.0 * q.apply_precond(g1) - 3j * q.apply_precond(g2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-11 * np.linalg.norm(rhs)
+
+
+def test_robin_residual_support_invariants():
+    """As for the PML sweep: g = f - A v off columns beta_j, beta_j+1 and f - A P f off
+    beta_j+1, beta_j+2 vanish (every strip solve is exact away from its two boundaries)."""
+    p, _ = _robin_problem(n=(45, 21), J=4)
+    p.factor()
+    f = media.random_rhs(tuple(reversed(p.N)), 7)
+    Pf, v, g, w = p.apply_precond(f, return_parts=True)
+    b = p.beta
+    keep_g = sorted({b[j] for j in range(1, 4)} | {b[j] + 1 for j in range(1, 4)})
+    keep_r = sorted({b[j] + 1 for j in range(1, 4)} | {b[j] + 2 for j in range(1, 4)})
+    assert np.linalg.norm(np.delete(g, keep_g, axis=-1)) <= 1e-10 * np.linalg.norm(f)
+    r = f - p.matvec(Pf)
+    assert np.linalg.norm(np.delete(r, keep_r, axis=-1)) <= 1e-10 * np.linalg.norm(f)
+
+
+def test_robin_iterations_follow_table4():
+    """Table 4 (constant medium, layers of 10 points): Robin transmission needs more
+    iterations than PML transmission at every size, and more as the domain grows (the
+    paper's 9 and 13 at N_x = 100 and 200), while the PML counts stay flat."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table4_robin_iterations.txt"))
+    its = {}
+    for n, J in ((99, 10), (199, 20)):
+        h = 1.0 / (n + 1)
+        c = np.ones((n, n))
+        omega = 2 * math.pi / (10 * h)
+        f = media.point_sources((n, n), 10, h, [((n - 1) // 2, (n - 1) // 2)])[0]
+        for tr in ("pml", "robin"):
+            prob = HelmholtzDD(c, h, omega, 10, 10, J, transmission=tr).factor()
+            _, it, rr, _ = prob.solve(f, tol=1e-6, maxit=300)
+            assert rr <= 1e-6
+            its[(n, tr)] = it
+    for n, paper in ((99, rows[0, 2]), (199, rows[1, 2])):
+        assert its[(n, "robin")] > its[(n, "pml")] + 2
+        assert 0.6 * paper <= its[(n, "robin")] <= 1.4 * paper, (n, its[(n, "robin")], paper)
+    assert its[(199, "robin")] > its[(99, "robin")]
+    assert its[(199, "pml")] <= its[(99, "pml")] + 1
+
+
+def test_robin_condition_annihilates_outgoing_plane_waves():
+    """The discrete Robin data at a left boundary (d_x u + ik u, Section 4.4) of a plane
+    wave leaving through it, e^{-ikx}, is O((kh)^2) relative to k|u| and falls by 4 when h
+    halves; an incoming wave e^{+ikx} gives 2ik u (u on the half point).  Checked through robin_ab on a constant
+    medium, at the strip boundary column and its outer neighbour."""
+    errs = []
+    k = 10.0
+    for n in (80, 160):   # kh = 0.125, 0.0625
+        h = 1.0 / n
+        c = np.ones((6, n))
+        p = HelmholtzDD(c, h, k, 0, 1, 2, transmission="robin")
+        col = p.strips[1].lo
+        a, b = p.robin_ab(col)
+        x_in, x_out = col * h, (col - 1) * h
+        out_in, out_out = np.exp(-1j * k * x_in), np.exp(-1j * k * x_out)
+        inc_in, inc_out = np.exp(1j * k * x_in), np.exp(1j * k * x_out)
+        e = np.abs(a * out_in + b * out_out) / (k * np.abs(out_in))
+        errs.append(float(e.max()))
+        # the data lives on the half point between the two columns
+        g = (a * inc_in + b * inc_out) / (2j * k * np.exp(1j * k * (x_in - 0.5 * h)))
+        assert np.allclose(g, 1.0, atol=0.01)
+    assert errs[0] < 0.01
+    assert 3.5 <= errs[0] / errs[1] <= 4.5, errs
