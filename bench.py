@@ -27,6 +27,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -391,6 +393,89 @@ def run_layered(helm, torch, stream, args):
     return out
 
 
+def run_table3(helm, torch, stream, args):
+    """Iterations against the added-layer width on the 3-D constant medium (Section 4.3,
+    Example 3, Table 3 shape: unit cube, c = 1, 10 points per wavelength, strips of about
+    10 planes), mixed precision, one centre source.  The GPU counts at 31^3 and 47^3 sit
+    next to the oracle's (tests/golden/table3_oracle_iterations.txt, a stored file written
+    by the oracle); 63^3 (79^3 padded, J = 7 strips of 9 planes, the largest cube whose
+    slab blocks fit the 2048-unknown limit at w_sub = 6) is GPU only."""
+    media = media_mod()
+    golden = {}
+    try:
+        for n, J, wo, ws, it in np.loadtxt(os.path.join(ROOT, "tests", "golden", "table3_oracle_iterations.txt"),
+                                           dtype=int, ndmin=2):
+            golden[(int(n), int(ws))] = int(it)
+    except OSError:
+        pass
+    out = {"workload": "const_cube_3d (Table 3 shape)", "w_sub": [2, 3, 4, 5, 6], "rows": []}
+    for n, J, wo in ((31, 3, 6), (47, 4, 8), (63, 7, 8)):
+        h = 1.0 / (n + 1)
+        c = np.ones((n, n, n))
+        omega = 2 * math.pi / (10 * h)
+        m = (n - 1) // 2
+        f = torch.as_tensor(media.point_sources((n, n, n), wo, h, [(m, m, m)]), device="cuda")
+        row = {"n": n, "J": J, "w_outer": wo, "gpu_iters": [], "ms_per_solve": [], "factor_ms": [],
+               "oracle_iters": [golden.get((n, ws)) for ws in out["w_sub"]]}
+        for ws in out["w_sub"]:
+            g = helm.HelmDD(c, h, omega, wo, ws, J, "mixed")
+            g.set_stream(stream.cuda_stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record()
+            g.factor()
+            ev[1].record()
+            g.solve(f, tol=1e-6)
+            ev[2].record()
+            _, info = g.solve(f, tol=1e-6)
+            ev[3].record()
+            torch.cuda.synchronize()
+            row["gpu_iters"].append(info[0]["iters"])
+            row["ms_per_solve"].append(ev[2].elapsed_time(ev[3]))
+            row["factor_ms"].append(ev[0].elapsed_time(ev[1]))
+            g.close()
+        out["rows"].append(row)
+    return out
+
+
+def run_robin_table4(helm, torch, stream, args):
+    """Table 4 of Section 4.4 on the GPU: the 2-D constant medium on the unit square at 10
+    points per wavelength, layers of 10 points (w_outer = w_sub = 10, strips of 10 columns,
+    J = N_x / 10), one centre source, iterations and solve time with PML transmission and
+    with Robin transmission (no added layers, overlap of one column), mixed precision.
+    The paper's counts (its own media and PML profile) are quoted beside them."""
+    media = media_mod()
+    paper = {}
+    for name in ("table4_pml_iterations.txt", "table4_robin_iterations.txt"):
+        try:
+            for N, J, it in np.loadtxt(os.path.join(ROOT, "tests", "golden", name), ndmin=2):
+                paper[(name.split("_")[1], int(N))] = int(it)
+        except OSError:
+            pass
+    rows = []
+    for n in (99, 199, 399, 799, 1599):
+        J = (n + 1) // 10
+        h = 1.0 / (n + 1)
+        c = np.ones((n, n))
+        omega = 2 * math.pi / (10 * h)
+        f = torch.as_tensor(media.point_sources((n, n), 10, h, [((n - 1) // 2, (n - 1) // 2)]), device="cuda")
+        row = {"N_x": n, "J": J}
+        for tr in ("pml", "robin"):
+            g = helm.HelmDD(c, h, omega, 10, 10, J, "mixed", transmission=tr)
+            g.set_stream(stream.cuda_stream)
+            g.factor()
+            g.solve(f, tol=1e-6, maxit=400)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            _, info = g.solve(f, tol=1e-6, maxit=400)
+            ev[1].record()
+            torch.cuda.synchronize()
+            row[tr] = {"iters": info[0]["iters"], "rel_res": info[0]["rel_res"], "ms_per_solve": ev[0].elapsed_time(ev[1]),
+                       "paper_iters": paper.get((tr, n + 1))}
+            g.close()
+        rows.append(row)
+    return {"workload": "const2d (Table 4 shape)", "precision": "mixed", "rows": rows}
+
+
 def run_ours(args):
     rank, world, local = rank_env()
     if world > 1:
@@ -501,6 +586,14 @@ def run_ours(args):
     if world == 1 and not args.no_layered:
         layered = run_layered(helm, torch, stream, args)
 
+    robin = None
+    if world == 1 and not args.no_robin:
+        robin = run_robin_table4(helm, torch, stream, args)
+
+    table3 = None
+    if world == 1 and not args.no_3d:
+        table3 = run_table3(helm, torch, stream, args)
+
     slab3d = None
     if world == 1 and not args.no_3d:
         from paper_1208_3956_gb300 import media
@@ -562,6 +655,10 @@ def run_ours(args):
             line["batched"] = batched
         if layered:
             line["layered4095"] = layered
+        if table3:
+            line["table3_3d"] = table3
+        if robin:
+            line["robin_table4"] = robin
         if slab3d:
             line["slab3d"] = slab3d
     if rank == 0 and not args.no_cpu_baseline:
@@ -593,6 +690,7 @@ def main():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched right-hand-side panels")
     ap.add_argument("--no-layered", action="store_true", help="skip the 4095^2 layered workload (64 sources)")
+    ap.add_argument("--no-robin", action="store_true", help="skip the Robin / PML transmission comparison")
     ap.add_argument("--only-3d", action="store_true",
                     help="run only the 3-D workload and print its object (a profiling case)")
     args = ap.parse_args()

@@ -69,6 +69,11 @@ typedef enum {
     HELM_PREC_MIXED = 1   /* complex64 factors and sweeps (FP32 accumulate), FP64 FGMRES */
 } helm_prec;
 
+typedef enum {
+    HELM_TRANSMISSION_PML = 0,    /* added PML layers, single-layer transfers (Section 2.1)  */
+    HELM_TRANSMISSION_ROBIN = 1   /* Robin transmission conditions (Section 4.4)           */
+} helm_transmission;
+
 typedef struct {
     int iters;        /* Arnoldi steps (= preconditioner applications in the Krylov loop) */
     double rel_res;   /* true final ||f - A u||_2 / ||f||_2 over the padded grid           */
@@ -112,13 +117,27 @@ helm_status helm_dd_set_sep_groups(helm_dd* h, int G);
 /* G in use after helm_dd_factor (0 before). */
 int helm_dd_sep_groups(const helm_dd* h);
 
-/* Right-hand sides per internal panel of helm_dd_solve and helm_dd_gradient (the
- * batching of Section 4's many-source runs, not the paper's own parameter): a
- * call with more right-hand sides runs them panel after panel, so that the
- * Krylov basis (2 restart + 2 complex128 fields per right-hand side) and the
- * sweep buffers are held for one panel only.  0 (the default) takes as many as
- * the free device memory holds.  Results do not depend on the panel width. */
+/* Most right-hand sides per internal panel of helm_dd_solve, helm_dd_solve_reduced
+ * and helm_dd_gradient (the batching of many-source runs, not the paper's own
+ * parameter): a call with more right-hand sides runs them panel after panel, so
+ * that the Krylov basis (2 restart + 2 complex128 fields per right-hand side in
+ * the full space) and the sweep buffers are held for one panel only.  A panel is
+ * never wider than the free device memory holds; 0 (the default) sets no other
+ * cap.  Results do not depend on the panel width beyond rounding. */
 helm_status helm_dd_set_panel(helm_dd* h, int nrhs);
+
+/* Transmission condition of the double sweep (before helm_dd_factor; default PML).
+ * HELM_TRANSMISSION_ROBIN is the comparison method of Section 4.4: the strips keep
+ * their physical columns beta_{j-1}+1 .. beta_j+1 (an overlap of one column) but
+ * carry no added PML (w_sub is ignored); at the half point beyond an internal
+ * boundary column the condition -+d_x u + ik u = data holds, discretised as
+ * a u_in + b u_out with a = 1/h + ik/2, b = -1/h + ik/2 (d_x u one-sided over the
+ * half point, u the mean of the two values, k at the boundary column), the ghost
+ * value eliminated into the strip operator.  The right sweep passes
+ * d_x v^(j-1) + ik v^(j-1) at l^(j), the left sweep (on the residual g)
+ * -d_x w^(j+1) + ik w^(j+1) at r^(j); the outer PML stays on the outer boundary.
+ * 2-D grids only (helm_dd_factor returns HELM_EINVAL in 3-D). */
+helm_status helm_dd_set_transmission(helm_dd* h, helm_transmission t);
 
 /* Algorithm 1 (preparation): assemble every strip operator A^(j) on the grid of
  * Eq. grid_A_j (physical columns beta_{j-1}+1 .. beta_j+1 plus w_sub added PML

@@ -142,6 +142,11 @@ struct Geom {
     const double2* stc_y;
     const double2* stc_z;
     int fx0, fx1, fy0, fy1, fz0, fz1;
+    // Robin transmission (Section 4.4; null with PML transmission): rab[j * Ny + k] = a/b
+    // of the discrete Robin condition on row k next to padded column beta_j + 1, the
+    // boundary column shared by strip j (its first) and strip j-1 (its last), j = 1..J-1;
+    // a = 1/h + ik/2, b = -1/h + ik/2
+    const double2* rab;
 };
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }

@@ -60,7 +60,9 @@ struct helm_dd {
     int64_t N[3] = {1, 1, 1};
     double h = 1.0, omega = 1.0, c_ref = 0.0;
     int w_outer = 0, w_sub = 0, J = 1, P_req = 0, G_req = 0;
-    int panel = 0;   // right-hand sides per internal panel of solve / gradient (0: as many as fit)
+    int panel = 0;   // most right-hand sides per internal panel of solve / gradient (0: as many as fit)
+    int transmission = HELM_TRANSMISSION_PML;
+    double2* d_rab = nullptr;   // Robin a/b per interface and row ([J][Ny]), Robin transmission only
     helm_prec prec = HELM_PREC_FP64;
     std::vector<double> c;
     // geometry
@@ -173,8 +175,10 @@ void build_geometry(helm_dd* h) {
         s.j = j;
         s.lo = h->beta[j] + 1;
         s.hi = (j < h->J - 1) ? h->beta[j + 1] + 1 : Nx - 1;
-        s.lpml = j > 0 ? h->w_sub : 0;
-        s.rpml = j < h->J - 1 ? h->w_sub : 0;
+        // Robin transmission (Section 4.4): no added layers, the same physical columns
+        const bool robin = h->transmission == HELM_TRANSMISSION_ROBIN;
+        s.lpml = j > 0 && !robin ? h->w_sub : 0;
+        s.rpml = j < h->J - 1 && !robin ? h->w_sub : 0;
         s.W = s.lpml + (s.hi - s.lo + 1) + s.rpml;
         h->Wmax = std::max(h->Wmax, s.W);
     }
@@ -462,6 +466,27 @@ helm_status prepare_geom(helm_dd* h) {
     if (!h->icols.empty())
         CK(h, cudaMemcpyAsync(h->d_icols, h->icols.data(), h->icols.size() * sizeof(int), cudaMemcpyHostToDevice,
                               h->stream));
+    // Robin coefficients a/b per interface j and row (k^2 = omega^2 / c^2 as k_k2 forms it)
+    if (h->d_rab) cudaFree(h->d_rab);
+    h->d_rab = nullptr;
+    if (h->transmission == HELM_TRANSMISSION_ROBIN && h->dim == 2) {
+        std::vector<double2> rab((size_t)h->J * Ny, make_double2(0.0, 0.0));
+        const int nx = (int)h->n[0], ny = (int)h->n[1], wo = h->w_outer;
+        const double om2 = h->omega * h->omega;
+        for (int j = 1; j < h->J; ++j) {
+            const int col = h->beta[j] + 1;
+            const int xi = std::min(std::max(col - wo, 0), nx - 1);
+            for (int y = 0; y < Ny; ++y) {
+                const int yi = std::min(std::max(y - wo, 0), ny - 1);
+                const double cv = h->c[(size_t)yi * nx + xi];
+                const double k = sqrt(om2 / (cv * cv));
+                const cd a(1.0 / h->h, 0.5 * k), b(-1.0 / h->h, 0.5 * k);
+                rab[(size_t)j * Ny + y] = to_d2h(a / b);
+            }
+        }
+        CK(h, cudaMalloc(&h->d_rab, rab.size() * sizeof(double2)));
+        CK(h, cudaMemcpyAsync(h->d_rab, rab.data(), rab.size() * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    }
     Geom& g = h->geom;
     g.dim = h->dim;
     g.Nx = (int)h->N[0];
@@ -487,6 +512,7 @@ helm_status prepare_geom(helm_dd* h) {
     g.fx0 = frange[0][0]; g.fx1 = frange[0][1];
     g.fy0 = frange[1][0]; g.fy1 = frange[1][1];
     g.fz0 = frange[2][0]; g.fz1 = frange[2][1];
+    g.rab = h->d_rab;
     g.strips = h->d_strips;
     g.cmeta = reinterpret_cast<const int4*>(h->d_ints);
     g.r0 = h->d_ints + 8 * h->P;
@@ -701,6 +727,15 @@ helm_status helm_dd_set_panel(helm_dd* h, int nrhs) {
     return HELM_OK;
 }
 
+helm_status helm_dd_set_transmission(helm_dd* h, helm_transmission t) {
+    if (!h || (t != HELM_TRANSMISSION_PML && t != HELM_TRANSMISSION_ROBIN)) return HELM_EINVAL;
+    if (h->factored) return fail(h, HELM_ESTATE, "set_transmission after factor");
+    h->transmission = t;
+    build_geometry(h);
+    h->prepared = false;
+    return HELM_OK;
+}
+
 helm_status helm_dd_set_stream(helm_dd* h, void* stream) {
     if (!h) return HELM_EINVAL;
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;   // null until first device use
@@ -731,6 +766,8 @@ int helm_dd_kernel_stats(helm_dd* h, char (*names)[48], int64_t* launches, doubl
 
 helm_status helm_dd_factor(helm_dd* h) {
     if (!h) return HELM_EINVAL;
+    if (h->dim == 3 && h->transmission == HELM_TRANSMISSION_ROBIN)
+        return fail(h, HELM_EINVAL, "Robin transmission is implemented for 2-D grids");
     helm_status ps = prepare_geom(h);
     if (ps != HELM_OK) return ps;
     if (h->dim == 3) return factor_slabs(h);
@@ -862,13 +899,13 @@ void release_if_short(helm_dd* h, size_t need) {
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_red}) ws_free(*w);
 }
 
-// Right-hand sides per internal panel of a solve or gradient: the handle's setting, or
-// as many as the free device memory holds.  Per right-hand side a panel needs the
+// Right-hand sides per internal panel of a solve or gradient: as many as the free device
+// memory holds, at most the handle's setting.  Per right-hand side a panel needs the
 // FGMRES basis V_0..V_m, Z_0..Z_{m-1} and W (2m+2 fields), the preconditioner's
 // forward field and residual (2 fields), `extra` fields of the caller and the
 // strip chain solutions; the workspaces the handle already holds count as free.
 int panel_width(helm_dd* h, int nrhs, int m, int extra) {
-    if (h->panel > 0) return std::min(h->panel, nrhs);
+    if (h->panel > 0) nrhs = std::min(h->panel, nrhs);   // the caller's cap
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return nrhs; }
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_grad}) fr += w->bytes;
@@ -941,6 +978,11 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         sp.pdir = 0;
         sp.t0 = beta[j];
         sp.tcoef = -ih2;
+        if (h->d_rab && j > 0) {   // Robin data d_x v + ik v at l^(j) (Section 4.4)
+            sp.tcoef = ih2;
+            sp.rbk = h->d_rab + (int64_t)j * Ny;
+            sp.rb_in = 1;
+        }
         CK(h, strip_solve(j, sp));
         if ((j + 1) % kOutBatch == 0 || j == J - 1)
             CK(h, outputs(0, j + 1 - ((j % kOutBatch) + 1), (j % kOutBatch) + 1, (J == 1) ? out : V, nullptr,
@@ -961,6 +1003,10 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         sp.pdir = 1;
         sp.t0 = beta[j + 1] + 1;
         sp.tcoef = ih2;
+        if (h->d_rab && sp.prev >= 0) {   // Robin data -d_x w + ik w at r^(j)
+            sp.rbk = h->d_rab + (int64_t)(j + 1) * Ny;
+            sp.rb_in = 0;
+        }
         CK(h, strip_solve(j, sp));
         const int done = J - 1 - j;   // strips solved so far in this sweep: j .. J-2
         if (done % kOutBatch == 0 || j == 0) CK(h, outputs(1, j, (done - 1) % kOutBatch + 1, out, V, j == 0));
@@ -1560,10 +1606,11 @@ helm_status unstage_out(helm_dd* h, double* p, const double2* dev, size_t bytes)
     return HELM_OK;
 }
 
-// Right-hand sides per panel of the reduced solve: per right-hand side four full fields
+// Right-hand sides per panel of the reduced solve (at most the handle's setting): per
+// right-hand side four full fields
 // of its own, the preconditioner's two, the strip chain solutions, and m+4 reduced vectors.
 int panel_width_reduced(helm_dd* h, int nrhs, int m) {
-    if (h->panel > 0) return std::min(h->panel, nrhs);
+    if (h->panel > 0) nrhs = std::min(h->panel, nrhs);   // the caller's cap
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return nrhs; }
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_kry, &h->ws_small, &h->ws_red}) fr += w->bytes;
@@ -1861,6 +1908,7 @@ void helm_dd_destroy(helm_dd* h) {
     cudaFree(h->d_slab_sxz);
     cudaFree(h->d_counters);
     cudaFree(h->d_icols);
+    cudaFree(h->d_rab);
     for (auto* w : {&h->ws_V, &h->ws_G, &h->ws_Y, &h->ws_parts, &h->ws_io_in, &h->ws_io_out, &h->ws_io_aux,
                     &h->ws_kry, &h->ws_small, &h->ws_grad, &h->ws_red})
         ws_free(*w);

@@ -100,6 +100,11 @@ struct SweepStep {
     int pdir;               // that strip's transfer columns: 0 forward (its right end), 1 backward (its left end)
     int t0;                 // first padded column receiving the transfer
     double tcoef;           // transfer coefficient (-1/h^2 forward, +1/h^2 backward)
+    // Robin transmission (Section 4.4): the transfer is tcoef (rbk[k] x_in + x_out) with
+    // x_in = x(to[rb_in]) (the receiving strip's boundary column) and x_out the other
+    // transfer column; null for the PML transfer tcoef (x(to1) - x(to0))
+    const double2* rbk;
+    int rb_in;
 };
 
 struct SweepWork {

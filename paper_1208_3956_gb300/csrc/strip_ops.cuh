@@ -12,6 +12,8 @@
 //   D_k(c,c)   = s_y(k)[a_x(c+1/2) + a_x(c-1/2)]/h^2 + s_x(c)[a_y(k+1/2) + a_y(k-1/2)]/h^2
 //                - s_x(c) s_y(k) k^2(c,k)
 //   D_k(c,c+1) = D_k(c+1,c) = -s_y(k) a_x(c+1/2)/h^2
+// With Robin transmission the strips carry no added layers and the diagonal of an
+// internal boundary column gains s_x s_y (a/b)/h^2 (Geom::rab).
 #pragma once
 
 #include "common.cuh"
@@ -45,7 +47,15 @@ __device__ __forceinline__ double2 strip_diag(const Geom& g, const StripDev& st,
     double2 ys = cadd(g.gy_half[k + 1], g.gy_half[k]);
     double2 d = cscale(cadd(cmul(sy, xs), cmul(sx, ys)), g.inv_h2);
     double k2 = g.k2[(int64_t)k * g.Nx + strip_k2_col(st, c)];
-    return csub(d, cscale(cmul(sx, sy), k2));
+    d = csub(d, cscale(cmul(sx, sy), k2));
+    if (g.rab) {
+        // Robin rows (Section 4.4): the ghost value beyond an internal boundary column,
+        // eliminated through a u_in + b u_ghost = data, adds (a/b)/h^2 to the diagonal
+        if (c == 0 && st.j > 0) d = cadd(d, cscale(cmul(cmul(sx, sy), g.rab[(int64_t)st.j * g.Ny + k]), g.inv_h2));
+        if (c == st.W - 1 && st.j < g.J - 1)
+            d = cadd(d, cscale(cmul(cmul(sx, sy), g.rab[(int64_t)(st.j + 1) * g.Ny + k]), g.inv_h2));
+    }
+    return d;
 }
 __device__ __forceinline__ double2 strip_offdiag(const Geom& g, const StripDev& st, int k, int c) {
     // entry (c, c+1) = (c+1, c)

@@ -585,12 +585,19 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             }
             asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");
             // tcoef (x[to1] - x[to0]) enters this strip on columns t0, t0+1 (Eqs. solve_upward,
-            // solve_downward), scaled to the symmetric form like the source
+            // solve_downward), scaled to the symmetric form like the source; with Robin
+            // transmission (Section 4.4) the Robin data enters the one boundary column
             for (int o = tid; o < nrow * nb * 2; o += ptid) {
                 const int i = o & 1, b = (o >> 1) % nb, r = (o >> 1) / nb;
                 const int c = A.sp.t0 + i - cofs;
                 if (c < 0 || c >= W) continue;
-                const C tv = csub(xt[(r * BT + b) * 2 + 1], xt[(r * BT + b) * 2]);
+                C tv;
+                if (A.sp.rbk) {   // Robin data a x_in + b x_out, over b h^2 (tcoef = 1/h^2)
+                    const C w = CT<C>::from(A.sp.rbk[r0 + r]);
+                    tv = cadd(cmul(w, xt[(r * BT + b) * 2 + A.sp.rb_in]), xt[(r * BT + b) * 2 + 1 - A.sp.rb_in]);
+                } else {
+                    tv = csub(xt[(r * BT + b) * 2 + 1], xt[(r * BT + b) * 2]);
+                }
                 const C add = cmul(cscale(tv, (R)A.sp.tcoef), cmul(ct[A.st.ctab + c], ct[A.g.ct_sy + r0 + r]));
                 const C* cur = r < m ? &zb[(r * BT + b) * W + c] : &rsep[b * 64 + c];
                 put(r, b, c, cadd(*cur, add));

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "helm_dd.h")
 STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ECUDA", -4: "HELM_ESTATE",
           -5: "HELM_ENOTCONV", -6: "HELM_ENUMERIC", -7: "HELM_ETIMEOUT"}
 PREC = {"fp64": 0, "mixed": 1}
+TRANSMISSION = {"pml": 0, "robin": 1}
 
 
 class HelmError(RuntimeError):
@@ -55,6 +56,7 @@ def load() -> ctypes.CDLL:
         "helm_dd_set_sep_groups": (I, [P, I]),
         "helm_dd_sep_groups": (I, [P]),
         "helm_dd_set_panel": (I, [P, I]),
+        "helm_dd_set_transmission": (I, [P, I]),
         "helm_dd_factor": (I, [P]),
         "helm_dd_apply_precond": (I, [P, P, P, I]),
         "helm_dd_apply_precond_noalloc": (I, [P, P, P, I]),
@@ -120,11 +122,13 @@ class HelmDD:
     omega: angular frequency; w_outer / w_sub: outer and added PML widths;
     J: strips along x; precision: "fp64" or "mixed"; c_ref: speed fixing the
     PML strength (default max c); chunks: y-partition count (0 = built-in);
-    sep_groups: groups of the separator system (0 = built-in, 1 = one chain).
+    sep_groups: groups of the separator system (0 = built-in, 1 = one chain);
+    panel: most right-hand sides per internal panel (0 = as many as fit);
+    transmission: "pml" (Section 2.1) or "robin" (Section 4.4).
     """
 
     def __init__(self, c, h, omega, w_outer, w_sub, J, precision="mixed", c_ref=None, chunks=0,
-                 sep_groups=0, panel=0):
+                 sep_groups=0, panel=0, transmission="pml"):
         self.lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.dim = c.ndim
@@ -152,6 +156,8 @@ class HelmDD:
             self._check(self.lib.helm_dd_set_sep_groups(self._h, int(sep_groups)))
         if panel:
             self._check(self.lib.helm_dd_set_panel(self._h, int(panel)))
+        if transmission != "pml":
+            self._check(self.lib.helm_dd_set_transmission(self._h, TRANSMISSION[transmission]))
         N = (ctypes.c_int64 * 3)()
         self.lib.helm_dd_dims(self._h, N)
         self.N = tuple(int(N[a]) for a in range(self.dim))

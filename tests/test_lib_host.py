@@ -110,3 +110,14 @@ def test_interface_lines_match_oracle(lib, name):
         ref += [beta[j] + 1, beta[j] + 2]
     assert s.interface_lines() == ref
     s.close()
+
+
+def test_robin_strip_geometry_matches_oracle(lib):
+    """Robin transmission (Section 4.4): the same physical columns, no added layers."""
+    n, J = (61, 45), 4
+    c = np.ones(tuple(reversed(n)))
+    s = helm.HelmDD(c, 1.0 / 32, 10.0, 6, 5, J, "mixed", transmission="robin")
+    o = HelmholtzDD(c, 1.0 / 32, 10.0, 6, 5, J, transmission="robin")
+    assert s.strip_widths() == [st.W for st in o.strips]
+    assert s.strip_widths() == [st.hi - st.lo + 1 for st in o.strips]
+    s.close()
