@@ -184,7 +184,8 @@ class HelmholtzDD:
     """Discrete problem plus the double-sweep preconditioner (Sections 2.1-2.3)."""
 
     def __init__(self, c: np.ndarray, h: float, omega: float, w_outer: int,
-                 w_sub: int, J: int, c_ref: float | None = None, transmission: str = "pml"):
+                 w_sub: int, J: int, c_ref: float | None = None, transmission: str = "pml",
+                 sweep: str = "double"):
         c = np.asarray(c, dtype=float)
         if not np.all(np.isfinite(c)) or np.any(c <= 0):
             raise ValueError("speed must be positive and finite")
@@ -198,6 +199,9 @@ class HelmholtzDD:
         if transmission not in ("pml", "robin"):
             raise ValueError("transmission is 'pml' or 'robin'")
         self.transmission = transmission
+        if sweep not in ("double", "concurrent") or (sweep == "concurrent" and transmission != "pml"):
+            raise ValueError("sweep is 'double' or 'concurrent' (the latter with PML transmission)")
+        self.sweep = sweep
         self.N = tuple(k + 2 * self.w_outer for k in self.n)
         # c_ref fixes the PML strength; by default the maximum of the medium
         self.c_max = float(c.max()) if c_ref is None else float(c_ref)
@@ -341,6 +345,8 @@ class HelmholtzDD:
         """P f = v + w: forward sweep, residual, backward sweep, compose."""
         if self.transmission == "robin":
             return self.apply_precond_robin(f, return_parts)
+        if self.sweep == "concurrent":
+            return self.apply_precond_concurrent(f)
         f = np.asarray(f, dtype=complex)
         J, h = self.J, self.h
         beta = self.beta
@@ -385,6 +391,74 @@ class HelmholtzDD:
         if return_parts:
             return v + w, v, g, w
         return v + w
+
+    def _transfer_up(self, j: int, v_prev: np.ndarray, r: np.ndarray):
+        """Add -2 delta(x - b_j) d_x v^(j-1) (Eq. solve_upward) to strip j's right-hand side r."""
+        st, pst, h, b = self.strips[j], self.strips[j - 1], self.h, self.beta[j]
+        dv = (v_prev[..., pst.local(b + 1)] - v_prev[..., pst.local(b)]) / h
+        t = -2.0 * (1.0 / (2.0 * h)) * dv
+        r[..., st.local(b)] += t
+        r[..., st.local(b + 1)] += t
+
+    def _transfer_down(self, j: int, w_next: np.ndarray, r: np.ndarray):
+        """Add +2 delta(x - b~_{j+1}) d_x w^(j+1) (Eq. solve_downward) to strip j's r."""
+        st, nst, h, b = self.strips[j], self.strips[j + 1], self.h, self.beta[j + 1]
+        dw = (w_next[..., nst.local(b + 2)] - w_next[..., nst.local(b + 1)]) / h
+        t = 2.0 * (1.0 / (2.0 * h)) * dw
+        r[..., st.local(b + 1)] += t
+        r[..., st.local(b + 2)] += t
+
+    def apply_precond_concurrent(self, f: np.ndarray):
+        """The upward and downward sequences of solves performed simultaneously (Section 1.2,
+        "Results"; Section 3.1 in 1-D: at step n only the n-th and the (J+1-n)-th subdomain
+        are updated).  Reading for the PML transfer, which passes one-way fields only:
+
+        * upward, j = 1..J-1: v^(j) from f on D^(j) and -2 delta(x-b_{j-1}) d_x v^(j-1)
+          (Eq. solve_upward) -- the field of the sources left of b_j;
+        * downward, j = J..2: y^(j) from f on D~^(j) and +2 delta(x-b~_j) d_x y^(j+1)
+          (Eq. solve_downward with f in place of g) -- the field of the sources right of
+          b~_{j-1};
+        the two sequences are independent; where they have crossed, strip j's total field
+        u^(j) solves A^(j) u^(j) = f on its physical columns beta_{j-1}+1 .. beta_j+1 plus
+        both transfers, from v^(j-1) and from y^(j+1); P f = u^(j) on D^(j).  With perfect
+        PML layers (Theorem 1's setting) this is A^{-1} f, as the double sweep is.
+        """
+        f = np.asarray(f, dtype=complex)
+        J, beta = self.J, self.beta
+        v = [None] * J
+        y = [None] * J
+        for j in range(J - 1):                              # upward sequence
+            st = self.strips[j]
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            core = np.arange(beta[j] + 1, beta[j + 1] + 1)
+            r[..., core - st.lo + st.lpml] = f[..., core]
+            if j > 0:
+                self._transfer_up(j, v[j - 1], r)
+            v[j] = self.strip_solve(j, r)
+        for j in range(J - 1, 0, -1):                       # downward sequence on f
+            st = self.strips[j]
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            lo_t = beta[j] + 2
+            hi_t = beta[j + 1] + 1 if j < J - 1 else self.N[0] - 1
+            dt = np.arange(lo_t, hi_t + 1)
+            r[..., dt - st.lo + st.lpml] = f[..., dt]
+            if j < J - 1:
+                self._transfer_down(j, y[j + 1], r)
+            y[j] = self.strip_solve(j, r)
+        u = np.zeros_like(f)
+        for j in range(J):                                  # total fields
+            st = self.strips[j]
+            r = np.zeros(f.shape[:-1] + (st.W,), dtype=complex)
+            phys = np.arange(st.lo, st.hi + 1)
+            r[..., phys - st.lo + st.lpml] = f[..., phys]
+            if j > 0:
+                self._transfer_up(j, v[j - 1], r)
+            if j < J - 1:
+                self._transfer_down(j, y[j + 1], r)
+            uj = self.strip_solve(j, r)
+            core = np.arange(beta[j] + 1, beta[j + 1] + 1)
+            u[..., core] = uj[..., core - st.lo + st.lpml]
+        return u
 
     def apply_precond_robin(self, f: np.ndarray, return_parts: bool = False):
         """The double sweep with Robin transmission conditions (Section 4.4).
