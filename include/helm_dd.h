@@ -74,6 +74,11 @@ typedef enum {
     HELM_TRANSMISSION_ROBIN = 1   /* Robin transmission conditions (Section 4.4)           */
 } helm_transmission;
 
+typedef enum {
+    HELM_SWEEP_DOUBLE = 0,        /* forward sweep, residual, backward sweep (Section 2.1)   */
+    HELM_SWEEP_CONCURRENT = 1     /* upward and downward sequences at once (Sections 1.2, 3.1) */
+} helm_sweep;
+
 typedef struct {
     int iters;        /* Arnoldi steps (= preconditioner applications in the Krylov loop) */
     double rel_res;   /* true final ||f - A u||_2 / ||f||_2 over the padded grid           */
@@ -125,6 +130,19 @@ int helm_dd_sep_groups(const helm_dd* h);
  * never wider than the free device memory holds; 0 (the default) sets no other
  * cap.  Results do not depend on the panel width beyond rounding. */
 helm_status helm_dd_set_panel(helm_dd* h, int nrhs);
+
+/* Order of the strip solves of P (before helm_dd_factor; default HELM_SWEEP_DOUBLE).
+ * HELM_SWEEP_CONCURRENT performs the upward and downward sequences simultaneously
+ * (Section 1.2, "Results"; Section 3.1 states it for 1-D): an upward sequence v^(j)
+ * on f (Eq. solve_upward) and a downward sequence y^(j) on f (Eq. solve_downward with
+ * f in place of the residual g) run side by side on three streams; strip j's total
+ * field u^(j) -- f on its physical columns plus the transfers from v^(j-1) and
+ * y^(j+1) -- is v^(j) plus one more strip solve, and P f = u^(j) on D^(j).  It is
+ * exact with perfect layers, like the double sweep, has about half its sequential
+ * depth (J strip solves against 2J-1) and 3J-2 solves in all; the built-in chunk
+ * count is capped at a third of the SMs so that three strip solves fit side by side.
+ * PML transmission and 2-D grids only (HELM_EINVAL otherwise). */
+helm_status helm_dd_set_sweep(helm_dd* h, helm_sweep mode);
 
 /* Transmission condition of the double sweep (before helm_dd_factor; default PML).
  * HELM_TRANSMISSION_ROBIN is the comparison method of Section 4.4: the strips keep

@@ -62,6 +62,12 @@ struct helm_dd {
     int w_outer = 0, w_sub = 0, J = 1, P_req = 0, G_req = 0;
     int panel = 0;   // most right-hand sides per internal panel of solve / gradient (0: as many as fit)
     int transmission = HELM_TRANSMISSION_PML;
+    int sweep = HELM_SWEEP_DOUBLE;
+    int nsm = 0;                        // SMs of the device (chunk count of concurrent sweeps)
+    // concurrent sweeps: the downward sequence and the total-field corrections run on two
+    // more streams, ordered by events
+    cudaStream_t cstream[2] = {nullptr, nullptr};
+    cudaEvent_t cev[4] = {nullptr, nullptr, nullptr, nullptr};
     double2* d_rab = nullptr;   // Robin a/b per interface and row ([J][Ny]), Robin transmission only
     helm_prec prec = HELM_PREC_FP64;
     std::vector<double> c;
@@ -233,6 +239,8 @@ void chunk_layout(helm_dd* h) {
     // factor 0.93 (fewer, longer chunks) is the measured optimum on a 1055-row grid,
     // where the chunk steps are slightly cheaper than the separator steps.
     int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(0.93 * pow((double)Ny, 2.0 / 3.0)));
+    // concurrent sweeps run three strip solves side by side (one CTA per chunk and SM)
+    if (h->P_req == 0 && h->sweep == HELM_SWEEP_CONCURRENT && h->nsm >= 3) P = std::min(P, h->nsm / 3);
     P = std::min(P, (Ny + 1) / 2);
     h->P = std::max(P, 1);
     const int rows = Ny - (h->P - 1);
@@ -277,7 +285,10 @@ void chunk_layout(helm_dd* h) {
 // starts 16-byte aligned for bulk copies.
 int work_stride(const helm_dd* h) { return (h->Wmax + 1) & ~1; }
 
-size_t counter_bytes(const helm_dd* h) { return (size_t)kMaxTiles * (h->G + 1) * sizeof(int); }
+// one set per stream that runs strip solves (three for concurrent sweeps)
+int sweep_streams(const helm_dd* h) { return h->sweep == HELM_SWEEP_CONCURRENT ? 3 : 1; }
+size_t counter_set_bytes(const helm_dd* h) { return (size_t)kMaxTiles * (h->G + 1) * sizeof(int); }
+size_t counter_bytes(const helm_dd* h) { return counter_set_bytes(h) * sweep_streams(h); }
 
 double2 to_d2h(cd v) { return make_double2(v.real(), v.imag()); }
 
@@ -330,6 +341,15 @@ helm_status ensure_device(helm_dd* h) {
     if (h->dev_ready) return HELM_OK;
     if (!h->own_stream) CK(h, cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
     if (!h->stream) h->stream = h->own_stream;
+    {
+        int dev = 0;
+        CK(h, cudaGetDevice(&dev));
+        CK(h, cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    for (auto& cs : h->cstream)
+        if (!cs) CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (auto& ev : h->cev)
+        if (!ev) CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     if (!h->side) {
         int lo = 0, hi = 0;
         CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));   // lo: the lowest priority
@@ -727,9 +747,21 @@ helm_status helm_dd_set_panel(helm_dd* h, int nrhs) {
     return HELM_OK;
 }
 
+helm_status helm_dd_set_sweep(helm_dd* h, helm_sweep mode) {
+    if (!h || (mode != HELM_SWEEP_DOUBLE && mode != HELM_SWEEP_CONCURRENT)) return HELM_EINVAL;
+    if (h->factored) return fail(h, HELM_ESTATE, "set_sweep after factor");
+    if (mode == HELM_SWEEP_CONCURRENT && h->transmission != HELM_TRANSMISSION_PML)
+        return fail(h, HELM_EINVAL, "concurrent sweeps use PML transmission");
+    h->sweep = mode;
+    h->prepared = false;
+    return HELM_OK;
+}
+
 helm_status helm_dd_set_transmission(helm_dd* h, helm_transmission t) {
     if (!h || (t != HELM_TRANSMISSION_PML && t != HELM_TRANSMISSION_ROBIN)) return HELM_EINVAL;
     if (h->factored) return fail(h, HELM_ESTATE, "set_transmission after factor");
+    if (t != HELM_TRANSMISSION_PML && h->sweep == HELM_SWEEP_CONCURRENT)
+        return fail(h, HELM_EINVAL, "concurrent sweeps use PML transmission");
     h->transmission = t;
     build_geometry(h);
     h->prepared = false;
@@ -768,6 +800,8 @@ helm_status helm_dd_factor(helm_dd* h) {
     if (!h) return HELM_EINVAL;
     if (h->dim == 3 && h->transmission == HELM_TRANSMISSION_ROBIN)
         return fail(h, HELM_EINVAL, "Robin transmission is implemented for 2-D grids");
+    if (h->dim == 3 && h->sweep == HELM_SWEEP_CONCURRENT)
+        return fail(h, HELM_EINVAL, "concurrent sweeps are implemented for 2-D grids");
     helm_status ps = prepare_geom(h);
     if (ps != HELM_OK) return ps;
     if (h->dim == 3) return factor_slabs(h);
@@ -863,8 +897,10 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
     const int Ny = (int)h->N[1];
     sz[0] = (size_t)B * NV * sizeof(double2);
     sz[1] = sz[0];
-    sz[2] = (size_t)h->J * B * Ny * work_stride(h) * h->esize;
-    sz[3] = (size_t)B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
+    // concurrent sweeps keep three sets of chain solutions (upward, downward, corrections)
+    // and one separator-parts buffer per stream
+    sz[2] = (size_t)sweep_streams(h) * h->J * B * Ny * work_stride(h) * h->esize;
+    sz[3] = (size_t)sweep_streams(h) * B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
     if (h->dim == 3) {   // right-hand sides and two strip solutions, [B][Ny][slab_ld] each
         sz[2] = (size_t)3 * B * Ny * h->slab_ld * h->esize;
         sz[3] = 256;
@@ -873,6 +909,7 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
 helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
+helm_status run_precond_concurrent(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
 
 // P applied to B device fields (Section 2.1): in -> out (distinct buffers).
 helm_status dev_precond(helm_dd* h, const double2* in, double2* out, int B) {
@@ -922,6 +959,7 @@ int panel_width(helm_dd* h, int nrhs, int m, int extra) {
 // The double sweep itself on caller-provided buffers.
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf) {
     if (h->dim == 3) return run_precond_slabs(h, in, out, B, bf);
+    if (h->sweep == HELM_SWEEP_CONCURRENT && h->J > 1) return run_precond_concurrent(h, in, out, B, bf);
     const int Ny = (int)h->N[1], Nx = (int)h->N[0];
     helm_status s;
     if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
@@ -1070,6 +1108,113 @@ helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B
         CK(h, emit(j, 1, slot, out, V));
     }
     CK(h, launch_copy_cols(V, out, B, Nx, Ny, Nz, beta[J - 1] + 2, Nx - 1, h->stream, &h->timer));
+    return HELM_OK;
+}
+
+// The upward and downward sequences performed simultaneously (Section 1.2 "Results";
+// Section 3.1), PML transfers.  Three streams run strip solves side by side:
+//   upward (the handle's stream):  v^(j), j = 1..J, f on D^(j) + the transfer from v^(j-1);
+//   downward (cstream[0]):         y^(j), j = J..2, f on D~^(j) + the transfer from y^(j+1);
+//   corrections (cstream[1]):      s^(j), j = 1..J-1, f on the overlap column beta_j+1 +
+//                                  the transfer from y^(j+1), each once y^(j+1) is done.
+// Strip j's total field, A^(j) u^(j) = f on its physical columns + both transfers, is
+// v^(j) + s^(j) by linearity (u^(J) = v^(J)); out = u^(j) on D^(j).  Each stream has
+// its own separator-parts buffer and arrival counters.
+helm_status run_precond_concurrent(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf) {
+    const int Ny = (int)h->N[1], Nx = (int)h->N[0];
+    if (B > kMaxTiles) return fail(h, HELM_EINVAL, "too many right-hand sides in one call");
+    double2* V = bf.V;
+    const int ws = work_stride(h);
+    const int64_t ystride = (int64_t)B * Ny * ws;
+    const int J = h->J;
+    const auto& beta = h->beta;
+    const double ih2 = 1.0 / (h->h * h->h);
+    const bool mixed = h->prec == HELM_PREC_MIXED;
+    const size_t es = h->esize;
+    char* Yset[3] = {(char*)bf.Y, (char*)bf.Y + (size_t)J * ystride * es, (char*)bf.Y + (size_t)2 * J * ystride * es};
+    const size_t psz = (size_t)B * std::max(h->P - 1, 1) * 4 * ws * es;
+    void* parts[3] = {bf.parts, (char*)bf.parts + psz, (char*)bf.parts + 2 * psz};
+    const size_t cset = counter_set_bytes(h) / sizeof(int);
+    int* ctr[3] = {bf.counters, bf.counters + cset, bf.counters + 2 * cset};
+    cudaStream_t st[3] = {h->stream, h->cstream[0], h->cstream[1]};
+    auto ybuf = [&](int set, int j) { return Yset[set] + (size_t)j * ystride * es; };
+    // set: 0 upward, 1 downward, 2 corrections; the transfer comes from set `pset`
+    auto strip_solve = [&](int set, int j, const SweepStep& sp, int pset) -> cudaError_t {
+        SweepWork wk{ybuf(set, j), parts[set], ctr[set], h->d_status, ws, B, h->zrows,
+                     sp.prev >= 0 ? ybuf(pset, sp.prev) : nullptr};
+        wk.pdl = false;   // a pre-launched successor would hold SMs the other streams need
+        const StripDev* pst = sp.prev >= 0 ? &h->strips[sp.prev] : nullptr;
+        if (mixed)
+            return launch_strip_solve<float2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, st[set], &h->timer);
+        return launch_strip_solve<double2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, st[set], &h->timer);
+    };
+    auto outputs = [&](int set, int jlo, int n, double2* dst, const double2* base, int maxcta) -> cudaError_t {
+        if (n <= 0) return cudaSuccess;
+        OutArgs O{h->geom, 0, jlo, n, Yset[set], ystride, ws, B, B > 1 ? 4 : 1, dst, base, maxcta};
+        if (mixed) return launch_outputs<float2>(O, h->d_pool, h->side, &h->timer);
+        return launch_outputs<double2>(O, h->d_pool, h->side, &h->timer);
+    };
+    cudaEvent_t ev_fork = h->cev[0], ev_y = h->cev[1], ev_down = h->cev[2], ev_corr = h->cev[3];
+    // fork: the other two streams start once the input is ready on the handle's stream
+    CK(h, cudaEventRecord(ev_fork, st[0]));
+    CK(h, cudaStreamWaitEvent(st[1], ev_fork, 0));
+    CK(h, cudaStreamWaitEvent(st[2], ev_fork, 0));
+    const int kOutBatch = 8;
+    // Issue the three sequences interleaved in time order, so that each stream's next
+    // launch is queued while the others run.
+    for (int t = 0; t < J; ++t) {
+        {   // upward: v^(t)
+            const int j = t;
+            SweepStep sp{};
+            sp.src = in;
+            sp.mlo = beta[j] + 1;
+            sp.mhi = beta[j + 1];
+            sp.prev = j > 0 ? j - 1 : -1;
+            sp.pdir = 0;
+            sp.t0 = beta[j];
+            sp.tcoef = -ih2;
+            CK(h, strip_solve(0, j, sp, 0));
+            if ((j + 1) % kOutBatch == 0 || j == J - 1) {   // v on D^(j), beside the solves
+                CK(h, cudaEventRecord(h->ev_main, st[0]));
+                CK(h, cudaStreamWaitEvent(h->side, h->ev_main, 0));
+                const int n = (j % kOutBatch) + 1;
+                CK(h, outputs(0, j + 1 - n, n, V, nullptr, j == J - 1 ? 0 : 56));
+            }
+        }
+        const int j = J - 1 - t;   // downward: y^(j), j = J-1 .. 1; then the correction s^(j-1)
+        if (j >= 1) {
+            SweepStep sp{};
+            sp.src = in;
+            sp.mlo = beta[j] + 2;
+            sp.mhi = j < J - 1 ? beta[j + 1] + 1 : Nx - 1;
+            sp.prev = j < J - 1 ? j + 1 : -1;
+            sp.pdir = 1;
+            sp.t0 = beta[j + 1] + 1;
+            sp.tcoef = ih2;
+            CK(h, strip_solve(1, j, sp, 1));
+            CK(h, cudaEventRecord(ev_y, st[1]));
+            CK(h, cudaStreamWaitEvent(st[2], ev_y, 0));
+            SweepStep sc{};
+            sc.src = in;
+            sc.mlo = beta[j] + 1;   // strip j-1's overlap column
+            sc.mhi = beta[j] + 1;
+            sc.prev = j;
+            sc.pdir = 1;
+            sc.t0 = beta[j] + 1;
+            sc.tcoef = ih2;
+            CK(h, strip_solve(2, j - 1, sc, 1));
+        }
+    }
+    // out = v + s on D^(j), j < J-1 (after the v outputs on the side stream and every
+    // correction), and v on D^(J)
+    CK(h, cudaEventRecord(ev_corr, st[2]));
+    CK(h, cudaStreamWaitEvent(h->side, ev_corr, 0));
+    CK(h, outputs(2, 0, J - 1, out, V, 0));
+    CK(h, cudaEventRecord(ev_down, st[1]));
+    CK(h, cudaStreamWaitEvent(st[0], ev_down, 0));
+    CK(h, cudaEventRecord(h->ev_side, h->side));
+    CK(h, cudaStreamWaitEvent(st[0], h->ev_side, 0));
+    CK(h, launch_copy_cols(V, out, B, Nx, Ny, (int)h->N[2], beta[J - 1] + 1, Nx - 1, st[0], &h->timer));
     return HELM_OK;
 }
 
@@ -1915,6 +2060,8 @@ void helm_dd_destroy(helm_dd* h) {
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     if (h->ev_side) cudaEventDestroy(h->ev_side);
+    for (auto cs : h->cstream) if (cs) cudaStreamDestroy(cs);
+    for (auto ev : h->cev) if (ev) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     cudaGetLastError();
     delete h;

@@ -116,6 +116,9 @@ struct SweepWork {
     int B;
     int zrows;              // longest chain of one CTA (chunk rows, group size, G-1)
     const void* pybuf;      // the previous strip solve's chain solution (when SweepStep::prev >= 0)
+    // launch with programmatic stream serialisation (the next strip solve's CTAs stage their
+    // blocks while this one finishes); off where strip solves of several streams share the SMs
+    bool pdl = true;
 };
 
 // Output pass of a sweep (k_sweep_output) over strips jlo .. jlo+nstrip-1,

@@ -1160,7 +1160,7 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
     // consecutive strip solves with programmatic stream serialisation (see pdl_wait)
     cudaLaunchAttribute pdl[1];
     pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    pdl[0].val.programmaticStreamSerializationAllowed = wk.pdl ? 1 : 0;
     auto config = [&](dim3 grid, int nthr, size_t bytes) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;

@@ -21,6 +21,7 @@ STATUS = {0: "HELM_OK", -1: "HELM_EINVAL", -2: "HELM_ENOMEM", -3: "HELM_ECUDA", 
           -5: "HELM_ENOTCONV", -6: "HELM_ENUMERIC", -7: "HELM_ETIMEOUT"}
 PREC = {"fp64": 0, "mixed": 1}
 TRANSMISSION = {"pml": 0, "robin": 1}
+SWEEP = {"double": 0, "concurrent": 1}
 
 
 class HelmError(RuntimeError):
@@ -57,6 +58,7 @@ def load() -> ctypes.CDLL:
         "helm_dd_sep_groups": (I, [P]),
         "helm_dd_set_panel": (I, [P, I]),
         "helm_dd_set_transmission": (I, [P, I]),
+        "helm_dd_set_sweep": (I, [P, I]),
         "helm_dd_factor": (I, [P]),
         "helm_dd_apply_precond": (I, [P, P, P, I]),
         "helm_dd_apply_precond_noalloc": (I, [P, P, P, I]),
@@ -124,11 +126,12 @@ class HelmDD:
     PML strength (default max c); chunks: y-partition count (0 = built-in);
     sep_groups: groups of the separator system (0 = built-in, 1 = one chain);
     panel: most right-hand sides per internal panel (0 = as many as fit);
-    transmission: "pml" (Section 2.1) or "robin" (Section 4.4).
+    transmission: "pml" (Section 2.1) or "robin" (Section 4.4);
+    sweep: "double" (Section 2.1) or "concurrent" (upward and downward sequences at once).
     """
 
     def __init__(self, c, h, omega, w_outer, w_sub, J, precision="mixed", c_ref=None, chunks=0,
-                 sep_groups=0, panel=0, transmission="pml"):
+                 sep_groups=0, panel=0, transmission="pml", sweep="double"):
         self.lib = load()
         c = np.ascontiguousarray(c, dtype=np.float64)
         self.dim = c.ndim
@@ -158,6 +161,8 @@ class HelmDD:
             self._check(self.lib.helm_dd_set_panel(self._h, int(panel)))
         if transmission != "pml":
             self._check(self.lib.helm_dd_set_transmission(self._h, TRANSMISSION[transmission]))
+        if sweep != "double":
+            self._check(self.lib.helm_dd_set_sweep(self._h, SWEEP[sweep]))
         N = (ctypes.c_int64 * 3)()
         self.lib.helm_dd_dims(self._h, N)
         self.N = tuple(int(N[a]) for a in range(self.dim))
