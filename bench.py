@@ -7,10 +7,16 @@ device.  Metric: Mdof*RHS/s = padded unknowns x right-hand sides / solve time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
 
-With the mixed-precision sweep (default) the line also carries "fp64_sweep": the same
-solve with complex128 factors and sweep (FP64 GMRES), and the mixed / FP64 ratio; and, on
-one GPU, "slab3d": the 3-D workload (63^3 smooth random medium, padded 79^3, J = 8 slabs
-of dense W N_z blocks) with its own roofline for the slab strip-solve kernel.
+On one GPU the line also carries (each skippable with its --no-... flag):
+  fp64_sweep         the same solve with complex128 factors and sweep, and the ratio
+  batched            panels of 4, 16, 32 sources on the same handle
+  concurrent_sweeps  upward and downward sequences at once, against the double sweep
+  layered4095        the 4095^2 layered medium, 64 sources, reduced space (Algorithms 2-5)
+  gradient_blob1023  misfit and adjoint gradient, 32 sources, 256 receivers
+  const127           the small constant-medium case
+  robin_table4       Table 4: PML against Robin transmission, 99^2 .. 1599^2
+  table3_3d          Table 3 shape: iterations against w_sub on a 3-D constant cube
+  slab3d             the 63^3 smooth random medium (3-D slabs), 1 and 16 sources
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 
 Multi-GPU (torchrun, one process per GPU): every rank solves its own source
@@ -523,6 +529,79 @@ def run_concurrent(helm, torch, stream, wl, c, omega, f_dev, x_dev, t_p_double, 
     return out
 
 
+def run_gradient(helm, torch, stream, args):
+    """The misfit workload (blob1023: the smooth random medium times a seeded 10 % Gaussian
+    blob, 32 sources and 256 receivers on the top row): observed data from the background
+    medium (GPU solves at tol 1e-8), then the misfit 1/2 sum_s ||R u_s - d_s||^2 and its
+    adjoint gradient with respect to 1/c^2 at the blob model (helm_dd_gradient, forward and
+    adjoint solves of all 32 sources in panels, tol 1e-6), mixed precision, PML held at the
+    background's maximum speed.  Metric: gradients per second (factor excluded)."""
+    media = media_mod()
+    wl = media.WORKLOADS["blob1023"]
+    c0 = media.background_medium("blob1023")
+    c = media.medium("blob1023")
+    omega = media.omega_for(c0, wl.h, wl.ppw)
+    cref = float(c0.max())
+    src = [media.padded_index(p, wl.n, wl.w_outer) for p in media.source_positions("blob1023")]
+    rec = [media.padded_index(p, wl.n, wl.w_outer) for p in media.receiver_positions("blob1023")]
+    g0 = helm.HelmDD(c0, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref)
+    g0.set_stream(stream.cuda_stream)
+    g0.factor()
+    F = torch.zeros((len(src),) + g0.shape, dtype=torch.complex128, device="cuda")
+    Ff = F.view(len(src), -1)
+    for s_, i in enumerate(src):
+        Ff[s_, i] = 1.0 / wl.h ** 2
+    u0, _ = g0.solve(F, tol=1e-8)
+    d = u0.view(len(src), -1)[:, torch.as_tensor(rec, device="cuda")].cpu().numpy()
+    g0.close()
+    del F, u0
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref)
+    g.set_stream(stream.cuda_stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    g.factor()
+    ev[1].record()
+    g.gradient(src, rec, d, tol=1e-6)   # warm-up
+    ev[2].record()
+    J, grad = g.gradient(src, rec, d, tol=1e-6)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t = ev[2].elapsed_time(ev[3])
+    g.close()
+    return {"workload": "blob1023", "nsrc": len(src), "nrec": len(rec), "precision": "mixed", "tol": 1e-6,
+            "value": 1e3 / t, "unit": "gradients/s", "ms_per_gradient": t, "factor_ms": ev[0].elapsed_time(ev[1]),
+            "solves_per_gradient": 2 * len(src), "misfit": J, "grad_norm": float(np.linalg.norm(grad))}
+
+
+def run_const127(helm, torch, stream, args):
+    """The small constant-medium case (127^2 interior, J = 8, one centre source): solve time
+    and iterations in both precisions (it is L2-resident and latency-bound)."""
+    media = media_mod()
+    wl = media.WORKLOADS["const127"]
+    c = media.medium("const127")
+    omega = media.omega_for(c, wl.h, wl.ppw)
+    f = torch.as_tensor(media.point_sources(wl.n, wl.w_outer, wl.h, media.source_positions("const127")),
+                        device="cuda")
+    out = {"workload": "const127", "grid": "127x127 interior, 147x147 padded", "J": wl.J}
+    for prec in ("mixed", "fp64"):
+        g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, prec)
+        g.set_stream(stream.cuda_stream)
+        g.factor()
+        for _ in range(3):
+            g.solve(f, tol=1e-6)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(10):
+            _, info = g.solve(f, tol=1e-6)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 10
+        out[prec] = {"value": g.ndof / (t * 1e-3) / 1e6, "unit": "Mdof*RHS/s", "ms_per_solve": t,
+                     "iters": info[0]["iters"], "rel_res": info[0]["rel_res"]}
+        g.close()
+    return out
+
+
 def run_ours(args):
     rank, world, local = rank_env()
     if world > 1:
@@ -640,6 +719,11 @@ def run_ours(args):
     if world == 1 and not args.no_layered:
         layered = run_layered(helm, torch, stream, args)
 
+    gradient = None
+    if world == 1 and not args.no_gradient:
+        gradient = run_gradient(helm, torch, stream, args)
+    const127 = run_const127(helm, torch, stream, args) if world == 1 and not args.no_const127 else None
+
     robin = None
     if world == 1 and not args.no_robin:
         robin = run_robin_table4(helm, torch, stream, args)
@@ -715,6 +799,10 @@ def run_ours(args):
             line["table3_3d"] = table3
         if robin:
             line["robin_table4"] = robin
+        if gradient:
+            line["gradient_blob1023"] = gradient
+        if const127:
+            line["const127"] = const127
         if slab3d:
             line["slab3d"] = slab3d
     if rank == 0 and not args.no_cpu_baseline:
@@ -748,6 +836,8 @@ def main():
     ap.add_argument("--no-layered", action="store_true", help="skip the 4095^2 layered workload (64 sources)")
     ap.add_argument("--no-robin", action="store_true", help="skip the Robin / PML transmission comparison")
     ap.add_argument("--no-concurrent", action="store_true", help="skip the concurrent-sequence solve")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the 32-source misfit gradient")
+    ap.add_argument("--no-const127", action="store_true", help="skip the small constant-medium case")
     ap.add_argument("--only-3d", action="store_true",
                     help="run only the 3-D workload and print its object (a profiling case)")
     args = ap.parse_args()
