@@ -646,13 +646,25 @@ helm_status factor_slabs(helm_dd* h) {
     sc.pivrow = sc.pinv + nmax;
     sc.bar = (unsigned*)(sc.pivrow + nmax);
     cudaError_t e = cudaSuccess;
-    for (size_t jj = 0; jj < h->strips.size() && e == cudaSuccess; ++jj) {
-        if (h->prec == HELM_PREC_MIXED)
-            e = launch_slab_factor<float2>(h->geom, h->strips[jj], h->d_pool[0], sc, h->d_status, h->stream, &h->timer);
-        else
-            e = launch_slab_factor<double2>(h->geom, h->strips[jj], h->d_pool[0], sc, h->d_status, h->stream,
-                                            &h->timer);
+    if (h->prec == HELM_PREC_MIXED) {
+        // complex64: blocked Gauss-Jordan with tensor-core updates, up to 8 strips side by side
+        const int ns_max = 8;
+        void* tcs = nullptr;
+        const size_t tcb = slab_factor_tc_scratch(nmax, std::min<int>(ns_max, (int)h->strips.size()));
+        e = cudaMalloc(&tcs, tcb);
+        for (size_t j0 = 0; j0 < h->strips.size() && e == cudaSuccess; j0 += ns_max) {
+            const int ns = (int)std::min<size_t>(ns_max, h->strips.size() - j0);
+            e = launch_slab_factor_tc(h->geom, h->strips.data() + j0, ns, h->d_pool[0], tcs, h->d_status, h->stream,
+                                      &h->timer);
+        }
+        if (tcs) {
+            cudaError_t e2 = cudaStreamSynchronize(h->stream);
+            if (e == cudaSuccess) e = e2;
+            cudaFree(tcs);
+        }
     }
+    for (size_t jj = 0; jj < h->strips.size() && e == cudaSuccess && h->prec != HELM_PREC_MIXED; ++jj)
+        e = launch_slab_factor<double2>(h->geom, h->strips[jj], h->d_pool[0], sc, h->d_status, h->stream, &h->timer);
     int st = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

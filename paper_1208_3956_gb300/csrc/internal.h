@@ -179,6 +179,17 @@ struct SlabWork {
 template <typename C>
 cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, const SlabScratch& sc, int* status,
                                cudaStream_t s, KernelTimer* tm);
+// M (column-major, leading dimension ldm) = D_k - C_k Xp C_k (Xp = X_{k-1} in the sweep
+// layout, leading dimension ld; M = D_k when Xp is null).
+template <typename C>
+cudaError_t launch_slab_build(const Geom& g, const StripDev& st, int k, const C* Xp, int ld, C* M, int ldm,
+                              cudaStream_t s, KernelTimer* tm);
+// slab_tc.cu: the blocks X_k = S_k^{-1}, k = 0 .. Ny-1, of up to 8 strips side by side in
+// complex64, inverted by blocked Gauss-Jordan elimination whose rank-12 updates run on the
+// tensor cores; scratch of slab_factor_tc_scratch(max n, strips) bytes.
+size_t slab_factor_tc_scratch(int nmax, int ns);
+cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns, void* pool, void* scratch,
+                                  int* status, cudaStream_t s, KernelTimer* tm);
 // Right-hand side and block forward / back substitution of strip st (into wk.ybuf).
 template <typename C>
 cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev* pst, const SweepStep& sp,

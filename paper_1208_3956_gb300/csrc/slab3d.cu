@@ -726,6 +726,17 @@ cudaError_t launch_slab_out(const Geom& g, const StripDev& st, int dir, const vo
     return cudaGetLastError();
 }
 
+template <typename C>
+cudaError_t launch_slab_build(const Geom& g, const StripDev& st, int k, const C* Xp, int ld, C* M, int ldm,
+                              cudaStream_t s, KernelTimer* tm) {
+    const int n = st.W * g.Nz;
+    TimedLaunch t(tm, "slab_build", s);
+    k_slab_build<C><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(g, st, k, Xp, ld, M, ldm);
+    return cudaGetLastError();
+}
+template cudaError_t launch_slab_build<float2>(const Geom&, const StripDev&, int, const float2*, int, float2*, int,
+                                               cudaStream_t, KernelTimer*);
+
 // Loads this file's module onto the current device (the strip-solve kernels of a
 // preconditioner application).
 cudaError_t preload_slab_kernels() {
