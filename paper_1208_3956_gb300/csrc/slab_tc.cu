@@ -4,25 +4,27 @@
 // Every block X_k = S_k^{-1}, S_k = D_k - C_k X_{k-1} C_k (n x n, n = W N_z), is inverted
 // by blocked Gauss-Jordan elimination with partial pivoting, the J strips of the grid side
 // by side.  Pivot rows are not exchanged: a row that has served as the pivot of a column is
-// marked (kstep) and left out of later pivot searches.  Per panel of kTcNb columns:
+// marked (kstep) and left out of later pivot searches.  The columns go in panels of kTcBig,
+// each made of sub-panels of kTcNb:
 //
-//   k_tc_panel  (one CTA per strip, the panel's n x kTcNb entries in shared memory): for each
-//               column of the panel the largest unused |entry| is the pivot q; the pivot row
-//               is scaled by 1/pivot and eliminated from every other row, within the panel
-//               only.  The panel then holds G, the panel's columns of the accumulated row
-//               transformation.  Written out: G into the block, G as the update's A operand,
-//               and T = the panel's pivot rows as they were (all columns), expanded for the
-//               complex product.
-//   k_tc_update (tiles of 128 rows x 32 columns, all strips): every column outside the panel
-//               becomes  A(:, j) <- A(:, j) with the panel's pivot rows zeroed + G T(:, j),
-//               a complex product of inner dimension kTcNb on the tensor cores: tcgen05.mma
-//               kind::tf32 with operands staged in shared memory and the accumulator in
-//               tensor memory, each complex64 operand split into a TF32 high part and a TF32
-//               remainder (3 products: hi.hi + hi.lo + lo.hi) so that the product keeps
-//               complex64 accuracy.
-//   k_tc_store  after the last panel the block N holds the inverse up to the pivot order:
-//               X(a, c) = N(q_a, pos(c)), q_a the pivot row of step a and pos(c) the step
-//               whose pivot row was c; written in the sweep layout of the factor pool.
+//   k_tc_panel   (one CTA per strip, the sub-panel's n x kTcNb entries in shared memory): for
+//                each of its columns the largest unused |entry| is the pivot q; the pivot row is
+//                scaled by 1/pivot and eliminated from every other row, within the sub-panel.
+//                The sub-panel then holds G, its columns of the accumulated row transformation.
+//   k_tc_gather  T = the sub-panel's (or panel's) pivot rows as they are, on the columns to be
+//                updated, expanded for the complex product.
+//   k_tc_update  every column j to be updated becomes
+//                    A(:, j) <- A(:, j) with the source's pivot rows zeroed + G T(:, j),
+//                a complex product on the tensor cores: tcgen05.mma kind::tf32 with operands
+//                staged in shared memory (inner dimension in chunks of kTcNb complex columns)
+//                and the accumulator in tensor memory, each complex64 operand split into a TF32
+//                high part and a TF32 remainder (3 products: hi.hi + hi.lo + lo.hi) so that the
+//                product keeps complex64 accuracy.  After a sub-panel it updates the other
+//                columns of its panel; after the whole panel (G = the panel's kTcBig columns)
+//                every column outside it.
+//   k_tc_store   after the last panel the block N holds the inverse up to the pivot order:
+//                X(a, c) = N(q_a, pos(c)), q_a the pivot row of step a and pos(c) the step
+//                whose pivot row was c; written in the sweep layout of the factor pool.
 //
 // The complex product uses real operands: a row of G is (Re g_0, Im g_0, Re g_1, ...), and
 // complex column j of T gives two B rows, (Re t_0, -Im t_0, Re t_1, ...) for the real part
@@ -35,8 +37,10 @@ namespace helm {
 
 namespace {
 
-constexpr int kTcNb = 12;                // panel width (complex columns)
-constexpr int kTcK = 2 * kTcNb;          // real inner dimension of the update (24 = 3 x 8)
+constexpr int kTcNb = 12;                // sub-panel width (complex columns)
+constexpr int kTcK = 2 * kTcNb;          // real inner dimension of one chunk (24 = 3 MMAs of 8)
+constexpr int kTcBig = 4 * kTcNb;        // panel width (complex columns)
+constexpr int kTcKT = 2 * kTcBig;        // row length of the T buffer (real)
 constexpr int kTcRows = 128;             // rows of an update tile (the MMA's M)
 constexpr int kTcCols = 32;              // complex columns of an update tile (N = 64 real)
 constexpr int kTcPanelThreads = 1024;
@@ -73,24 +77,26 @@ struct TcStrip {
     float2* M;     // n x n, column-major, leading dimension ldm
     int n, ldm, npad;   // npad: n rounded up to kTcRows
     int* qs;       // [n] pivot row of step i
-    int* kstep;    // [n] panel in which row r was a pivot row, -1 before
+    int* kstep;    // [n] sub-panel in which row r was a pivot row, -1 before
     int* pos;      // [n] step whose pivot row was r
-    float* G;      // [npad][kTcK] the panel's columns of the transformation, real interleaved
-    float* T;      // [2 npad][kTcK] the panel's pivot rows, expanded (B operand rows)
+    float* T;      // [2 npad][kTcKT] the source's pivot rows, expanded (B operand rows)
     float2* X;     // the factor pool's block k (row-major, leading dimension xld)
     int xld;
 };
 constexpr int kTcMaxStrips = 8;
 struct TcArgs {
     TcStrip s[kTcMaxStrips];
-    int p;          // panel index
-    int* status;    // 6: zero or non-finite pivot, 7: a bounded wait gave up
+    int sp;          // k_tc_panel: the sub-panel (columns sp kTcNb ..)
+    int glo, ghi;    // gather / update: the source columns (G) and their pivot rows (T)
+    int ulo, uhi;    // gather / update: the columns to update (the source's own skipped)
+    int kmin;        // update: rows with kstep >= kmin are the source's pivot rows
+    int* status;     // 6: zero or non-finite pivot, 7: a bounded wait gave up
 };
 
 __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(16) unsigned char tc_panel_smem[];
     const TcStrip& S = a.s[blockIdx.x];
-    const int n = S.n, ldm = S.ldm, c0 = a.p * kTcNb, tid = threadIdx.x;
+    const int n = S.n, ldm = S.ldm, c0 = a.sp * kTcNb, tid = threadIdx.x;
     if (c0 >= n) return;
     const int nbp = imin(kTcNb, n - c0);
     float2* P = reinterpret_cast<float2*>(tc_panel_smem);   // [kTcNb][n]
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_const
                 for (bx = 0; bx < n && ust[bx] >= 0; ++bx) {}
                 if (bx >= n) bx = 0;
             }
-            ust[bx] = a.p;
+            ust[bx] = a.sp;
             s_q[t] = bx;
             S.qs[c0 + t] = bx;
         }
@@ -149,31 +155,31 @@ __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_const
         }
         __syncthreads();
     }
-    // T first (the pivot rows of the block as they were, outside the panel), then the
-    // panel's own columns, G and the pivot marks
-    for (int e = tid; e < S.npad * kTcNb; e += kTcPanelThreads) {
-        const int j = e / kTcNb, t = e % kTcNb;
-        float2 v = make_float2(0.f, 0.f);
-        if (t < nbp && j < n && (j < c0 || j >= c0 + nbp)) v = S.M[(int64_t)j * ldm + s_q[t]];
-        float* row_re = S.T + (size_t)(2 * j) * kTcK;
-        float* row_im = row_re + kTcK;
+    for (int e = tid; e < nbp * n; e += kTcPanelThreads) {
+        const int t = e / n, r = e % n;
+        S.M[(int64_t)(c0 + t) * ldm + r] = P[e];
+    }
+    for (int r = tid; r < n; r += kTcPanelThreads) S.kstep[r] = ust[r];
+}
+
+// T(j) for the columns j in [ulo, uhi) outside the source [glo, ghi): the source's pivot rows
+// (steps glo .. ghi-1) at column j, expanded into the two B rows of complex column j.
+__global__ void k_tc_gather(const __grid_constant__ TcArgs a) {
+    const TcStrip& S = a.s[blockIdx.y];
+    const int n = S.n, glo = a.glo, ghi = imin(a.ghi, n), ulo = a.ulo, uhi = imin(a.uhi, n);
+    if (glo >= n) return;
+    const int nk = ghi - glo, nj = uhi - ulo;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nj * kTcBig; e += gridDim.x * blockDim.x) {
+        const int j = ulo + e / kTcBig, t = e % kTcBig;
+        if (j >= glo && j < ghi) continue;
+        const float2 v = t < nk ? S.M[(int64_t)j * S.ldm + S.qs[glo + t]] : make_float2(0.f, 0.f);
+        float* row_re = S.T + (size_t)(2 * j) * kTcKT;
+        float* row_im = row_re + kTcKT;
         row_re[2 * t] = v.x;
         row_re[2 * t + 1] = -v.y;
         row_im[2 * t] = v.y;
         row_im[2 * t + 1] = v.x;
     }
-    __syncthreads();
-    for (int e = tid; e < nbp * n; e += kTcPanelThreads) {
-        const int t = e / n, r = e % n;
-        S.M[(int64_t)(c0 + t) * ldm + r] = P[e];
-    }
-    for (int e = tid; e < S.npad * kTcNb; e += kTcPanelThreads) {
-        const int r = e / kTcNb, t = e % kTcNb;
-        const float2 v = (r < n && t < nbp) ? P[t * n + r] : make_float2(0.f, 0.f);
-        S.G[(size_t)r * kTcK + 2 * t] = v.x;
-        S.G[(size_t)r * kTcK + 2 * t + 1] = v.y;
-    }
-    for (int r = tid; r < n; r += kTcPanelThreads) S.kstep[r] = ust[r];
 }
 
 // Shared memory of the update tile: the operands in the core-matrix layout, the mbarrier
@@ -185,11 +191,10 @@ constexpr uint32_t kTcUpdSmem = 2 * kTcGBytes + 2 * kTcTBytes + 64;
 __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_upd_smem[];
     const TcStrip& S = a.s[blockIdx.z];
-    const int n = S.n, ldm = S.ldm, c0 = a.p * kTcNb;
-    if (c0 >= n) return;
-    const int nbp = imin(kTcNb, n - c0);
-    const int r0 = blockIdx.x * kTcRows, j0 = blockIdx.y * kTcCols;
-    if (r0 >= n || j0 >= n) return;
+    const int n = S.n, ldm = S.ldm, glo = a.glo, ghi = imin(a.ghi, n), uhi = imin(a.uhi, n);
+    if (glo >= n) return;
+    const int r0 = blockIdx.x * kTcRows, j0 = a.ulo + blockIdx.y * kTcCols;
+    if (r0 >= n || j0 >= uhi) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* gh = tc_upd_smem;
     unsigned char* gl = gh + kTcGBytes;
@@ -197,26 +202,10 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
     unsigned char* tl = th + kTcTBytes;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tl + kTcTBytes);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tl + kTcTBytes + 16);
-    for (int e = tid; e < kTcRows * kTcK; e += kTcUpdThreads) {
-        const int r = e / kTcK, k = e % kTcK;
-        float hi, lo;
-        tc_split(S.G[(size_t)(r0 + r) * kTcK + k], hi, lo);
-        *reinterpret_cast<float*>(gh + tc_off(r, k)) = hi;
-        *reinterpret_cast<float*>(gl + tc_off(r, k)) = lo;
-    }
-    for (int e = tid; e < 2 * kTcCols * kTcK; e += kTcUpdThreads) {
-        const int r = e / kTcK, k = e % kTcK;
-        float hi, lo;
-        tc_split(S.T[(size_t)(2 * j0 + r) * kTcK + k], hi, lo);
-        *reinterpret_cast<float*>(th + tc_off(r, k)) = hi;
-        *reinterpret_cast<float*>(tl + tc_off(r, k)) = lo;
-    }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tslot)),
                      "r"(2 * kTcCols)
@@ -231,37 +220,68 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
     constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTcCols >> 3) << 17) |
                                ((uint32_t)(kTcRows >> 4) << 24);
     constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
-    if (tid == 0) {
-        const uint32_t ga[3] = {tc_smem(gh), tc_smem(gh), tc_smem(gl)};
-        const uint32_t tb[3] = {tc_smem(th), tc_smem(tl), tc_smem(th)};
-        for (int kk = 0; kk < kTcK / 8; ++kk)
-            for (int pr = 0; pr < 3; ++pr) {
-                const uint64_t ad = tc_desc(ga[pr] + kk * 2 * lbo, lbo, sbo);
-                const uint64_t bd = tc_desc(tb[pr] + kk * 2 * lbo, lbo, sbo);
-                const uint32_t acc = (kk > 0 || pr > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
-            }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         tc_smem(mbar))
-                     : "memory");
+    const int nch = (ghi - glo + kTcNb - 1) / kTcNb;
+    bool ok = true;
+    for (int ch = 0; ch < nch && ok; ++ch) {
+        // G chunk: rows r0.., source columns glo + ch kTcNb + t (straight from the block)
+        for (int e = tid; e < kTcRows * kTcNb; e += kTcUpdThreads) {
+            const int t = e / kTcRows, r = e % kTcRows, c = glo + ch * kTcNb + t;
+            const float2 v = (c < ghi && r0 + r < n) ? S.M[(int64_t)c * ldm + r0 + r] : make_float2(0.f, 0.f);
+            float hi, lo;
+            tc_split(v.x, hi, lo);
+            *reinterpret_cast<float*>(gh + tc_off(r, 2 * t)) = hi;
+            *reinterpret_cast<float*>(gl + tc_off(r, 2 * t)) = lo;
+            tc_split(v.y, hi, lo);
+            *reinterpret_cast<float*>(gh + tc_off(r, 2 * t + 1)) = hi;
+            *reinterpret_cast<float*>(gl + tc_off(r, 2 * t + 1)) = lo;
+        }
+        // T chunk: the two B rows of columns j0 .. j0+31
+        for (int e = tid; e < 2 * kTcCols * kTcK; e += kTcUpdThreads) {
+            const int rr = e / kTcK, k = e % kTcK, j = j0 + rr / 2;
+            const bool live = j < uhi && (j < glo || j >= ghi);
+            float hi = 0.f, lo = 0.f;
+            if (live) tc_split(S.T[(size_t)(2 * j + (rr & 1)) * kTcKT + ch * kTcK + k], hi, lo);
+            *reinterpret_cast<float*>(th + tc_off(rr, k)) = hi;
+            *reinterpret_cast<float*>(tl + tc_off(rr, k)) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ga[3] = {tc_smem(gh), tc_smem(gh), tc_smem(gl)};
+            const uint32_t tb[3] = {tc_smem(th), tc_smem(tl), tc_smem(th)};
+            for (int kk = 0; kk < kTcK / 8; ++kk)
+                for (int pr = 0; pr < 3; ++pr) {
+                    const uint64_t ad = tc_desc(ga[pr] + kk * 2 * lbo, lbo, sbo);
+                    const uint64_t bd = tc_desc(tb[pr] + kk * 2 * lbo, lbo, sbo);
+                    const uint32_t acc = (ch > 0 || kk > 0 || pr > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(mbar))
+                         : "memory");
+        }
+        // every thread waits for the chunk's products (its operands are overwritten next)
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(tc_smem(mbar)), "r"((uint32_t)(ch & 1))
+                : "memory");
+        ok = __syncthreads_and(done != 0);
     }
-    uint32_t ok = 0;
-    for (uint32_t it = 0; it < kTcWaitLimit && !ok; ++it)
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(tc_smem(mbar))
-            : "memory");
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
         if (tid == 0) atomicExch(a.status, 7);
     } else {
         const int r = r0 + warp * 32 + lane;
-        const bool zero_row = r < n && S.kstep[r] == a.p;   // a pivot row of this panel
+        const int ks = r < n ? S.kstep[r] : -1;
+        const bool zero_row = ks >= 0 && ks >= a.kmin;   // a pivot row of the source
         for (int cc = 0; cc < 2 * kTcCols; cc += 16) {
             uint32_t v[16];
             asm volatile(
@@ -275,7 +295,7 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int j = j0 + cc / 2 + e;
-                if (r >= n || j >= n || (j >= c0 && j < c0 + nbp)) continue;
+                if (r >= n || j >= uhi || (j >= glo && j < ghi)) continue;
                 float2* dst = S.M + (int64_t)j * ldm + r;
                 const float2 base = zero_row ? make_float2(0.f, 0.f) : *dst;
                 *dst = make_float2(base.x + __uint_as_float(v[2 * e]), base.y + __uint_as_float(v[2 * e + 1]));
@@ -317,7 +337,7 @@ size_t slab_factor_tc_scratch(int nmax, int ns) {
     const int npad = (nmax + kTcRows - 1) / kTcRows * kTcRows;
     const size_t ldm = (size_t)((nmax + 3) & ~3);
     const size_t per = ldm * nmax * sizeof(float2) + (size_t)3 * nmax * sizeof(int) +
-                       (size_t)npad * kTcK * sizeof(float) + (size_t)2 * npad * kTcK * sizeof(float) + 4 * 256;
+                       (size_t)2 * npad * kTcKT * sizeof(float) + 4 * 256;
     return per * ns;
 }
 
@@ -331,7 +351,8 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
     if (psmem > 220 * 1024) return cudaErrorInvalidValue;   // n <= 2048 (the block limit)
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -349,15 +370,24 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
         S.qs = (int*)sp; sp += align((size_t)nmax * sizeof(int));
         S.kstep = (int*)sp; sp += align((size_t)nmax * sizeof(int));
         S.pos = (int*)sp; sp += align((size_t)nmax * sizeof(int));
-        S.G = (float*)sp; sp += align((size_t)npad_max * kTcK * sizeof(float));
-        S.T = (float*)sp; sp += align((size_t)2 * npad_max * kTcK * sizeof(float));
+        S.T = (float*)sp; sp += align((size_t)2 * npad_max * kTcKT * sizeof(float));
         S.xld = strips[i].ld;
     }
-    const int npanels = (nmax + kTcNb - 1) / kTcNb;
-    const dim3 ugrid(npad_max / kTcRows, (npad_max + kTcCols - 1) / kTcCols, ns);
     const dim3 sgrid((nmax + 3 + 31) / 32, (nmax + 31) / 32, ns);
     float2* pool2 = reinterpret_cast<float2*>(pool);
     cudaError_t e = cudaSuccess;
+    // gather T, then update the columns [ulo, uhi) from the source [glo, ghi)
+    auto source_update = [&](int glo, int ghi, int ulo, int uhi, int kmin) {
+        A.glo = glo;
+        A.ghi = ghi;
+        A.ulo = ulo;
+        A.uhi = uhi;
+        A.kmin = kmin;
+        const int nj = uhi - ulo;
+        k_tc_gather<<<dim3((nj * kTcBig + 255) / 256, ns), 256, 0, s>>>(A);
+        TimedLaunch t(tm, "slab_tc_update", s);
+        k_tc_update<<<dim3(npad_max / kTcRows, (nj + kTcCols - 1) / kTcCols, ns), kTcUpdThreads, kTcUpdSmem, s>>>(A);
+    };
     for (int k = 0; k < g.Ny && e == cudaSuccess; ++k) {
         for (int i = 0; i < ns && e == cudaSuccess; ++i) {
             const StripDev& st = strips[i];
@@ -366,17 +396,25 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
                                           st.ld, A.s[i].M, A.s[i].ldm, s, tm);
             if (e == cudaSuccess) e = cudaMemsetAsync(A.s[i].kstep, 0xFF, (size_t)A.s[i].n * sizeof(int), s);
         }
-        for (int p = 0; p < npanels && e == cudaSuccess; ++p) {
-            A.p = p;
-            {
-                TimedLaunch t(tm, "slab_tc_panel", s);
-                k_tc_panel<<<ns, kTcPanelThreads, psmem, s>>>(A);
+        int sub = 0;
+        for (int c0 = 0; c0 < nmax && e == cudaSuccess; c0 += kTcBig) {
+            const int c1 = imin(c0 + kTcBig, nmax), first = sub;
+            for (int s0 = c0; s0 < c1 && e == cudaSuccess; s0 += kTcNb, ++sub) {
+                A.sp = sub;
+                {
+                    TimedLaunch t(tm, "slab_tc_panel", s);
+                    k_tc_panel<<<ns, kTcPanelThreads, psmem, s>>>(A);
+                }
+                // the sub-panel's transformation on the other columns of its panel
+                if (c1 - c0 > kTcNb) source_update(s0, s0 + kTcNb, c0, c1, sub);
+                e = cudaGetLastError();
             }
-            {
-                TimedLaunch t(tm, "slab_tc_update", s);
-                k_tc_update<<<ugrid, kTcUpdThreads, kTcUpdSmem, s>>>(A);
+            // the panel's transformation on every column outside it
+            if (e == cudaSuccess && nmax > c1 - c0) {
+                if (c0 > 0) source_update(c0, c1, 0, c0, first);
+                if (c1 < nmax) source_update(c0, c1, c1, nmax, first);
+                e = cudaGetLastError();
             }
-            e = cudaGetLastError();
         }
         if (e != cudaSuccess) break;
         k_tc_pos<<<dim3(8, ns), 256, 0, s>>>(A);
