@@ -122,6 +122,7 @@ struct Geom {
     // and the right-hand-side scaling is s_x(c) s_y(k).
     const void* ct;
     int64_t ct_sy, ct_cy;
+    int64_t ct_sz;             // 3-D strips: ct[ct_sz + z] = s_z(z)
     // second level of nested dissection on the separator system: groups
     // g = 0..G-1 of separators gq0[g] .. gq1[g]-1; level-2 separator r (r < G-1)
     // is separator gq1[r]; sepmap[q] = group of separator q, or -(r+1) for a

@@ -553,6 +553,7 @@ helm_status prepare_geom(helm_dd* h) {
     g.ct = h->d_ct;
     g.ct_sy = 0;
     g.ct_cy = Ny;
+    g.ct_sz = h->ct_sz;
     // rows of the sweep's z buffer: the longest chain one CTA runs (a chunk, a
     // separator group, or the level-2 system)
     h->zrows = std::max(h->G - 1, 1);

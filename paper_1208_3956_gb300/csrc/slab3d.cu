@@ -81,14 +81,11 @@ __device__ double2 slab_xoff(const Geom& g, const StripDev& st, int k, int c, in
 __device__ double2 slab_zoff(const Geom& g, const StripDev& st, int k, int c, int z) {
     return cscale(cmul(cmul(strip_sx(g, st, c), glob_sy(g, k)), g.gz_half[z + 1]), -g.inv_h2);
 }
-// C_k(e), k >= 1
-__device__ double2 slab_coupling(const Geom& g, const StripDev& st, int k, int c, int z) {
-    return cscale(cmul(cmul(strip_sx(g, st, c), slab_sz(g, z)), g.gy_half[k]), -g.inv_h2);
-}
 // D_k(r, a) for any pair (zero off the stencil)
 __device__ double2 slab_dentry(const Geom& g, const StripDev& st, int k, int r, int a) {
     const int W = st.W;
     const int lo = imin(r, a), d = r > a ? r - a : a - r;
+    if (d != 0 && d != 1 && d != W) return make_double2(0.0, 0.0);
     const int c = lo % W, z = lo / W;
     if (d == 0) return slab_diag(g, st, k, c, z);
     if (d == 1 && c + 1 < W) return slab_xoff(g, st, k, c, z);
@@ -96,8 +93,8 @@ __device__ double2 slab_dentry(const Geom& g, const StripDev& st, int k, int r, 
     return make_double2(0.0, 0.0);
 }
 
-// M (column-major, ldm) = D_k - C_k Xp C_k, Xp = X_{k-1} in the row-major sweep
-// layout (leading dimension ld), or M = D_k for k = 0.  32 x 32 tiles.
+// M (column-major, ldm) = - C_k Xp C_k, Xp = X_{k-1} in the row-major sweep layout
+// (leading dimension ld), or M = 0 for k = 0; k_slab_dadd then adds D_k.  32 x 32 tiles.
 template <typename C>
 __global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, const C* __restrict__ Xp, int ld,
                                                     C* __restrict__ M, int ldm) {
@@ -113,7 +110,10 @@ __global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, 
         }
         if (threadIdx.x < 64) {
             const int e = (threadIdx.x < 32 ? r0 : a0) + tx;
-            const C v = e < n ? CT<C>::from(slab_coupling(g, st, k, e % st.W, e / st.W)) : CT<C>::zero();
+            // C_k(e) = s_x(c) s_z(z) (-alpha_y(y_{k-1/2}) / h^2) from the working-precision table
+            const C* ct = reinterpret_cast<const C*>(g.ct);
+            const C v = e < n ? cmul(cmul(ct[st.ctab + e % st.W], ct[g.ct_sz + e / st.W]), ct[g.ct_cy + k])
+                              : CT<C>::zero();
             (threadIdx.x < 32 ? cr : cc)[tx] = v;
         }
     }
@@ -122,9 +122,21 @@ __global__ void __launch_bounds__(256) k_slab_build(Geom g, StripDev st, int k, 
     for (int i = ty; i < 32; i += 8) {
         const int a = a0 + i, r = r0 + tx;
         if (a >= n || r >= n) continue;
-        C v = CT<C>::from(slab_dentry(g, st, k, r, a));
-        if (Xp) v = csub(v, cmul(cmul(cr[tx], tile[tx][i]), cc[i]));
-        M[(int64_t)a * ldm + r] = v;
+        M[(int64_t)a * ldm + r] = Xp ? cneg(cmul(cmul(cr[tx], tile[tx][i]), cc[i])) : CT<C>::zero();
+    }
+}
+
+// M(r, a) += D_k(r, a) on the stencil entries of row r: a = r, r +- 1 (same z), r +- W; one
+// entry per thread (the entries are evaluated in FP64, so they are spread over the GPU).
+template <typename C>
+__global__ void __launch_bounds__(64) k_slab_dadd(Geom g, StripDev st, int k, C* __restrict__ M, int ldm) {
+    const int n = st.W * g.Nz, W = st.W;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 5 * n; e += gridDim.x * blockDim.x) {
+        const int r = e / 5, i = e % 5, c = r % W;
+        const int a = i == 0 ? r : i == 1 ? (c > 0 ? r - 1 : -1) : i == 2 ? (c + 1 < W ? r + 1 : -1) : i == 3 ? r - W : r + W;
+        if (a < 0 || a >= n) continue;
+        C* p = M + (int64_t)a * ldm + r;
+        *p = cadd(*p, CT<C>::from(slab_dentry(g, st, k, r, a)));
     }
 }
 
@@ -626,6 +638,7 @@ cudaError_t launch_slab_factor(const Geom& g, const StripDev& st, void* pool, co
             TimedLaunch t(tm, "slab_build", s);
             k_slab_build<C><<<tiles, 256, 0, s>>>(g, st, k, k > 0 ? X + (int64_t)(k - 1) * st.bs : nullptr, st.ld,
                                                    M, sc.ldm);
+            k_slab_dadd<C><<<(5 * n + 63) / 64, 64, 0, s>>>(g, st, k, M, sc.ldm);
         }
         e = cudaMemsetAsync(sc.bar, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
@@ -732,6 +745,7 @@ cudaError_t launch_slab_build(const Geom& g, const StripDev& st, int k, const C*
     const int n = st.W * g.Nz;
     TimedLaunch t(tm, "slab_build", s);
     k_slab_build<C><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(g, st, k, Xp, ld, M, ldm);
+    k_slab_dadd<C><<<(5 * n + 63) / 64, 64, 0, s>>>(g, st, k, M, ldm);
     return cudaGetLastError();
 }
 template cudaError_t launch_slab_build<float2>(const Geom&, const StripDev&, int, const float2*, int, float2*, int,

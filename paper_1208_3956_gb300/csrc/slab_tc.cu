@@ -5,23 +5,24 @@
 // by blocked Gauss-Jordan elimination with partial pivoting, the J strips of the grid side
 // by side.  Pivot rows are not exchanged: a row that has served as the pivot of a column is
 // marked (kstep) and left out of later pivot searches.  The columns go in panels of kTcBig,
-// each made of sub-panels of kTcNb:
+// each made of sub-panels of kTcSub:
 //
-//   k_tc_panel   (one CTA per strip, the sub-panel's n x kTcNb entries in shared memory): for
+//   k_tc_panel   (one cluster per strip, the sub-panel's n x kTcSub entries in registers): for
 //                each of its columns the largest unused |entry| is the pivot q; the pivot row is
 //                scaled by 1/pivot and eliminated from every other row, within the sub-panel.
-//                The sub-panel then holds G, its columns of the accumulated row transformation.
-//   k_tc_gather  T = the sub-panel's (or panel's) pivot rows as they are, on the columns to be
-//                updated, expanded for the complex product.
+//                The sub-panel then holds G, its columns of the accumulated row transformation;
+//                the kernel also gathers T for the other columns of its panel (below).
+//   k_tc_gather  T = the panel's pivot rows as they are, on the columns outside the panel,
+//                expanded for the complex product.
 //   k_tc_update  every column j to be updated becomes
 //                    A(:, j) <- A(:, j) with the source's pivot rows zeroed + G T(:, j),
 //                a complex product on the tensor cores: tcgen05.mma kind::tf32 with operands
 //                staged in shared memory (inner dimension in chunks of kTcNb complex columns)
 //                and the accumulator in tensor memory, each complex64 operand split into a TF32
 //                high part and a TF32 remainder (3 products: hi.hi + hi.lo + lo.hi) so that the
-//                product keeps complex64 accuracy.  After a sub-panel it updates the other
-//                columns of its panel; after the whole panel (G = the panel's kTcBig columns)
-//                every column outside it.
+//                product keeps complex64 accuracy.  After a sub-panel (the source) it updates the
+//                other columns of its panel; after the whole panel (G = the panel's kTcBig
+//                columns) every column outside it.
 //   k_tc_store   after the last panel the block N holds the inverse up to the pivot order:
 //                X(a, c) = N(q_a, pos(c)), q_a the pivot row of step a and pos(c) the step
 //                whose pivot row was c; written in the sweep layout of the factor pool.
@@ -30,6 +31,8 @@
 // complex column j of T gives two B rows, (Re t_0, -Im t_0, Re t_1, ...) for the real part
 // and (Im t_0, Re t_0, ...) for the imaginary part, so that the accumulator's columns 2j,
 // 2j+1 are the real and imaginary parts of output column j.
+#include <climits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -37,31 +40,32 @@ namespace helm {
 
 namespace {
 
-constexpr int kTcNb = 12;                // sub-panel width (complex columns)
+constexpr int kTcSub = 8;                // sub-panel width (complex columns)
+constexpr int kTcNb = 12;                // inner-dimension chunk of an update (complex columns)
 constexpr int kTcK = 2 * kTcNb;          // real inner dimension of one chunk (24 = 3 MMAs of 8)
-constexpr int kTcBig = 4 * kTcNb;        // panel width (complex columns)
+constexpr int kTcBig = 96;               // panel width (complex columns)
 constexpr int kTcKT = 2 * kTcBig;        // row length of the T buffer (real)
 constexpr int kTcRows = 128;             // rows of an update tile (the MMA's M)
 constexpr int kTcCols = 32;              // complex columns of an update tile (N = 64 real)
-constexpr int kTcPanelThreads = 1024;
+constexpr int kTcPanelCl = 8;            // CTAs (one cluster) per strip in k_tc_panel
+constexpr int kTcPanelThreads = 256;     // one row per thread: n <= kTcPanelCl kTcPanelThreads = 2048
+constexpr int kTcPanelWarps = kTcPanelThreads / 32;
 constexpr int kTcUpdThreads = 128;
 constexpr uint32_t kTcWaitLimit = 1u << 22;
+static_assert(kTcBig % kTcSub == 0 && kTcBig % kTcNb == 0 && kTcSub <= kTcNb, "panel geometry");
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor of a K-major operand without swizzle: core matrices of 8
-// rows x 16 bytes, lbo bytes apart along K, sbo bytes apart between groups of 8 rows.
+// rows x 16 bytes, lbo bytes apart along K, sbo bytes apart between groups of 8 rows.  The
+// operands here put element (r, k) of a kTcK-column operand at byte
+//     (r / 8) (kTcK / 4) 128 + (k / 4) 128 + (r mod 8) 16 + (k mod 4) 4.
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;   // descriptor version of the tcgen05 family
     return d;
-}
-
-// byte offset of element (r, k) of a K-major operand with kTcK columns in that layout
-__device__ __forceinline__ uint32_t tc_off(int r, int k) {
-    return (uint32_t)((r >> 3) * (kTcK / 4) * 128 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
 // TF32 keeps the top 19 bits of an FP32 value; hi + lo represents x to about 2^-21
@@ -75,135 +79,284 @@ __device__ __forceinline__ void tc_split(float x, float& hi, float& lo) {
 // One strip's block under inversion and its work arrays.
 struct TcStrip {
     float2* M;     // n x n, column-major, leading dimension ldm
-    int n, ldm, npad;   // npad: n rounded up to kTcRows
+    int n, ldm;
     int* qs;       // [n] pivot row of step i
     int* kstep;    // [n] sub-panel in which row r was a pivot row, -1 before
     int* pos;      // [n] step whose pivot row was r
-    float* T;      // [2 npad][kTcKT] the source's pivot rows, expanded (B operand rows)
+    float* Th;     // [2 npad][kTcKT] the source's pivot rows, expanded (B operand rows; npad: n
+    float* Tl;     // rounded up to kTcRows), TF32 high part and remainder
     float2* X;     // the factor pool's block k (row-major, leading dimension xld)
     int xld;
 };
 constexpr int kTcMaxStrips = 8;
 struct TcArgs {
     TcStrip s[kTcMaxStrips];
-    int sp;          // k_tc_panel: the sub-panel (columns sp kTcNb ..)
+    int sp;          // k_tc_panel: the sub-panel (columns sp kTcSub ..)
     int glo, ghi;    // gather / update: the source columns (G) and their pivot rows (T)
-    int ulo, uhi;    // gather / update: the columns to update (the source's own skipped)
+    int ulo, uhi;    // the columns to update, [ulo, glo) and [ghi, uhi); k_tc_panel: its panel
     int kmin;        // update: rows with kstep >= kmin are the source's pivot rows
     int* status;     // 6: zero or non-finite pivot, 7: a bounded wait gave up
 };
 
-__global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_constant__ TcArgs a) {
-    extern __shared__ __align__(16) unsigned char tc_panel_smem[];
-    const TcStrip& S = a.s[blockIdx.x];
-    const int n = S.n, ldm = S.ldm, c0 = a.sp * kTcNb, tid = threadIdx.x;
-    if (c0 >= n) return;
-    const int nbp = imin(kTcNb, n - c0);
-    float2* P = reinterpret_cast<float2*>(tc_panel_smem);   // [kTcNb][n]
-    int* ust = reinterpret_cast<int*>(P + (size_t)kTcNb * n); // [n] kstep
-    __shared__ float s_best[kTcPanelThreads / 32];
-    __shared__ int s_idx[kTcPanelThreads / 32];
-    __shared__ int s_q[kTcNb];
-    __shared__ float2 s_prow[kTcNb];
-    for (int e = tid; e < kTcNb * n; e += kTcPanelThreads) {
-        const int t = e / n, r = e % n;
-        P[e] = t < nbp ? S.M[(int64_t)(c0 + t) * ldm + r] : make_float2(0.f, 0.f);
-    }
-    for (int r = tid; r < n; r += kTcPanelThreads) ust[r] = S.kstep[r];
-    __syncthreads();
-    for (int t = 0; t < nbp; ++t) {
-        float best = -1.f;
-        int bi = n;
-        for (int r = tid; r < n; r += kTcPanelThreads) {
-            const float v = cabs2(P[t * n + r]);
-            if (ust[r] < 0 && v > best) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if ((tid & 31) == 0) { s_best[tid >> 5] = best; s_idx[tid >> 5] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            float bb = s_best[0];
-            int bx = s_idx[0];
-            for (int w = 1; w < kTcPanelThreads / 32; ++w)
-                if (s_best[w] > bb || (s_best[w] == bb && s_idx[w] < bx)) { bb = s_best[w]; bx = s_idx[w]; }
-            if (!(bb > 0.f) || !(bb < INFINITY) || bx >= n) {
-                atomicExch(a.status, 6);   // zero or non-finite pivot: the result is invalid
-                for (bx = 0; bx < n && ust[bx] >= 0; ++bx) {}
-                if (bx >= n) bx = 0;
-            }
-            ust[bx] = a.sp;
-            s_q[t] = bx;
-            S.qs[c0 + t] = bx;
-        }
-        __syncthreads();
-        const int q = s_q[t];
-        if (tid < nbp) s_prow[tid] = P[tid * n + q];
-        __syncthreads();
-        const float2 ip = cinv(s_prow[t]);
-        for (int r = tid; r < n; r += kTcPanelThreads) {
-            const float2 m = P[t * n + r];
-            for (int s = 0; s < nbp; ++s) {
-                if (s == t) continue;
-                const float2 v = cmul(s_prow[s], ip);
-                P[s * n + r] = r == q ? v : csub(P[s * n + r], cmul(m, v));
-            }
-            P[t * n + r] = r == q ? ip : cneg(cmul(m, ip));
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < nbp * n; e += kTcPanelThreads) {
-        const int t = e / n, r = e % n;
-        S.M[(int64_t)(c0 + t) * ldm + r] = P[e];
-    }
-    for (int r = tid; r < n; r += kTcPanelThreads) S.kstep[r] = ust[r];
+// expanded T entries of complex column j, source step t, split into TF32 high part and remainder
+__device__ __forceinline__ void tc_put_t(const TcStrip& S, int j, int t, float2 v) {
+    const size_t o = (size_t)(2 * j) * kTcKT + 2 * t;
+    float h, l;
+    tc_split(v.x, h, l);
+    S.Th[o] = h;
+    S.Tl[o] = l;
+    S.Th[o + kTcKT + 1] = h;
+    S.Tl[o + kTcKT + 1] = l;
+    tc_split(v.y, h, l);
+    S.Th[o + kTcKT] = h;
+    S.Tl[o + kTcKT] = l;
+    S.Th[o + 1] = -h;
+    S.Tl[o + 1] = -l;
 }
 
-// T(j) for the columns j in [ulo, uhi) outside the source [glo, ghi): the source's pivot rows
-// (steps glo .. ghi-1) at column j, expanded into the two B rows of complex column j.
+// A warp's pivot candidate for the next column: |entry|^2, its row, and that row's entries in
+// the sub-panel's columns (so that the winner's row reaches every thread with the decision).
+struct TcCand {
+    float best;
+    int idx;
+    float2 row[kTcSub];
+};
+
+__device__ __forceinline__ void tc_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t tc_cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t tc_mapa(const void* p, uint32_t rank) {
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(tc_smem(p)), "r"(rank));
+    return d;
+}
+// 8 bytes into the shared memory of another CTA of the cluster, counted by its mbarrier
+__device__ __forceinline__ void tc_st_async(uint32_t addr, uint32_t lo, uint32_t hi, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "r"(lo), "r"(hi), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_arm(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(mbar)), "r"(bytes) : "memory");
+}
+
+// One cluster of kTcPanelCl CTAs per strip; thread g = rank kTcPanelThreads + tid of the cluster
+// owns row g of the sub-panel in registers.  During step t register s holds column
+// (t + s) mod kTcSub (the registers rotate by one column per step, so that the loop body
+// indexes them statically).  After the elimination of column t-1 every warp sends its
+// candidate for column t, with the candidate row, into every CTA of the cluster (st.async,
+// counted by that CTA's mbarrier of the step's buffer); every thread waits for the step's
+// kTcPanelCl kTcPanelWarps candidates and reduces them.  No cluster-wide barrier per step: a
+// buffer is rewritten two steps later, by senders that have already received this CTA's next
+// candidate, which it sends only after reading the buffer.
+__global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_constant__ TcArgs a) {
+    constexpr int kCands = kTcPanelCl * kTcPanelWarps;
+    constexpr uint32_t kStepBytes = kCands * sizeof(TcCand);
+    const uint32_t rank = tc_cluster_rank();
+    const TcStrip& S = a.s[blockIdx.x / kTcPanelCl];
+    const int n = S.n, ldm = S.ldm, c0 = a.sp * kTcSub, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (c0 >= n) return;   // uniform over the cluster
+    const int nbp = imin(kTcSub, n - c0);
+    const int r = (int)rank * kTcPanelThreads + tid;
+    __shared__ __align__(16) TcCand cand[2][kCands];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ int s_q[kTcSub];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc_arm(&mbar[0], kStepBytes);
+        if (nbp > 1) tc_arm(&mbar[1], kStepBytes);
+    }
+    float2 P[kTcSub];
+    bool fr = r < n && S.kstep[r] < 0;   // row still free (never a pivot row)
+    bool mine = false;                   // row became a pivot row in this sub-panel
+#pragma unroll
+    for (int t = 0; t < kTcSub; ++t)
+        P[t] = (r < n && t < nbp) ? S.M[(int64_t)(c0 + t) * ldm + r] : make_float2(0.f, 0.f);
+    tc_cluster_sync();   // every CTA's barriers are armed before the first remote write
+    // the warp's candidate for the column at position 0 into cand[buf] of every CTA
+    auto propose = [&](int buf) {
+        float v = cabs2(P[0]);
+        v = v == v ? v : 0.f;   // a NaN entry competes as zero (every free row is a candidate)
+        float wb = fr ? v : -1.f;
+        int wi = fr ? r : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, wb, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+            if (ob > wb || (ob == wb && oi < wi)) { wb = ob; wi = oi; }
+        }
+        // the winner's row (row g sits in lane g mod 32) to every lane, then lane d < kTcPanelCl
+        // sends the candidate to CTA d
+        const int wl = wi == INT_MAX ? 0 : (wi & 31);
+        float2 row[kTcSub];
+#pragma unroll
+        for (int s = 0; s < kTcSub; ++s) {
+            row[s].x = __shfl_sync(0xffffffffu, P[s].x, wl);
+            row[s].y = __shfl_sync(0xffffffffu, P[s].y, wl);
+        }
+        if (lane < kTcPanelCl) {
+            const uint32_t dst = tc_mapa(&cand[buf][rank * kTcPanelWarps + warp], (uint32_t)lane);
+            const uint32_t mb = tc_mapa(&mbar[buf], (uint32_t)lane);
+            tc_st_async(dst, __float_as_uint(wb), (uint32_t)wi, mb);
+#pragma unroll
+            for (int s = 0; s < kTcSub; ++s)
+                tc_st_async(dst + 8 + 8 * s, __float_as_uint(row[s].x), __float_as_uint(row[s].y), mb);
+        }
+    };
+    propose(0);
+    bool ok = true;
+#pragma unroll 1
+    for (int t = 0; t < kTcSub; ++t) {
+        if (t < nbp && ok) {   // uniform
+            uint32_t done = 0;
+            for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(tc_smem(&mbar[t & 1])), "r"((uint32_t)((t >> 1) & 1))
+                    : "memory");
+            // the buffer's next use is armed before any of this CTA's next candidates leave
+            if (tid == 0 && done && t + 2 < nbp) tc_arm(&mbar[t & 1], kStepBytes);
+            ok = __syncthreads_and(done != 0);   // uniform in the CTA
+            if (!ok) {
+                if (tid == 0) atomicExch(a.status, 7);
+                continue;
+            }
+            const TcCand* cd = cand[t & 1];
+            float bb = -1.f;
+            int bx = INT_MAX, bw = 0;
+#pragma unroll
+            for (int h = 0; h < kCands; h += 32) {
+                const float ob = cd[h + lane].best;
+                const int oi = cd[h + lane].idx;
+                if (ob > bb || (ob == bb && oi < bx)) { bb = ob; bx = oi; bw = h + lane; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, bb, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bx, o);
+                const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+                if (ob > bb || (ob == bb && oi < bx)) { bb = ob; bx = oi; bw = ow; }
+            }
+            if (rank == 0 && tid == 0 && (!(bb > 0.f) || !(bb < INFINITY) || bx >= n))
+                atomicExch(a.status, 6);   // zero or non-finite pivot: the result is invalid
+            if (bx >= n) { bx = 0; bw = 0; }   // unreachable while a row is free; keeps every index in range
+            if (tid == 0) {
+                s_q[t] = bx;
+                if (rank == 0) S.qs[c0 + t] = bx;
+            }
+            const float2* prow = cd[bw].row;
+            const float2 ip = cinv(prow[0]);
+            const bool piv = r == bx;
+            const float2 m = P[0];
+            if (piv) { fr = false; mine = true; }
+#pragma unroll
+            for (int s = 1; s < kTcSub; ++s) {
+                const float2 v = cmul(prow[s], ip);
+                P[s] = piv ? v : csub(P[s], cmul(m, v));
+            }
+            P[0] = piv ? ip : cneg(cmul(m, ip));
+        }
+        // rotate: column t + 1 to position 0 (kTcSub rotations restore the order)
+        const float2 p0 = P[0];
+#pragma unroll
+        for (int s = 0; s + 1 < kTcSub; ++s) P[s] = P[s + 1];
+        P[kTcSub - 1] = p0;
+        if (t + 1 < nbp && ok) propose((t + 1) & 1);
+    }
+    // no CTA leaves while a candidate may still be on its way to it
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    if (ok && r < n) {
+#pragma unroll
+        for (int t = 0; t < kTcSub; ++t)
+            if (t < nbp) S.M[(int64_t)(c0 + t) * ldm + r] = P[t];
+        if (mine) S.kstep[r] = a.sp;
+    }
+    // T for the sub-panel's update of the other columns of its panel: the pivot rows at those
+    // columns, still untouched by this sub-panel (shared out over the cluster)
+    __syncthreads();
+    const int plo = a.ulo, phi = imin(a.uhi, n), np = phi - plo;
+    if (ok)
+        for (int e = r; e < np * kTcSub; e += kTcPanelCl * kTcPanelThreads) {
+            const int j = plo + e / kTcSub, t = e % kTcSub;
+            if ((j >= c0 && j < c0 + nbp) || t >= nbp) continue;
+            tc_put_t(S, j, t, S.M[(int64_t)j * ldm + s_q[t]]);
+        }
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The columns to update: [ulo, glo) then [ghi, uhi), at most n.
+__device__ __forceinline__ int tc_left(const TcArgs& a) { return a.glo > a.ulo ? a.glo - a.ulo : 0; }
+
+// T for the columns outside the source [glo, ghi): its pivot rows (steps glo .. ghi-1) at each
+// column, expanded into the two B rows of the column.
 __global__ void k_tc_gather(const __grid_constant__ TcArgs a) {
     const TcStrip& S = a.s[blockIdx.y];
-    const int n = S.n, glo = a.glo, ghi = imin(a.ghi, n), ulo = a.ulo, uhi = imin(a.uhi, n);
+    const int n = S.n, glo = a.glo, ghi = imin(a.ghi, n);
     if (glo >= n) return;
-    const int nk = ghi - glo, nj = uhi - ulo;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nj * kTcBig; e += gridDim.x * blockDim.x) {
-        const int j = ulo + e / kTcBig, t = e % kTcBig;
-        if (j >= glo && j < ghi) continue;
-        const float2 v = t < nk ? S.M[(int64_t)j * S.ldm + S.qs[glo + t]] : make_float2(0.f, 0.f);
-        float* row_re = S.T + (size_t)(2 * j) * kTcKT;
-        float* row_im = row_re + kTcKT;
-        row_re[2 * t] = v.x;
-        row_re[2 * t + 1] = -v.y;
-        row_im[2 * t] = v.y;
-        row_im[2 * t + 1] = v.x;
+    const int nk = ghi - glo, nl = tc_left(a), nr = imax(imin(a.uhi, n) - ghi, 0);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (nl + nr) * kTcBig; e += gridDim.x * blockDim.x) {
+        const int i = e / kTcBig, t = e % kTcBig;
+        const int j = i < nl ? a.ulo + i : ghi + (i - nl);
+        tc_put_t(S, j, t, t < nk ? S.M[(int64_t)j * S.ldm + S.qs[glo + t]] : make_float2(0.f, 0.f));
     }
 }
 
-// Shared memory of the update tile: the operands in the core-matrix layout, the mbarrier
-// and the tensor-memory address slot.
+// Shared memory of the update tile: two stages of the operands in the core-matrix layout (G
+// high and low parts, T high and low parts), two mbarriers and the tensor-memory address slot.
 constexpr uint32_t kTcGBytes = kTcRows * kTcK * 4;        // 12 KB per split part
 constexpr uint32_t kTcTBytes = 2 * kTcCols * kTcK * 4;    // 6 KB per split part
-constexpr uint32_t kTcUpdSmem = 2 * kTcGBytes + 2 * kTcTBytes + 64;
+constexpr uint32_t kTcStage = 2 * kTcGBytes + 2 * kTcTBytes;
+constexpr uint32_t kTcUpdSmem = 2 * kTcStage + 64;
 
+__device__ __forceinline__ void tc_sts4(unsigned char* base, uint32_t off, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(tc_smem(base + off)), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(tc_smem(mbar)), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+
+// One 128-row x 32-column tile of the update.  Column tiles blockIdx.y < ceil(nl / 32) cover
+// [ulo, glo), the others [ghi, uhi).  Thread tid stages row tid of every G chunk and half a B
+// row of every T chunk; chunk ch + 1 is read from global memory while the products of chunk ch
+// run (two operand stages, one mbarrier each).
 __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_upd_smem[];
     const TcStrip& S = a.s[blockIdx.z];
-    const int n = S.n, ldm = S.ldm, glo = a.glo, ghi = imin(a.ghi, n), uhi = imin(a.uhi, n);
+    const int n = S.n, ldm = S.ldm, glo = a.glo, ghi = imin(a.ghi, n);
     if (glo >= n) return;
-    const int r0 = blockIdx.x * kTcRows, j0 = a.ulo + blockIdx.y * kTcCols;
-    if (r0 >= n || j0 >= uhi) return;
+    const int nl = tc_left(a), tl_n = (nl + kTcCols - 1) / kTcCols;
+    const int y = blockIdx.y;
+    const int j0 = y < tl_n ? a.ulo + y * kTcCols : ghi + (y - tl_n) * kTcCols;
+    const int jlim = y < tl_n ? glo : imin(a.uhi, n);
+    const int r0 = blockIdx.x * kTcRows;
+    if (r0 >= n || j0 >= jlim) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* gh = tc_upd_smem;
-    unsigned char* gl = gh + kTcGBytes;
-    unsigned char* th = gl + kTcGBytes;
-    unsigned char* tl = th + kTcTBytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tl + kTcTBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tl + kTcTBytes + 16);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_upd_smem + 2 * kTcStage);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_upd_smem + 2 * kTcStage + 16);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(mbar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -212,6 +365,65 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // this thread's row of the tile as it is (the epilogue adds the product to it), loaded now
+    // so that the reads overlap the staging and the products
+    const int r = r0 + warp * 32 + lane;
+    const int ks = r < n ? S.kstep[r] : -1;
+    const bool zero_row = ks >= 0 && ks >= a.kmin;   // a pivot row of the source
+    float2 base[kTcCols];
+#pragma unroll
+    for (int e = 0; e < kTcCols; ++e)
+        base[e] = (r < n && j0 + e < jlim && !zero_row) ? S.M[(int64_t)(j0 + e) * ldm + r] : make_float2(0.f, 0.f);
+    // staging registers: G row tid (kTcNb complex entries), T half row (kTcK / 2 reals, both parts)
+    const int nk = ghi - glo, nch = (nk + kTcNb - 1) / kTcNb;
+    const int grow = r0 + tid;
+    const int brow = tid >> 1, bhalf = tid & 1, bj = j0 + (brow >> 1);
+    float2 gv[kTcNb];
+    float4 tvh[kTcK / 8], tvl[kTcK / 8];
+    auto load = [&](int ch) {
+#pragma unroll
+        for (int t = 0; t < kTcNb; ++t) {
+            const int c = glo + ch * kTcNb + t;
+            gv[t] = (c < ghi && grow < n) ? S.M[(int64_t)c * ldm + grow] : make_float2(0.f, 0.f);
+        }
+        const size_t to = (size_t)(2 * bj + (brow & 1)) * kTcKT + ch * kTcK + bhalf * (kTcK / 2);
+#pragma unroll
+        for (int i = 0; i < kTcK / 8; ++i) {
+            const int t0 = ch * kTcNb + bhalf * (kTcNb / 2) + 2 * i;   // complex source steps t0, t0 + 1
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+            if (bj < jlim && t0 < nk) {
+                h = *reinterpret_cast<const float4*>(S.Th + to + 4 * i);
+                l = *reinterpret_cast<const float4*>(S.Tl + to + 4 * i);
+                if (t0 + 1 >= nk) { h.z = h.w = 0.f; l.z = l.w = 0.f; }
+            }
+            tvh[i] = h;
+            tvl[i] = l;
+        }
+    };
+    auto store = [&](unsigned char* st) {
+        unsigned char* gh = st;
+        unsigned char* gl = gh + kTcGBytes;
+        unsigned char* th = gl + kTcGBytes;
+        unsigned char* tl = th + kTcTBytes;
+        const uint32_t gbase = (uint32_t)((tid >> 3) * (kTcK / 4) * 128 + (tid & 7) * 16);
+#pragma unroll
+        for (int i = 0; i < kTcNb / 2; ++i) {   // complex entries 2i, 2i+1 = reals 4i .. 4i+3
+            float h0, l0, h1, l1, h2, l2, h3, l3;
+            tc_split(gv[2 * i].x, h0, l0);
+            tc_split(gv[2 * i].y, h1, l1);
+            tc_split(gv[2 * i + 1].x, h2, l2);
+            tc_split(gv[2 * i + 1].y, h3, l3);
+            tc_sts4(gh, gbase + i * 128, h0, h1, h2, h3);
+            tc_sts4(gl, gbase + i * 128, l0, l1, l2, l3);
+        }
+        const uint32_t tbase = (uint32_t)((brow >> 3) * (kTcK / 4) * 128 + (brow & 7) * 16) + bhalf * (kTcK / 8) * 128;
+#pragma unroll
+        for (int i = 0; i < kTcK / 8; ++i) {
+            tc_sts4(th, tbase + i * 128, tvh[i].x, tvh[i].y, tvh[i].z, tvh[i].w);
+            tc_sts4(tl, tbase + i * 128, tvl[i].x, tvl[i].y, tvl[i].z, tvl[i].w);
+        }
+    };
+    if (nch > 0) load(0);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -220,37 +432,24 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
     constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTcCols >> 3) << 17) |
                                ((uint32_t)(kTcRows >> 4) << 24);
     constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
-    const int nch = (ghi - glo + kTcNb - 1) / kTcNb;
     bool ok = true;
-    for (int ch = 0; ch < nch && ok; ++ch) {
-        // G chunk: rows r0.., source columns glo + ch kTcNb + t (straight from the block)
-        for (int e = tid; e < kTcRows * kTcNb; e += kTcUpdThreads) {
-            const int t = e / kTcRows, r = e % kTcRows, c = glo + ch * kTcNb + t;
-            const float2 v = (c < ghi && r0 + r < n) ? S.M[(int64_t)c * ldm + r0 + r] : make_float2(0.f, 0.f);
-            float hi, lo;
-            tc_split(v.x, hi, lo);
-            *reinterpret_cast<float*>(gh + tc_off(r, 2 * t)) = hi;
-            *reinterpret_cast<float*>(gl + tc_off(r, 2 * t)) = lo;
-            tc_split(v.y, hi, lo);
-            *reinterpret_cast<float*>(gh + tc_off(r, 2 * t + 1)) = hi;
-            *reinterpret_cast<float*>(gl + tc_off(r, 2 * t + 1)) = lo;
-        }
-        // T chunk: the two B rows of columns j0 .. j0+31
-        for (int e = tid; e < 2 * kTcCols * kTcK; e += kTcUpdThreads) {
-            const int rr = e / kTcK, k = e % kTcK, j = j0 + rr / 2;
-            const bool live = j < uhi && (j < glo || j >= ghi);
-            float hi = 0.f, lo = 0.f;
-            if (live) tc_split(S.T[(size_t)(2 * j + (rr & 1)) * kTcKT + ch * kTcK + k], hi, lo);
-            *reinterpret_cast<float*>(th + tc_off(rr, k)) = hi;
-            *reinterpret_cast<float*>(tl + tc_off(rr, k)) = lo;
-        }
+    for (int ch = 0; ch < nch; ++ch) {
+        unsigned char* st = tc_upd_smem + (ch & 1) * kTcStage;
+        // the stage's previous chunk (ch - 2) must have been consumed by its products
+        const bool free_ok = ch < 2 || tc_wait(mbar + (ch & 1), (uint32_t)(((ch - 2) >> 1) & 1));
+        store(st);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        ok = __syncthreads_and(free_ok);
+        if (!ok) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ga[3] = {tc_smem(gh), tc_smem(gh), tc_smem(gl)};
-            const uint32_t tb[3] = {tc_smem(th), tc_smem(tl), tc_smem(th)};
+            const uint32_t g_hi = tc_smem(st), g_lo = g_hi + kTcGBytes, t_hi = g_lo + kTcGBytes,
+                           t_lo = t_hi + kTcTBytes;
+            const uint32_t ga[3] = {g_hi, g_hi, g_lo};
+            const uint32_t tb[3] = {t_hi, t_lo, t_hi};
+#pragma unroll
             for (int kk = 0; kk < kTcK / 8; ++kk)
+#pragma unroll
                 for (int pr = 0; pr < 3; ++pr) {
                     const uint64_t ad = tc_desc(ga[pr] + kk * 2 * lbo, lbo, sbo);
                     const uint64_t bd = tc_desc(tb[pr] + kk * 2 * lbo, lbo, sbo);
@@ -262,26 +461,18 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
                         : "memory");
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem(mbar))
+                             tc_smem(mbar + (ch & 1)))
                          : "memory");
         }
-        // every thread waits for the chunk's products (its operands are overwritten next)
-        uint32_t done = 0;
-        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(tc_smem(mbar)), "r"((uint32_t)(ch & 1))
-                : "memory");
-        ok = __syncthreads_and(done != 0);
+        if (ch + 1 < nch) load(ch + 1);   // in flight while the products run
     }
+    // the last commit covers every product issued before it
+    if (ok && nch > 0) ok = __syncthreads_and(tc_wait(mbar + ((nch - 1) & 1), (uint32_t)(((nch - 1) >> 1) & 1)));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
         if (tid == 0) atomicExch(a.status, 7);
     } else {
-        const int r = r0 + warp * 32 + lane;
-        const int ks = r < n ? S.kstep[r] : -1;
-        const bool zero_row = ks >= 0 && ks >= a.kmin;   // a pivot row of the source
+#pragma unroll
         for (int cc = 0; cc < 2 * kTcCols; cc += 16) {
             uint32_t v[16];
             asm volatile(
@@ -293,12 +484,11 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
                 : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = j0 + cc / 2 + e;
-                if (r >= n || j >= uhi || (j >= glo && j < ghi)) continue;
-                float2* dst = S.M + (int64_t)j * ldm + r;
-                const float2 base = zero_row ? make_float2(0.f, 0.f) : *dst;
-                *dst = make_float2(base.x + __uint_as_float(v[2 * e]), base.y + __uint_as_float(v[2 * e + 1]));
+            for (int i = 0; i < 8; ++i) {
+                const int e = cc / 2 + i, j = j0 + e;
+                if (r >= n || j >= jlim) continue;
+                S.M[(int64_t)j * ldm + r] =
+                    make_float2(base[e].x + __uint_as_float(v[2 * i]), base[e].y + __uint_as_float(v[2 * i + 1]));
             }
         }
     }
@@ -311,7 +501,10 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
 // pos[q_a] = a
 __global__ void k_tc_pos(const __grid_constant__ TcArgs a) {
     const TcStrip& S = a.s[blockIdx.y];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) S.pos[S.qs[i]] = i;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+        const int q = S.qs[i];
+        if (q >= 0 && q < S.n) S.pos[q] = i;
+    }
 }
 
 // X(a, c) = N(q_a, pos(c)) in the row-major sweep layout (columns n .. xld-1 zero).
@@ -323,13 +516,14 @@ __global__ void __launch_bounds__(256) k_tc_store(const __grid_constant__ TcArgs
     if (a0 >= n || c0 >= S.xld) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int i = ty; i < 32; i += 8) {   // column c0+i of X, rows a0+tx
-        const int c = c0 + i, r = a0 + tx;
-        tile[i][tx] = (c < n && r < n) ? S.M[(int64_t)S.pos[c] * S.ldm + S.qs[r]] : make_float2(0.f, 0.f);
+        const int c = c0 + i, rr = a0 + tx;
+        const int pc = (c < n && rr < n) ? S.pos[c] : -1, q = pc >= 0 ? S.qs[rr] : -1;
+        tile[i][tx] = (pc < n && q >= 0 && q < n) ? S.M[(int64_t)pc * S.ldm + q] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
-        const int r = a0 + i, c = c0 + tx;
-        if (r < n && c < S.xld) S.X[(int64_t)r * S.xld + c] = tile[tx][i];
+        const int rr = a0 + i, c = c0 + tx;
+        if (rr < n && c < S.xld) S.X[(int64_t)rr * S.xld + c] = tile[tx][i];
     }
 }
 
@@ -337,7 +531,7 @@ size_t slab_factor_tc_scratch(int nmax, int ns) {
     const int npad = (nmax + kTcRows - 1) / kTcRows * kTcRows;
     const size_t ldm = (size_t)((nmax + 3) & ~3);
     const size_t per = ldm * nmax * sizeof(float2) + (size_t)3 * nmax * sizeof(int) +
-                       (size_t)2 * npad * kTcKT * sizeof(float) + 4 * 256;
+                       (size_t)4 * npad * kTcKT * sizeof(float) + 6 * 256;
     return per * ns;
 }
 
@@ -347,12 +541,10 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
     static bool attr_set = false;
     int nmax = 0;
     for (int i = 0; i < ns; ++i) nmax = imax(nmax, strips[i].W * g.Nz);
-    const size_t psmem = (size_t)kTcNb * nmax * sizeof(float2) + (size_t)nmax * sizeof(int);
-    if (psmem > 220 * 1024) return cudaErrorInvalidValue;   // n <= 2048 (the block limit)
+    if (nmax > kTcPanelCl * kTcPanelThreads) return cudaErrorInvalidValue;   // the block limit
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -365,29 +557,42 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
         TcStrip& S = A.s[i];
         S.n = strips[i].W * g.Nz;
         S.ldm = (nmax + 3) & ~3;
-        S.npad = (S.n + kTcRows - 1) / kTcRows * kTcRows;
         S.M = (float2*)sp; sp += align((size_t)S.ldm * nmax * sizeof(float2));
         S.qs = (int*)sp; sp += align((size_t)nmax * sizeof(int));
         S.kstep = (int*)sp; sp += align((size_t)nmax * sizeof(int));
         S.pos = (int*)sp; sp += align((size_t)nmax * sizeof(int));
-        S.T = (float*)sp; sp += align((size_t)2 * npad_max * kTcKT * sizeof(float));
+        S.Th = (float*)sp; sp += align((size_t)2 * npad_max * kTcKT * sizeof(float));
+        S.Tl = (float*)sp; sp += align((size_t)2 * npad_max * kTcKT * sizeof(float));
         S.xld = strips[i].ld;
     }
     const dim3 sgrid((nmax + 3 + 31) / 32, (nmax + 31) / 32, ns);
     float2* pool2 = reinterpret_cast<float2*>(pool);
-    cudaError_t e = cudaSuccess;
-    // gather T, then update the columns [ulo, uhi) from the source [glo, ghi)
-    auto source_update = [&](int glo, int ghi, int ulo, int uhi, int kmin) {
+    // update the columns [ulo, glo) and [ghi, uhi) from the source [glo, ghi)
+    auto update = [&](int glo, int ghi, int ulo, int uhi, int kmin, const char* name) {
         A.glo = glo;
         A.ghi = ghi;
         A.ulo = ulo;
         A.uhi = uhi;
         A.kmin = kmin;
-        const int nj = uhi - ulo;
-        k_tc_gather<<<dim3((nj * kTcBig + 255) / 256, ns), 256, 0, s>>>(A);
-        TimedLaunch t(tm, "slab_tc_update", s);
-        k_tc_update<<<dim3(npad_max / kTcRows, (nj + kTcCols - 1) / kTcCols, ns), kTcUpdThreads, kTcUpdSmem, s>>>(A);
+        const int nl = imax(glo - ulo, 0), nr = imax(uhi - ghi, 0);
+        const int tiles = (nl + kTcCols - 1) / kTcCols + (nr + kTcCols - 1) / kTcCols;
+        TimedLaunch t(tm, name, s);
+        k_tc_update<<<dim3(npad_max / kTcRows, tiles, ns), kTcUpdThreads, kTcUpdSmem, s>>>(A);
     };
+    // k_tc_panel: one cluster of kTcPanelCl CTAs per strip
+    cudaLaunchAttribute pattr[1];
+    pattr[0].id = cudaLaunchAttributeClusterDimension;
+    pattr[0].val.clusterDim.x = kTcPanelCl;
+    pattr[0].val.clusterDim.y = 1;
+    pattr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t pcfg{};
+    pcfg.gridDim = dim3(ns * kTcPanelCl);
+    pcfg.blockDim = dim3(kTcPanelThreads);
+    pcfg.dynamicSmemBytes = 0;
+    pcfg.stream = s;
+    pcfg.attrs = pattr;
+    pcfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < g.Ny && e == cudaSuccess; ++k) {
         for (int i = 0; i < ns && e == cudaSuccess; ++i) {
             const StripDev& st = strips[i];
@@ -399,20 +604,26 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
         int sub = 0;
         for (int c0 = 0; c0 < nmax && e == cudaSuccess; c0 += kTcBig) {
             const int c1 = imin(c0 + kTcBig, nmax), first = sub;
-            for (int s0 = c0; s0 < c1 && e == cudaSuccess; s0 += kTcNb, ++sub) {
+            for (int s0 = c0; s0 < c1 && e == cudaSuccess; s0 += kTcSub, ++sub) {
                 A.sp = sub;
+                A.ulo = c0;
+                A.uhi = c1;
                 {
                     TimedLaunch t(tm, "slab_tc_panel", s);
-                    k_tc_panel<<<ns, kTcPanelThreads, psmem, s>>>(A);
+                    e = cudaLaunchKernelEx(&pcfg, k_tc_panel, A);
                 }
-                // the sub-panel's transformation on the other columns of its panel
-                if (c1 - c0 > kTcNb) source_update(s0, s0 + kTcNb, c0, c1, sub);
-                e = cudaGetLastError();
+                // the sub-panel's transformation on the other columns of its panel (T from the panel kernel)
+                if (e == cudaSuccess && c1 - c0 > kTcSub) update(s0, s0 + kTcSub, c0, c1, sub, "slab_tc_update_sub");
+                if (e == cudaSuccess) e = cudaGetLastError();
             }
             // the panel's transformation on every column outside it
             if (e == cudaSuccess && nmax > c1 - c0) {
-                if (c0 > 0) source_update(c0, c1, 0, c0, first);
-                if (c1 < nmax) source_update(c0, c1, c1, nmax, first);
+                A.glo = c0;
+                A.ghi = c1;
+                A.ulo = 0;
+                A.uhi = nmax;
+                k_tc_gather<<<dim3(((nmax - (c1 - c0)) * kTcBig + 255) / 256, ns), 256, 0, s>>>(A);
+                update(c0, c1, 0, nmax, first, "slab_tc_update");
                 e = cudaGetLastError();
             }
         }
