@@ -263,8 +263,60 @@ def run_slab3d(helm, media, torch, stream, steps):
                                                     "profiles/slab_sweep_smooth63_3d.md"),
                         "alg_bytes_per_launch": alg},
            "kernel_ms_per_step": {k: v[1] / k3 for k, v in stats.items()},
-           "batch16": batch16}
+           "batch16": batch16,
+           "factor": factor3d_stats(s3, peaks)}
     s3.close()
+    return out
+
+
+def tc_update_flops(ns, Ny, big=96, sub=8):
+    """Useful real flops of the tensor-core updates of one 3-D factorisation: complex MACs of
+    the blocked Gauss-Jordan updates (sub-panels of `sub` columns inside panels of `big`, the
+    loop of the factor kernel) x 8, for every strip block n in ns and every grid row."""
+    nmax, macs = max(ns), 0
+    for n in ns:
+        for c0 in range(0, nmax, big):
+            c1 = min(c0 + big, nmax)
+            if c0 >= n:
+                break
+            pw = min(c1, n) - c0
+            if c1 - c0 > sub:
+                for s0 in range(c0, c1, sub):
+                    if s0 >= n:
+                        break
+                    nb = min(sub, n - s0)
+                    macs += nb * (pw - nb) * n
+            if nmax > c1 - c0:
+                macs += pw * (n - pw) * n
+    return 8.0 * macs * Ny
+
+
+def factor3d_stats(s3, peaks):
+    """One more factorisation with per-launch events: time per kernel, and the tensor-core
+    update kernel against the TF32 peak (bf16 measured peak x the nominal TF32 / BF16 ratio
+    1.1 / 2.25).  `issued` counts the three TF32 products per complex64 product (hi.hi, hi.lo,
+    lo.hi); `useful` counts the Gauss-Jordan work once."""
+    s3.set_timing(True)
+    s3.factor()
+    st = s3.kernel_stats()
+    s3.set_timing(False)
+    Nz, Ny = s3.N[2], s3.N[1]
+    ns = [w * Nz for w in s3.strip_widths()]
+    groups = [ns[i:i + 8] for i in range(0, len(ns), 8)]
+    useful = sum(tc_update_flops(gr, Ny) for gr in groups)
+    upd_ms = sum(v[1] for k, v in st.items() if k.startswith("slab_tc_update"))
+    bf16 = peaks.get("bf16_tflops") if peaks else None
+    tf32 = (bf16 if bf16 else 1900.0) * 1.1 / 2.25
+    out = {"kernel_ms": {k: round(v[1], 3) for k, v in st.items()},
+           "kernel_launches": {k: v[0] for k, v in st.items()}}
+    if upd_ms > 0:
+        ach = useful / (upd_ms * 1e-3) / 1e12
+        out["update_roofline"] = {
+            "bound": "tensor", "kernel": "k_tc_update", "useful_tflops": ach, "issued_tflops": 3 * ach,
+            "peak": tf32, "unit": "TFLOP/s", "frac": 3 * ach / tf32,
+            "peak_source": ("bf16_tflops of MEASURED_PEAKS.json" if bf16 else "fallback 1900 TFLOP/s bf16")
+                           + " x 1.1/2.25 (nominal TF32 / BF16)",
+            "useful_flops": useful}
     return out
 
 
@@ -407,8 +459,8 @@ def run_table3(helm, torch, stream, args):
     Example 3, Table 3 shape: unit cube, c = 1, 10 points per wavelength, strips of about
     10 planes), mixed precision, one centre source.  The GPU counts at 31^3 and 47^3 sit
     next to the oracle's (tests/golden/table3_oracle_iterations.txt, a stored file written
-    by the oracle); 63^3 (79^3 padded, J = 7 strips of 9 planes, the largest cube whose
-    slab blocks fit the 2048-unknown limit at w_sub = 6) is GPU only."""
+    by the oracle); 63^3 (79^3 padded, J = 7 strips of 9 planes) and the paper's own 100^3
+    row (h = 0.01, J = 10, w_sub = 3 .. 6, its printed counts beside ours) are GPU only."""
     media = media_mod()
     golden = {}
     try:
@@ -417,16 +469,27 @@ def run_table3(helm, torch, stream, args):
             golden[(int(n), int(ws))] = int(it)
     except OSError:
         pass
+    paper = {}
+    try:
+        for n, J, ws, it in np.loadtxt(os.path.join(ROOT, "tests", "golden", "table3_paper_iterations.txt"),
+                                       dtype=int, ndmin=2):
+            paper[(int(n), int(ws))] = int(it)
+    except OSError:
+        pass
     out = {"workload": "const_cube_3d (Table 3 shape)", "w_sub": [2, 3, 4, 5, 6], "rows": []}
-    for n, J, wo in ((31, 3, 6), (47, 4, 8), (63, 7, 8)):
-        h = 1.0 / (n + 1)
+    # 100^3 with h = 0.01 and J = 10 is the paper's first row (w_pml = 3 .. 6), blocks of up
+    # to 23 x 116 = 2668 unknowns
+    for n, J, wo, wss in ((31, 3, 6, None), (47, 4, 8, None), (63, 7, 8, None), (100, 10, 8, [3, 4, 5, 6])):
+        wss = wss or out["w_sub"]
+        h = 1.0 / (n + 1) if n != 100 else 0.01
         c = np.ones((n, n, n))
         omega = 2 * math.pi / (10 * h)
         m = (n - 1) // 2
         f = torch.as_tensor(media.point_sources((n, n, n), wo, h, [(m, m, m)]), device="cuda")
-        row = {"n": n, "J": J, "w_outer": wo, "gpu_iters": [], "ms_per_solve": [], "factor_ms": [],
-               "oracle_iters": [golden.get((n, ws)) for ws in out["w_sub"]]}
-        for ws in out["w_sub"]:
+        row = {"n": n, "J": J, "w_outer": wo, "w_sub": wss, "gpu_iters": [], "ms_per_solve": [], "factor_ms": [],
+               "oracle_iters": [golden.get((n, ws)) for ws in wss],
+               "paper_iters": [paper.get((n, ws)) for ws in wss]}
+        for ws in wss:
             g = helm.HelmDD(c, h, omega, wo, ws, J, "mixed")
             g.set_stream(stream.cuda_stream)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -841,6 +904,18 @@ def main():
     ap.add_argument("--only-3d", action="store_true",
                     help="run only the 3-D workload and print its object (a profiling case)")
     args = ap.parse_args()
+    world_env = os.environ.get("WORLD_SIZE")
+    if args.gpus > 1 and world_env is None:
+        # one process per GPU: relaunch this command under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        return subprocess.call(cmd)
+    if world_env is not None and int(world_env) != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world_env}; the ranks launched decide", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
     if args.only_3d:

@@ -168,11 +168,14 @@ helm_status helm_dd_set_transmission(helm_dd* h, helm_transmission t);
  * memory, so HELM_EINVAL when a strip is too wide for it (complex128: about 50
  * columns; complex64: 64).  3-D grids: one dense block of n = W N_z unknowns (a slab of
  * W x-columns by all z-planes) per grid row y, factored top down with every
- * block inverted by Gauss-Jordan elimination with partial pivoting; its
- * inversions and the strip solves of the sweep run as cooperative launches
- * (all CTAs co-resident), and a bounded wait inside them that gives up returns
- * HELM_ETIMEOUT.  HELM_EINVAL when a 3-D block exceeds 2048 unknowns (use more
- * strips).  Factor memory: N_y n^2 complex entries per strip (8 or 16 bytes). */
+ * block inverted by Gauss-Jordan elimination with partial pivoting (complex64:
+ * blocked, the updates on the tensor cores, the panels on thread-block clusters;
+ * complex128: one cooperative launch per block); the strip solves of the sweep
+ * run as cooperative launches (all CTAs co-resident), and a bounded wait inside
+ * any of these kernels that gives up returns
+ * HELM_ETIMEOUT.  HELM_EINVAL when a 3-D block exceeds 4096 unknowns in complex64
+ * or 2048 in complex128 (use more strips).  Factor memory: N_y n^2 complex entries
+ * per strip (8 or 16 bytes). */
 helm_status helm_dd_factor(helm_dd* h);
 
 /* out = P in for nrhs right-hand sides (Section 2.1, Eqs. solve_upward and

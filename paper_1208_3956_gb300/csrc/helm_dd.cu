@@ -599,8 +599,14 @@ helm_status factor_slabs(helm_dd* h) {
         nmax = std::max(nmax, n);
         ldmax = std::max(ldmax, s.ld);
     }
-    if (nmax > 2048)
-        return fail(h, HELM_EINVAL, "a 3-D strip block has more than 2048 unknowns (W * N_z); use more strips");
+    // dense blocks: up to 4096 unknowns in complex64 (the tensor-core factor and the wide strip
+    // solve), 2048 in complex128
+    const int nlim = h->esize == (int)sizeof(float2) ? 4096 : 2048;
+    if (nmax > nlim)
+        return fail(h, HELM_EINVAL, h->esize == (int)sizeof(float2)
+                                        ? "a 3-D strip block has more than 4096 unknowns (W * N_z); use more strips"
+                                        : "a complex128 3-D strip block has more than 2048 unknowns (W * N_z); use "
+                                          "more strips or mixed precision");
     for (auto& p : h->d_pool) { if (p) cudaFree(p); p = nullptr; }
     h->factored = false;
     CK(h, cudaMalloc(&h->d_pool[0], (size_t)fac * h->esize));

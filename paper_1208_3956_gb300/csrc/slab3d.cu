@@ -22,6 +22,8 @@
 // matrix-vector product that streams X_k from HBM through shared memory.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "strip_ops.cuh"
 #include "internal.h"
@@ -387,10 +389,10 @@ __device__ __forceinline__ void bulk_row(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 constexpr int kSweepThreads = 288;   // 8 compute warps + 1 producer warp
-constexpr int kSegU = 8;             // columns per lane: 8 warps x 32 lanes x 8 >= xld (n <= 2048)
 constexpr int kMaxRpc = 32;          // rows per CTA and step
 
-template <typename C, int NB>
+// kSegU: columns per lane, 8 warps x 32 lanes x kSegU >= xld (8: n <= 2048, 16: n <= 4096)
+template <typename C, int NB, int kSegU>
 __global__ void __launch_bounds__(kSweepThreads, 1) k_slab_sweep(SlabSweepArgs<C> A) {
     using R = typename CT<C>::R;
     extern __shared__ __align__(128) unsigned char sweep_smem[];
@@ -683,12 +685,22 @@ cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev*
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int rpc = (n + nsm - 1) / nsm, ncta = (n + rpc - 1) / rpc;
-    if (rpc > kMaxRpc || st.ld > 8 * 32 * kSegU) return cudaErrorInvalidValue;
+    // column segments of 8 per lane up to 2048 unknowns, 16 up to 4096 (complex64 only: the
+    // complex128 input vector of 16 columns x 4 right-hand sides would not fit in registers)
+    const bool wide = st.ld > 8 * 32 * 8;
+    if (rpc > kMaxRpc || st.ld > 8 * 32 * 16 || (wide && sizeof(C) != sizeof(float2))) return cudaErrorInvalidValue;
     const size_t row = (size_t)st.ld * sizeof(C);
     const size_t kSmemMax = 227 * 1024;
+    // the kernel for a tile of one or NB right-hand sides
+    auto pick = [&](bool one, bool w) -> const void* {
+        if constexpr (std::is_same<C, float2>::value) {
+            if (w) return one ? (const void*)k_slab_sweep<C, 1, 16> : (const void*)k_slab_sweep<C, NB, 16>;
+        }
+        return one ? (const void*)k_slab_sweep<C, 1, 8> : (const void*)k_slab_sweep<C, NB, 8>;
+    };
     static bool attr_set = false;
     if (!attr_set) {
-        for (auto fn : {k_slab_sweep<C, 1>, k_slab_sweep<C, NB>}) {
+        for (const void* fn : {pick(true, false), pick(false, false), pick(true, true), pick(false, true)}) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
             if (e != cudaSuccess) return e;
         }
@@ -721,8 +733,7 @@ cudaError_t launch_slab_solve(const Geom& g, const StripDev& st, const StripDev*
         if (e != cudaSuccess) return e;
         TimedLaunch t(tm, "slab_sweep", s);
         void* args[] = {&A};
-        e = cudaLaunchCooperativeKernel(nbk == 1 ? (const void*)k_slab_sweep<C, 1> : (const void*)k_slab_sweep<C, NB>,
-                                        dim3(ncta), dim3(kSweepThreads), args, smem, s);
+        e = cudaLaunchCooperativeKernel(pick(nbk == 1, wide), dim3(ncta), dim3(kSweepThreads), args, smem, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -757,8 +768,8 @@ cudaError_t preload_slab_kernels() {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, k_slab_rhs<float2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_rhs<double2>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<float2, 1>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<double2, 1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<float2, 1, 8>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_sweep<double2, 1, 8>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_out<float2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_slab_out<double2>);
     return e;

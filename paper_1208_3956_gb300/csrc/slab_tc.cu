@@ -48,8 +48,10 @@ constexpr int kTcKT = 2 * kTcBig;        // row length of the T buffer (real)
 constexpr int kTcRows = 128;             // rows of an update tile (the MMA's M)
 constexpr int kTcCols = 32;              // complex columns of an update tile (N = 64 real)
 constexpr int kTcPanelCl = 8;            // CTAs (one cluster) per strip in k_tc_panel
-constexpr int kTcPanelThreads = 256;     // one row per thread: n <= kTcPanelCl kTcPanelThreads = 2048
+constexpr int kTcPanelThreads = 256;
 constexpr int kTcPanelWarps = kTcPanelThreads / 32;
+constexpr int kTcPanelRows = 2;          // rows per thread: n <= kTcPanelCl kTcPanelThreads kTcPanelRows = 4096
+constexpr int kTcPanelSpan = kTcPanelCl * kTcPanelThreads;   // rows of one sweep over the cluster's threads
 constexpr int kTcUpdThreads = 128;
 constexpr uint32_t kTcWaitLimit = 1u << 22;
 static_assert(kTcBig % kTcSub == 0 && kTcBig % kTcNb == 0 && kTcSub <= kTcNb, "panel geometry");
@@ -148,14 +150,14 @@ __device__ __forceinline__ void tc_arm(uint64_t* mbar, uint32_t bytes) {
 }
 
 // One cluster of kTcPanelCl CTAs per strip; thread g = rank kTcPanelThreads + tid of the cluster
-// owns row g of the sub-panel in registers.  During step t register s holds column
-// (t + s) mod kTcSub (the registers rotate by one column per step, so that the loop body
-// indexes them statically).  After the elimination of column t-1 every warp sends its
-// candidate for column t, with the candidate row, into every CTA of the cluster (st.async,
-// counted by that CTA's mbarrier of the step's buffer); every thread waits for the step's
-// kTcPanelCl kTcPanelWarps candidates and reduces them.  No cluster-wide barrier per step: a
-// buffer is rewritten two steps later, by senders that have already received this CTA's next
-// candidate, which it sends only after reading the buffer.
+// owns rows g + kTcPanelSpan k (k < kTcPanelRows) of the sub-panel in registers.  During step t
+// register s holds column (t + s) mod kTcSub (the registers rotate by one column per step, so
+// that the loop body indexes them statically).  After the elimination of column t-1 every warp
+// sends its candidate for column t, with the candidate row, into every CTA of the cluster
+// (st.async, counted by that CTA's mbarrier of the step's buffer); every thread waits for the
+// step's kTcPanelCl kTcPanelWarps candidates and reduces them.  No cluster-wide barrier per
+// step: a buffer is rewritten two steps later, by senders that have already received this
+// CTA's next candidate, which it sends only after reading the buffer.
 __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_constant__ TcArgs a) {
     constexpr int kCands = kTcPanelCl * kTcPanelWarps;
     constexpr uint32_t kStepBytes = kCands * sizeof(TcCand);
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_const
     const int n = S.n, ldm = S.ldm, c0 = a.sp * kTcSub, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (c0 >= n) return;   // uniform over the cluster
     const int nbp = imin(kTcSub, n - c0);
-    const int r = (int)rank * kTcPanelThreads + tid;
+    const int g = (int)rank * kTcPanelThreads + tid;
     __shared__ __align__(16) TcCand cand[2][kCands];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ int s_q[kTcSub];
@@ -175,33 +177,52 @@ __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_const
         tc_arm(&mbar[0], kStepBytes);
         if (nbp > 1) tc_arm(&mbar[1], kStepBytes);
     }
-    float2 P[kTcSub];
-    bool fr = r < n && S.kstep[r] < 0;   // row still free (never a pivot row)
-    bool mine = false;                   // row became a pivot row in this sub-panel
+    float2 P[kTcPanelRows][kTcSub];
+    bool fr[kTcPanelRows];     // row still free (never a pivot row)
+    bool mine[kTcPanelRows];   // row became a pivot row in this sub-panel
 #pragma unroll
-    for (int t = 0; t < kTcSub; ++t)
-        P[t] = (r < n && t < nbp) ? S.M[(int64_t)(c0 + t) * ldm + r] : make_float2(0.f, 0.f);
+    for (int k = 0; k < kTcPanelRows; ++k) {
+        const int r = g + kTcPanelSpan * k;
+        fr[k] = r < n && S.kstep[r] < 0;
+        mine[k] = false;
+#pragma unroll
+        for (int t = 0; t < kTcSub; ++t)
+            P[k][t] = (r < n && t < nbp) ? S.M[(int64_t)(c0 + t) * ldm + r] : make_float2(0.f, 0.f);
+    }
     tc_cluster_sync();   // every CTA's barriers are armed before the first remote write
     // the warp's candidate for the column at position 0 into cand[buf] of every CTA
     auto propose = [&](int buf) {
-        float v = cabs2(P[0]);
-        v = v == v ? v : 0.f;   // a NaN entry competes as zero (every free row is a candidate)
-        float wb = fr ? v : -1.f;
-        int wi = fr ? r : INT_MAX;
+        float wb = -1.f;
+        int wi = INT_MAX, wk = 0;
+#pragma unroll
+        for (int k = 0; k < kTcPanelRows; ++k) {
+            float v = cabs2(P[k][0]);
+            v = v == v ? v : 0.f;   // a NaN entry competes as zero (every free row is a candidate)
+            if (fr[k] && v > wb) { wb = v; wi = g + kTcPanelSpan * k; wk = k; }
+        }
+        // this lane's candidate row, then the warp's winner
+        float2 mrow[kTcSub];
+#pragma unroll
+        for (int s = 0; s < kTcSub; ++s) mrow[s] = P[0][s];
+#pragma unroll
+        for (int k = 1; k < kTcPanelRows; ++k)
+            if (wk == k)
+#pragma unroll
+                for (int s = 0; s < kTcSub; ++s) mrow[s] = P[k][s];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float ob = __shfl_xor_sync(0xffffffffu, wb, o);
             const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
             if (ob > wb || (ob == wb && oi < wi)) { wb = ob; wi = oi; }
         }
-        // the winner's row (row g sits in lane g mod 32) to every lane, then lane d < kTcPanelCl
+        // the winner's row (row r sits in lane r mod 32) to every lane, then lane d < kTcPanelCl
         // sends the candidate to CTA d
         const int wl = wi == INT_MAX ? 0 : (wi & 31);
         float2 row[kTcSub];
 #pragma unroll
         for (int s = 0; s < kTcSub; ++s) {
-            row[s].x = __shfl_sync(0xffffffffu, P[s].x, wl);
-            row[s].y = __shfl_sync(0xffffffffu, P[s].y, wl);
+            row[s].x = __shfl_sync(0xffffffffu, mrow[s].x, wl);
+            row[s].y = __shfl_sync(0xffffffffu, mrow[s].y, wl);
         }
         if (lane < kTcPanelCl) {
             const uint32_t dst = tc_mapa(&cand[buf][rank * kTcPanelWarps + warp], (uint32_t)lane);
@@ -257,37 +278,50 @@ __global__ void __launch_bounds__(kTcPanelThreads) k_tc_panel(const __grid_const
             }
             const float2* prow = cd[bw].row;
             const float2 ip = cinv(prow[0]);
-            const bool piv = r == bx;
-            const float2 m = P[0];
-            if (piv) { fr = false; mine = true; }
+            float2 m[kTcPanelRows];
+            bool piv[kTcPanelRows];
+#pragma unroll
+            for (int k = 0; k < kTcPanelRows; ++k) {
+                piv[k] = g + kTcPanelSpan * k == bx;
+                m[k] = P[k][0];
+                if (piv[k]) { fr[k] = false; mine[k] = true; }
+            }
 #pragma unroll
             for (int s = 1; s < kTcSub; ++s) {
                 const float2 v = cmul(prow[s], ip);
-                P[s] = piv ? v : csub(P[s], cmul(m, v));
+#pragma unroll
+                for (int k = 0; k < kTcPanelRows; ++k) P[k][s] = piv[k] ? v : csub(P[k][s], cmul(m[k], v));
             }
-            P[0] = piv ? ip : cneg(cmul(m, ip));
+#pragma unroll
+            for (int k = 0; k < kTcPanelRows; ++k) P[k][0] = piv[k] ? ip : cneg(cmul(m[k], ip));
         }
         // rotate: column t + 1 to position 0 (kTcSub rotations restore the order)
-        const float2 p0 = P[0];
 #pragma unroll
-        for (int s = 0; s + 1 < kTcSub; ++s) P[s] = P[s + 1];
-        P[kTcSub - 1] = p0;
+        for (int k = 0; k < kTcPanelRows; ++k) {
+            const float2 p0 = P[k][0];
+#pragma unroll
+            for (int s = 0; s + 1 < kTcSub; ++s) P[k][s] = P[k][s + 1];
+            P[k][kTcSub - 1] = p0;
+        }
         if (t + 1 < nbp && ok) propose((t + 1) & 1);
     }
     // no CTA leaves while a candidate may still be on its way to it
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    if (ok && r < n) {
+#pragma unroll
+    for (int k = 0; k < kTcPanelRows; ++k) {
+        const int r = g + kTcPanelSpan * k;
+        if (!ok || r >= n) continue;
 #pragma unroll
         for (int t = 0; t < kTcSub; ++t)
-            if (t < nbp) S.M[(int64_t)(c0 + t) * ldm + r] = P[t];
-        if (mine) S.kstep[r] = a.sp;
+            if (t < nbp) S.M[(int64_t)(c0 + t) * ldm + r] = P[k][t];
+        if (mine[k]) S.kstep[r] = a.sp;
     }
     // T for the sub-panel's update of the other columns of its panel: the pivot rows at those
     // columns, still untouched by this sub-panel (shared out over the cluster)
     __syncthreads();
     const int plo = a.ulo, phi = imin(a.uhi, n), np = phi - plo;
     if (ok)
-        for (int e = r; e < np * kTcSub; e += kTcPanelCl * kTcPanelThreads) {
+        for (int e = g; e < np * kTcSub; e += kTcPanelSpan) {
             const int j = plo + e / kTcSub, t = e % kTcSub;
             if ((j >= c0 && j < c0 + nbp) || t >= nbp) continue;
             tc_put_t(S, j, t, S.M[(int64_t)j * ldm + s_q[t]]);
@@ -541,7 +575,7 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
     static bool attr_set = false;
     int nmax = 0;
     for (int i = 0; i < ns; ++i) nmax = imax(nmax, strips[i].W * g.Nz);
-    if (nmax > kTcPanelCl * kTcPanelThreads) return cudaErrorInvalidValue;   // the block limit
+    if (nmax > kTcPanelSpan * kTcPanelRows) return cudaErrorInvalidValue;   // the block limit
     if (!attr_set) {
         const cudaError_t e =
             cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);

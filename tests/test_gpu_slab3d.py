@@ -141,13 +141,38 @@ def test_slab_full_size_smooth63_3d_mixed_solve_properties():
 
 
 def test_slab_block_size_limit_is_an_argument_error():
-    # one strip of 46 x-columns by 106 z-planes: 4876 unknowns per block > 2048
+    # one strip of 46 x-columns by 106 z-planes: 4876 unknowns per block > 4096 (complex64)
     c = np.full((100, 8, 40), 1.0)
     g = helm.HelmDD(c, 1.0 / 32, 20.0, 3, 2, 1, "mixed")
     with pytest.raises(helm.HelmError) as e:
         g.factor()
     assert e.value.status == -1   # HELM_EINVAL
+    assert "4096" in str(e.value)
+    g.close()
+    # blocks of 3234 and 3136 unknowns: within the complex64 limit, above the complex128 one
+    c = np.full((44, 4, 90), 1.0)
+    g = helm.HelmDD(c, 1.0 / 24, 20.0, 4, 6, 2, "fp64")
+    assert max(w * g.N[2] for w in g.strip_widths()) > 2048
+    with pytest.raises(helm.HelmError) as e:
+        g.factor()
+    assert e.value.status == -1
     assert "2048" in str(e.value)
+    g.close()
+
+
+def test_slab_precond_blocks_above_2048_match_oracle():
+    """Blocks of 3234 and 3136 unknowns (33 and 32 x-columns by 98 z-planes): the two-rows-per-
+    thread panel of the tensor-core factor and the 16-column-per-lane strip solve (all twelve
+    of its 256-column segments, 22 rows per CTA); B = 1 and a ragged B = 5."""
+    g, o = make3((44, 4, 90), 4, 6, 2, "mixed")
+    ns = [w * g.N[2] for w in g.strip_widths()]
+    assert min(ns) > 2048 and max(ns) > 11 * 256
+    g.factor()
+    o.factor()
+    f = media.random_rhs((5,) + g.shape, 23)
+    ref = np.stack([o.apply_precond(f[b]) for b in range(5)])
+    assert rel(g.apply_precond(f), ref) <= 2e-4
+    assert rel(g.apply_precond(f[:1]), ref[:1]) <= 2e-4
     g.close()
 
 
