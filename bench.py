@@ -307,6 +307,7 @@ def factor3d_stats(s3, peaks):
     upd_ms = sum(v[1] for k, v in st.items() if k.startswith("slab_tc_update"))
     bf16 = peaks.get("bf16_tflops") if peaks else None
     tf32 = (bf16 if bf16 else 1900.0) * 1.1 / 2.25
+    st = {k: v for k, v in st.items() if v[0] > 0}   # the handle's counters also list the solve's kernels
     out = {"kernel_ms": {k: round(v[1], 3) for k, v in st.items()},
            "kernel_launches": {k: v[0] for k, v in st.items()}}
     if upd_ms > 0:
