@@ -240,6 +240,8 @@ class HelmDD:
     def _out_like(self, f):
         if _is_torch(f):
             import torch
+            if f.device.type == "cpu" and f.is_pinned():   # page-locked in, page-locked out
+                return torch.empty(f.shape, dtype=f.dtype, pin_memory=True)
             return torch.empty_like(f)
         return np.empty(np.shape(f), dtype=np.complex128)
 

@@ -245,6 +245,13 @@ def test_device_pointer_path_matches_host_path():
     ud, _ = g.solve(fd, tol=1e-8)
     uh, _ = g.solve(f, tol=1e-8)
     assert rel(ud.cpu().numpy(), uh) <= 1e-12
+    # page-locked host tensors in, page-locked host tensor out (the end-to-end path of the bench)
+    fp = torch.from_numpy(f).pin_memory()
+    up, _ = g.solve(fp, tol=1e-8)
+    assert up.device.type == "cpu" and up.is_pinned()
+    assert rel(up.numpy(), uh) <= 1e-12
+    pp = g.apply_precond(fp)
+    assert pp.is_pinned() and rel(pp.numpy(), ph) <= 1e-14
 
 
 def test_gradient_matches_oracle():
