@@ -346,12 +346,13 @@ __global__ void k_tc_gather(const __grid_constant__ TcArgs a) {
     }
 }
 
-// Shared memory of the update tile: two stages of the operands in the core-matrix layout (G
-// high and low parts, T high and low parts), two mbarriers and the tensor-memory address slot.
+// Shared memory of the update tile: one stage of the operands in the core-matrix layout (G
+// high and low parts, T high and low parts), an mbarrier and the tensor-memory address slot.
+// 36 KB and about 100 registers a thread: five tiles per SM hide each other's load latency.
 constexpr uint32_t kTcGBytes = kTcRows * kTcK * 4;        // 12 KB per split part
 constexpr uint32_t kTcTBytes = 2 * kTcCols * kTcK * 4;    // 6 KB per split part
 constexpr uint32_t kTcStage = 2 * kTcGBytes + 2 * kTcTBytes;
-constexpr uint32_t kTcUpdSmem = 2 * kTcStage + 64;
+constexpr uint32_t kTcUpdSmem = kTcStage + 64;
 
 __device__ __forceinline__ void tc_sts4(unsigned char* base, uint32_t off, float a, float b, float c, float d) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(tc_smem(base + off)), "f"(a), "f"(b), "f"(c),
@@ -373,8 +374,11 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
 // One 128-row x 32-column tile of the update.  Column tiles blockIdx.y < ceil(nl / 32) cover
 // [ulo, glo), the others [ghi, uhi).  Thread tid stages row tid of every G chunk and half a B
 // row of every T chunk; chunk ch + 1 is read from global memory while the products of chunk ch
-// run (two operand stages, one mbarrier each).
-__global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_constant__ TcArgs a) {
+// run.  The tile's own entries are read at the start when the source is one chunk (a
+// sub-panel: kEarly, three tiles per SM), else while the last products run (a whole panel:
+// fewer registers, five tiles per SM).
+template <bool kEarly>
+__global__ void __launch_bounds__(kTcUpdThreads, kEarly ? 3 : 5) k_tc_update(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char tc_upd_smem[];
     const TcStrip& S = a.s[blockIdx.z];
     const int n = S.n, ldm = S.ldm, glo = a.glo, ghi = imin(a.ghi, n);
@@ -386,11 +390,10 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
     const int r0 = blockIdx.x * kTcRows;
     if (r0 >= n || j0 >= jlim) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_upd_smem + 2 * kTcStage);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_upd_smem + 2 * kTcStage + 16);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_upd_smem + kTcStage);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_upd_smem + kTcStage + 16);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(mbar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(mbar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -399,15 +402,18 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // this thread's row of the tile as it is (the epilogue adds the product to it), loaded now
-    // so that the reads overlap the staging and the products
     const int r = r0 + warp * 32 + lane;
     const int ks = r < n ? S.kstep[r] : -1;
     const bool zero_row = ks >= 0 && ks >= a.kmin;   // a pivot row of the source
+    // this thread's row of the tile as it is (the epilogue adds the product to it)
     float2 base[kTcCols];
+    auto load_base = [&]() {
 #pragma unroll
-    for (int e = 0; e < kTcCols; ++e)
-        base[e] = (r < n && j0 + e < jlim && !zero_row) ? S.M[(int64_t)(j0 + e) * ldm + r] : make_float2(0.f, 0.f);
+        for (int e = 0; e < kTcCols; ++e)
+            base[e] = (r < n && j0 + e < jlim && !zero_row) ? S.M[(int64_t)(j0 + e) * ldm + r]
+                                                            : make_float2(0.f, 0.f);
+    };
+    if (kEarly) load_base();
     // staging registers: G row tid (kTcNb complex entries), T half row (kTcK / 2 reals, both parts)
     const int nk = ghi - glo, nch = (nk + kTcNb - 1) / kTcNb;
     const int grow = r0 + tid;
@@ -468,9 +474,9 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
     constexpr uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
     bool ok = true;
     for (int ch = 0; ch < nch; ++ch) {
-        unsigned char* st = tc_upd_smem + (ch & 1) * kTcStage;
-        // the stage's previous chunk (ch - 2) must have been consumed by its products
-        const bool free_ok = ch < 2 || tc_wait(mbar + (ch & 1), (uint32_t)(((ch - 2) >> 1) & 1));
+        unsigned char* st = tc_upd_smem;
+        // the stage's previous chunk must have been consumed by its products
+        const bool free_ok = ch == 0 || tc_wait(mbar, (uint32_t)((ch - 1) & 1));
         store(st);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         ok = __syncthreads_and(free_ok);
@@ -495,13 +501,14 @@ __global__ void __launch_bounds__(kTcUpdThreads) k_tc_update(const __grid_consta
                         : "memory");
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem(mbar + (ch & 1)))
+                             tc_smem(mbar))
                          : "memory");
         }
         if (ch + 1 < nch) load(ch + 1);   // in flight while the products run
     }
+    if (!kEarly) load_base();   // while the last products run
     // the last commit covers every product issued before it
-    if (ok && nch > 0) ok = __syncthreads_and(tc_wait(mbar + ((nch - 1) & 1), (uint32_t)(((nch - 1) >> 1) & 1)));
+    if (ok && nch > 0) ok = __syncthreads_and(tc_wait(mbar, (uint32_t)((nch - 1) & 1)));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
         if (tid == 0) atomicExch(a.status, 7);
@@ -577,8 +584,9 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
     for (int i = 0; i < ns; ++i) nmax = imax(nmax, strips[i].W * g.Nz);
     if (nmax > kTcPanelSpan * kTcPanelRows) return cudaErrorInvalidValue;   // the block limit
     if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcUpdSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -611,7 +619,11 @@ cudaError_t launch_slab_factor_tc(const Geom& g, const StripDev* strips, int ns,
         const int nl = imax(glo - ulo, 0), nr = imax(uhi - ghi, 0);
         const int tiles = (nl + kTcCols - 1) / kTcCols + (nr + kTcCols - 1) / kTcCols;
         TimedLaunch t(tm, name, s);
-        k_tc_update<<<dim3(npad_max / kTcRows, tiles, ns), kTcUpdThreads, kTcUpdSmem, s>>>(A);
+        const dim3 grid(npad_max / kTcRows, tiles, ns);
+        if (ghi - glo <= kTcNb)
+            k_tc_update<true><<<grid, kTcUpdThreads, kTcUpdSmem, s>>>(A);
+        else
+            k_tc_update<false><<<grid, kTcUpdThreads, kTcUpdSmem, s>>>(A);
     };
     // k_tc_panel: one cluster of kTcPanelCl CTAs per strip
     cudaLaunchAttribute pattr[1];
