@@ -33,6 +33,15 @@ __host__ __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-
 __host__ __device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// a += v by two atomic adds (concurrent adds are summed in arrival order)
+__device__ __forceinline__ void catomic_add(float2* a, float2 v) {
+    atomicAdd(&a->x, v.x);
+    atomicAdd(&a->y, v.y);
+}
+__device__ __forceinline__ void catomic_add(double2* a, double2 v) {
+    atomicAdd(&a->x, v.x);
+    atomicAdd(&a->y, v.y);
+}
 __host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 __host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }

@@ -289,6 +289,8 @@ struct SepPools {
     C* GB2;
     C* P2L;    // level-2 right-hand-side products Rinv2 L, Rinv2 U (sweep layout)
     C* P2U;
+    C* Q2L;    // level-2 contributions of a group separator's right-hand side (sweep layout)
+    C* Q2U;
 };
 
 // Separator system of every strip (one CTA per strip): twisted LU of each group,
@@ -313,6 +315,7 @@ __global__ void k_factor_sep(Geom g, const C* __restrict__ GT, const C* __restri
     SepPools<C> P = pl;
     P.Rinv += st.red; P.E += st.red; P.F += st.red; P.GT2 += st.red; P.GB2 += st.red; P.P2L += st.red;
     P.P2U += st.red;
+    if (P.Q2L) { P.Q2L += st.red; P.Q2U += st.red; }
     const int G = g.G;
 
     // ---- level-1 blocks of separator q (row s = r1[q])
@@ -456,6 +459,128 @@ __global__ void k_factor_sep(Geom g, const C* __restrict__ GT, const C* __restri
         store_block(P.P2U + (int64_t)q * bs, Y, W, st.ld);
         __syncthreads();
     }
+    if (!P.Q2L) return;
+
+    // ---- level-2 contributions of the group separators.  A group's part of a level-2
+    // right-hand side is -P2L y(last) (to the level-2 separator below it) or -P2U y(first)
+    // (above), and the group solution's end values are linear in the group's right-hand sides
+    // a_i = Rinv_i bhat_i: y(last) = sum_i K_i a_i, y(first) = sum_i K'_i a_i.  The K blocks
+    // follow from the twisted solve's recurrences run backwards (the derivative of its last or
+    // first output with respect to every intermediate):
+    //   y(last):  G_{n-1} = I, G_{j-1} = -G_j F_j (j > tq); K_tq = G_tq;
+    //             K_{tq-1} = -G_tq E_tq, K_{j-1} = -K_j E_j (j < tq);
+    //             K_{tq+1} = G_{tq+1} - G_tq F_tq, K_j = G_j - K_{j-1} E_{j-1} (j > tq + 1)
+    //   y(first): G'_0 = I, G'_{j+1} = -G'_j F_j (j < tq); K'_tq = G'_tq;
+    //             K'_{tq+1} = -G'_tq F_tq, K'_{j+1} = -K'_j E_j (j > tq);
+    //             K'_{tq-1} = G'_{tq-1} - G'_tq E_tq, K'_{j-1} = G'_{j-1} - K'_j E_j (j < tq - 1)
+    // Stored per separator: Q2L_i = -P2L K_i, Q2U_i = -P2U K'_i, so that every chunk adds its
+    // share of the level-2 right-hand sides from its own separator parts.
+    const C one = CT<C>::from(make_double2(1.0, 0.0));
+    auto ident = [&](C* D) {
+        for (int e = threadIdx.x; e < W * W; e += blockDim.x) D[e] = (e % W == e / W) ? one : CT<C>::zero();
+        __syncthreads();
+    };
+    for (int gi = 0; gi < G; ++gi) {
+        const int q0 = g.gq0[gi], q1 = g.gq1[gi], n = q1 - q0, tq = (n - 1) / 2;
+        for (int side = 0; side < 2; ++side) {
+            const bool last = side == 0;   // y(last): level-2 separator below; y(first): above
+            if (last && gi == G - 1) continue;
+            if (!last && gi == 0) continue;
+            C* OUT = last ? P.Q2L : P.Q2U;
+            auto slot = [&](int i) { return OUT + (int64_t)(q0 + i) * bs; };
+            auto put = [&](int i, const C* src) {
+                rowmajor_store(slot(i), src);
+                __syncthreads();
+            };
+            auto get = [&](C* dst, int i) { rowmajor_load(dst, slot(i)); };
+            auto blk = [&](C* dst, const C* pool, int i) { load_block(dst, pool + (int64_t)(q0 + i) * bs, W, st.ld); };
+            if (last) {
+                ident(X);
+                put(n - 1, X);
+                for (int j = n - 1; j > tq; --j) {   // G_{j-1} = -G_j F_j
+                    blk(M, P.F, j);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, X, nullptr, M, W, false, (R)-1);
+                    block_copy(X, Y, W * W);
+                    put(j - 1, X);
+                }
+                block_copy(Z, X, W * W);             // G_tq = K_tq
+                for (int j = tq; j >= 1; --j) {      // K_{j-1} = -K_j E_j (K_tq = G_tq)
+                    blk(M, P.E, j);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, Z, nullptr, M, W, false, (R)-1);
+                    block_copy(Z, Y, W * W);
+                    put(j - 1, Z);
+                }
+                if (n - 1 > tq) {                    // K_{tq+1} = G_{tq+1} - G_tq F_tq
+                    get(Z, tq);
+                    blk(M, P.F, tq);
+                    get(Y, tq + 1);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, Z, nullptr, M, W, true, (R)-1);
+                    put(tq + 1, Y);
+                    block_copy(Z, Y, W * W);
+                    for (int j = tq + 2; j < n; ++j) {   // K_j = G_j - K_{j-1} E_{j-1}
+                        blk(M, P.E, j - 1);
+                        get(Y, j);
+                        __syncthreads();
+                        block_gemm_dscale<C>(Y, Z, nullptr, M, W, true, (R)-1);
+                        put(j, Y);
+                        block_copy(Z, Y, W * W);
+                    }
+                }
+            } else {
+                ident(X);
+                put(0, X);
+                for (int j = 0; j < tq; ++j) {       // G'_{j+1} = -G'_j F_j
+                    blk(M, P.F, j);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, X, nullptr, M, W, false, (R)-1);
+                    block_copy(X, Y, W * W);
+                    put(j + 1, X);
+                }
+                if (n - 1 > tq) {                    // K'_{tq+1} = -G'_tq F_tq, K'_{j+1} = -K'_j E_j
+                    blk(M, P.F, tq);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Z, X, nullptr, M, W, false, (R)-1);
+                    put(tq + 1, Z);
+                    for (int j = tq + 1; j + 1 < n; ++j) {
+                        blk(M, P.E, j);
+                        __syncthreads();
+                        block_gemm_dscale<C>(Y, Z, nullptr, M, W, false, (R)-1);
+                        block_copy(Z, Y, W * W);
+                        put(j + 1, Z);
+                    }
+                }
+                if (tq >= 1) {                       // K'_{tq-1} = G'_{tq-1} - G'_tq E_tq
+                    block_copy(Z, X, W * W);
+                    blk(M, P.E, tq);
+                    get(Y, tq - 1);
+                    __syncthreads();
+                    block_gemm_dscale<C>(Y, Z, nullptr, M, W, true, (R)-1);
+                    put(tq - 1, Y);
+                    block_copy(Z, Y, W * W);
+                    for (int j = tq - 1; j >= 1; --j) {   // K'_{j-1} = G'_{j-1} - K'_j E_j
+                        blk(M, P.E, j);
+                        get(Y, j - 1);
+                        __syncthreads();
+                        block_gemm_dscale<C>(Y, Z, nullptr, M, W, true, (R)-1);
+                        put(j - 1, Y);
+                        block_copy(Z, Y, W * W);
+                    }
+                }
+            }
+            // Q = -P2 K with P2L of the level-2 separator below, P2U of the one above
+            load_block(M, last ? P.P2L + (int64_t)q1 * bs : P.P2U + (int64_t)(q0 - 1) * bs, W, st.ld);
+            for (int i = 0; i < n; ++i) {
+                get(X, i);
+                __syncthreads();
+                block_gemm_dscale<C>(Y, M, nullptr, X, W, false, (R)-1);
+                store_block(slot(i), Y, W, st.ld);
+                __syncthreads();
+            }
+        }
+    }
 }
 
 // Transfer composites (with separator groups): for every chunk row k of chunk p and
@@ -525,7 +650,8 @@ cudaError_t launch_factor(const Geom& g, int Wmax, void* const* pool, int* statu
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (g.P > 1) {
-        SepPools<C> pl{(C*)pool[3], (C*)pool[4], (C*)pool[5], (C*)pool[6], (C*)pool[7], (C*)pool[8], (C*)pool[9]};
+        SepPools<C> pl{(C*)pool[3], (C*)pool[4], (C*)pool[5], (C*)pool[6], (C*)pool[7], (C*)pool[8], (C*)pool[9],
+                       g.G > 1 ? (C*)pool[11] : nullptr, g.G > 1 ? (C*)pool[12] : nullptr};
         TimedLaunch t(tm, "factor_sep", s);
         k_factor_sep<C><<<g.J, 256, smem_sep, s>>>(g, (const C*)pool[1], (const C*)pool[2], pl, status);
     }

@@ -93,9 +93,10 @@ struct helm_dd {
     int zrows = 1;
     StripDev* d_strips = nullptr;
     int* d_ints = nullptr;          // cmeta (8 per chunk) | r0 | r1 | rowmap | gq0 | gq1 | sepmap
-    // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator), transfer composites
-    void* d_pool[11] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                        nullptr};
+    // factors: Sinv GT GB (per grid row), Rinv E F GT2 GB2 P2L P2U (per separator), transfer composites,
+    // level-2 contributions Q2L Q2U (per separator)
+    void* d_pool[13] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int* d_status = nullptr;
     // 3-D strips: s_x s_z per block entry (working precision) and its per-strip offsets,
     // the offset of s_z in d_ct, the y-couplings -alpha_y(y_{k-1/2})/h^2 and the row
@@ -239,8 +240,9 @@ void chunk_layout(helm_dd* h) {
     // factor 0.93 (fewer, longer chunks) is the measured optimum on a 1055-row grid,
     // where the chunk steps are slightly cheaper than the separator steps.
     int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(0.93 * pow((double)Ny, 2.0 / 3.0)));
-    // concurrent sweeps run three strip solves side by side (one CTA per chunk and SM)
-    if (h->P_req == 0 && h->sweep == HELM_SWEEP_CONCURRENT && h->nsm >= 3) P = std::min(P, h->nsm / 3);
+    // concurrent sweeps run three strip solves side by side (one CTA per chunk and SM, and
+    // one for the level-2 system)
+    if (h->P_req == 0 && h->sweep == HELM_SWEEP_CONCURRENT && h->nsm >= 6) P = std::min(P, h->nsm / 3 - 1);
     P = std::min(P, (Ny + 1) / 2);
     h->P = std::max(P, 1);
     const int rows = Ny - (h->P - 1);
@@ -858,6 +860,8 @@ helm_status helm_dd_factor(helm_dd* h) {
     if (h->G > 1) {
         for (int i = 6; i < 10; ++i) CK(h, cudaMalloc(&h->d_pool[i], redb));
         CK(h, cudaMalloc(&h->d_pool[10], (size_t)xf * h->esize));
+        CK(h, cudaMalloc(&h->d_pool[11], redb));
+        CK(h, cudaMalloc(&h->d_pool[12], redb));
     }
     CK(h, cudaMemcpyAsync(h->d_strips, h->strips.data(), h->strips.size() * sizeof(StripDev),
                           cudaMemcpyHostToDevice, h->stream));
@@ -905,7 +909,7 @@ struct PrecondBufs {
     double2* V;      // [B][N] forward-sweep field v
     double2* G;      // [B][N] residual g = f - A v
     void* Y;         // [J][B][Ny][ws] chain solutions of every strip, working precision (ws = work_stride)
-    void* parts;     // [B][P-1][4][ws] separator right-hand-side parts
+    void* parts;     // per stream: separator right-hand-side parts, then level-2 contributions
     int* counters;   // [kMaxTiles][G+1] arrival counters, zero on entry
 };
 constexpr int kPrecondBufs = 4;
@@ -919,7 +923,7 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
     // concurrent sweeps keep three sets of chain solutions (upward, downward, corrections)
     // and one separator-parts buffer per stream
     sz[2] = (size_t)sweep_streams(h) * h->J * B * Ny * work_stride(h) * h->esize;
-    sz[3] = (size_t)sweep_streams(h) * B * std::max(h->P - 1, 1) * 4 * work_stride(h) * h->esize;
+    sz[3] = (size_t)sweep_streams(h) * sweep_parts_total_bytes(h->P, B, work_stride(h), h->esize);
     if (h->dim == 3) {   // right-hand sides and two strip solutions, [B][Ny][slab_ld] each
         sz[2] = (size_t)3 * B * Ny * h->slab_ld * h->esize;
         sz[3] = 256;
@@ -927,6 +931,14 @@ void precond_buf_bytes(const helm_dd* h, int B, size_t sz[kPrecondBufs]) {
 }
 
 helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
+// The level-2 accumulators of a separator-parts buffer start at zero (each strip solve's
+// level-2 CTA zeroes them again after reading them).
+cudaError_t zero_acc2(helm_dd* h, void* parts, int B) {
+    if (h->G <= 1) return cudaSuccess;
+    const int ws = work_stride(h);
+    return cudaMemsetAsync((char*)parts + sweep_parts_bytes(h->P, B, ws, h->esize), 0,
+                           sweep_parts2_bytes(h->P, B, ws, h->esize), h->stream);
+}
 helm_status run_precond_slabs(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
 helm_status run_precond_concurrent(helm_dd* h, const double2* in, double2* out, int B, const PrecondBufs& bf);
 
@@ -994,6 +1006,7 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
     // transfer from it, and the output columns of a whole sweep are written afterwards
     // in one launch
     auto ybuf = [&](int j) { return (char*)bf.Y + j * ystride * (int64_t)h->esize; };
+    CK(h, zero_acc2(h, bf.parts, B));
     auto strip_solve = [&](int j, const SweepStep& sp) -> cudaError_t {
         SweepWork wk{ybuf(j), bf.parts, bf.counters, h->d_status, ws, B, h->zrows,
                      sp.prev >= 0 ? ybuf(sp.prev) : nullptr};
@@ -1003,7 +1016,11 @@ helm_status run_precond(helm_dd* h, const double2* in, double2* out, int B, cons
         return launch_strip_solve<double2>(h->geom, j, h->strips[j], pst, sp, wk, h->d_pool, h->stream, &h->timer);
     };
     const int kOutBatch = 8;    // strips per output launch
-    const int kOutCTAs = 56;    // CTAs of an output launch beside the strip solves
+    // CTAs of an output launch beside the strip solves: the SMs a strip solve leaves free (one
+    // CTA per chunk, one for the level-2 system when the separators are grouped); 56 when the
+    // strip solve takes more than one wave anyway
+    const int solve_ctas = h->P + (h->G > 1 ? 1 : 0);
+    const int kOutCTAs = solve_ctas < h->nsm ? std::max(8, h->nsm - solve_ctas) : 56;
     // Output columns of strips jlo .. jlo+n-1, once their solves are done: on the side
     // stream, so that they run on the SMs the strip solves leave idle; join() makes the
     // main stream wait for every output pass issued so far.
@@ -1151,8 +1168,9 @@ helm_status run_precond_concurrent(helm_dd* h, const double2* in, double2* out, 
     const bool mixed = h->prec == HELM_PREC_MIXED;
     const size_t es = h->esize;
     char* Yset[3] = {(char*)bf.Y, (char*)bf.Y + (size_t)J * ystride * es, (char*)bf.Y + (size_t)2 * J * ystride * es};
-    const size_t psz = (size_t)B * std::max(h->P - 1, 1) * 4 * ws * es;
+    const size_t psz = sweep_parts_total_bytes(h->P, B, ws, es);
     void* parts[3] = {bf.parts, (char*)bf.parts + psz, (char*)bf.parts + 2 * psz};
+    for (void* pp : parts) CK(h, zero_acc2(h, pp, B));
     const size_t cset = counter_set_bytes(h) / sizeof(int);
     int* ctr[3] = {bf.counters, bf.counters + cset, bf.counters + 2 * cset};
     cudaStream_t st[3] = {h->stream, h->cstream[0], h->cstream[1]};
@@ -1576,6 +1594,7 @@ helm_status run_local_solves(helm_dd* h, const double2* F, double2* Ut, int B, c
     const int ws = work_stride(h);
     const int64_t ystride = (int64_t)B * Ny * ws;
     auto ybuf = [&](int j) { return (char*)bf.Y + j * ystride * (int64_t)h->esize; };
+    CK(h, zero_acc2(h, bf.parts, B));
     const int kOutBatch = 8;
     for (int j = 0; j < J; ++j) {
         const SweepStep sp = step_of(j);

@@ -107,9 +107,14 @@ struct SweepStep {
     int rb_in;
 };
 
+// Separator-parts buffer of one strip solve for B right-hand sides (sweep.cu): the parts,
+// then every chunk's contributions to the level-2 right-hand sides.
+size_t sweep_parts_bytes(int P, int B, int Wmax, size_t esize);
+size_t sweep_parts_total_bytes(int P, int B, int Wmax, size_t esize);
+size_t sweep_parts2_bytes(int P, int B, int Wmax, size_t esize);   // the trailing level-2 accumulators
 struct SweepWork {
     void* ybuf;             // [B][Ny][Wmax] working precision (this strip's chain solution)
-    void* parts;            // [B][P-1][4][Wmax] working precision
+    void* parts;            // sweep_parts_total_bytes: parts, then level-2 contributions
     int* counters;          // [RHS tile][G+1], zero between launches
     int* status;            // error word (7 = bounded wait timed out)
     int Wmax;               // row stride of ybuf and parts: even, >= every strip width

@@ -25,6 +25,8 @@
 //
 // Every mbarrier wait is bounded; on time-out the kernel records
 // HELM_ETIMEOUT in the status word, drains its copies (bounded) and returns.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -32,11 +34,11 @@ namespace helm {
 
 static constexpr int kMaxRing = 32;
 static constexpr uint32_t kWaitLimit = 1u << 22;
-static constexpr int kParts = 4;   // separator right-hand-side parts: 2 from chunks, 2 from groups
+static constexpr int kParts = 2;   // separator right-hand-side parts, one from each neighbouring chunk
 static constexpr int kAhead = 6;   // block loads in flight ahead of the chain (three dual steps)
 
 // load-order table entries: factor pool << 24 | block index in that pool
-enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kP2L = 4, kP2U = 5 };
+enum : int { kSinv = 0, kRinv = 1, kEo = 2, kFi = 3, kQ2L = 4, kQ2U = 5 };
 __host__ __device__ constexpr int enc(int pool, int idx) { return (pool << 24) | idx; }
 
 // ------------------------------------------------------------------ PTX
@@ -102,10 +104,12 @@ struct SweepArgs {
     const void* Rinv;
     const void* E;
     const void* F;
-    const void* P2L;         // level-2 products Rinv2 L, Rinv2 U (null with one group)
-    const void* P2U;
+    const void* Q2L;         // level-2 contributions of a group separator's part (null with one group)
+    const void* Q2U;
     void* ybuf;              // [B][Ny][Wmax] chunk solutions, then separator values
     void* parts;             // [B][P-1][kParts][Wmax] separator right-hand-side parts
+    void* acc2;              // [B][G-1][Wmax] the level-2 right-hand sides' shares from the group
+                             // separators, summed by the chunks' atomic adds; zero between launches
     // the previous strip solve, whose transfer enters this one (has_prev)
     int has_prev;
     StripDev pst;
@@ -142,7 +146,7 @@ __host__ __device__ inline SweepSmem sweep_smem(int ring, uint32_t slot_bytes, i
     uint32_t o = 0;
     s.slots = o; o += ring * slot_bytes;
     s.zb = o; o += ((uint32_t)zrows * Bt * W * esz + 15u) & ~15u;
-    s.tv = o; o += 7u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs, parts inputs
+    s.tv = o; o += 8u * Bt * 64 * esz;        // in/out vectors of both chains, separator-row rhs, parts inputs, zero
     s.cx = o; o += 64u * esz;
     s.cy = o; o += ((uint32_t)(zrows + 2) * esz + 15u) & ~15u;
     s.xv = o; o += ((uint32_t)(6 * Bt * 64 + (zrows + 1) * Bt * 2) * esz + 15u) & ~15u;   // incoming transfer
@@ -282,15 +286,21 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     // the owner lanes of each half's last step: pv_d from the down half, pv_u from the up half
     C* pv_d = v0 + 5 * BT * 64;
     C* pv_u = v0 + 6 * BT * 64;
+    const C* vzero = v0 + 7 * BT * 64;               // stays zero
     C* csx = reinterpret_cast<C*>(smem + L.cx);      // s_x(c)
     C* ccy = reinterpret_cast<C*>(smem + L.cy);      // -alpha_y(k-1/2)/h^2, k = r0..r1
     int* order = reinterpret_cast<int*>(smem + L.order);
     int* l2s = reinterpret_cast<int*>(smem + L.l2);  // level-2 separator indices gq1[i], i < 64
     volatile int* flags = reinterpret_cast<int*>(smem + L.flags);
     const int p = blockIdx.x, tile = blockIdx.y;
+    // with separator groups one more CTA (p = P) solves the level-2 system: it starts once
+    // every chunk has added its contributions to the level-2 right-hand sides, while the
+    // last chunk of each group solves the group
+    const bool l2cta = A.g.G > 1 && p == A.g.P;
+    const int pc = l2cta ? 0 : p;                    // geometry lookups of the level-2 CTA stay in range
     const int b0 = tile * BT;
     const int nb = imin(BT, A.B - b0);
-    const int r0 = A.g.r0[p], r1 = A.g.r1[p], m = r1 - r0;
+    const int r0 = A.g.r0[pc], r1 = A.g.r1[pc], m = r1 - r0;
     const int t = r0 + (m - 1) / 2;                  // twist row
     const int nd = t - r0, nu = r1 - 1 - t, nmx = imax(nd, nu);
     const int P = A.g.P, Q = P - 1;
@@ -307,23 +317,30 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     const C* Rinv = reinterpret_cast<const C*>(A.Rinv) + A.st.red;
     const C* Eb = reinterpret_cast<const C*>(A.E) + A.st.red;
     const C* Fb = reinterpret_cast<const C*>(A.F) + A.st.red;
-    const C* P2Lb = A.P2L ? reinterpret_cast<const C*>(A.P2L) + A.st.red : nullptr;
-    const C* P2Ub = A.P2U ? reinterpret_cast<const C*>(A.P2U) + A.st.red : nullptr;
+    const C* Q2Lb = A.Q2L ? reinterpret_cast<const C*>(A.Q2L) + A.st.red : nullptr;
+    const C* Q2Ub = A.Q2U ? reinterpret_cast<const C*>(A.Q2U) + A.st.red : nullptr;
     const bool resident = ring >= m + 2;
-    const bool has_below = p < P - 1, has_above = p > 0;
+    const bool has_below = !l2cta && p < P - 1, has_above = !l2cta && p > 0;
     // separator group of this chunk: group gi owns separators gq0..gq1-1 and chunks gq0..gq1
     const int NG = A.g.G;
-    const int gi = Q == 0 ? 0 : (p == Q ? NG - 1 : (A.g.sepmap[p] >= 0 ? A.g.sepmap[p] : -A.g.sepmap[p] - 1));
+    const int gi = Q == 0 ? 0 : (pc == Q ? NG - 1 : (A.g.sepmap[pc] >= 0 ? A.g.sepmap[pc] : -A.g.sepmap[pc] - 1));
     const int q0 = Q == 0 ? 0 : A.g.gq0[gi], q1 = Q == 0 ? 0 : A.g.gq1[gi], n1 = q1 - q0;
-    const bool up2 = gi > 0, dn2 = gi < NG - 1;   // level-2 separators above / below the group
     const int n2 = NG - 1;
+    // this chunk's contributions to the level-2 right-hand sides: its part of separator p
+    // (below) and of separator p-1 (above), each through the contribution block of that
+    // separator toward the level-2 separator below (q2dn) or above (q2up) its group
+    auto grp_of = [&](int q) { return A.g.sepmap[q]; };   // >= 0: a group member; < 0: a level-2 separator
+    const bool q2dnA = NG > 1 && has_below && grp_of(p) >= 0 && grp_of(p) < NG - 1;
+    const bool q2dnB = NG > 1 && has_above && grp_of(p - 1) >= 0 && grp_of(p - 1) < NG - 1;
+    const bool q2upA = NG > 1 && has_below && grp_of(p) > 0;
+    const bool q2upB = NG > 1 && has_above && grp_of(p - 1) > 0;
     // ---- ring state: load G lives in slot G % ring and completes phase (G / ring) & 1
     int nload = 0;                          // producer warp: length of the load sequence
     int cap = 0;                            // producer warp: loads from cap on wait for the next arrival
     int issued = 0, consumed = 0;
     int cslot = 0;
     uint32_t cpar = 0;
-    bool hold = resident;                   // a resident chunk's slots are read again by the back pass
+    bool hold = resident && !l2cta;         // a resident chunk's slots are read again by the back pass
     int nchunk = 0, ngroup = 0;             // producer warp: loads of the chunk and of the group chain
     auto src_of = [&](int G) -> const C* {
         const int e = order[G];
@@ -333,8 +350,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             case kRinv: return Rinv + o;
             case kEo: return Eb + o;
             case kFi: return Fb + o;
-            case kP2L: return P2Lb + o;
-            default: return P2Ub + o;
+            case kQ2L: return Q2Lb + o;
+            default: return Q2Ub + o;
         }
     };
     // producer warp: issue loads issued .. lim-1 (at most one ring, one per lane) together
@@ -384,7 +401,8 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
     // slot whose previous load has been consumed (and is no longer held)
     auto refill = [&]() {
         const int room = hold ? ring : consumed + ring;
-        issue_upto(imin(imin(cap, nload), imin(room, consumed + kAhead)));
+        // the level-2 CTA fills its whole ring while it waits for the chunks
+        issue_upto(imin(imin(cap, nload), imin(room, consumed + (l2cta ? ring : kAhead))));
     };
     // producer: wait (bounded) for the copies still in flight from load `from` on
     auto land = [&](int from) {
@@ -400,12 +418,16 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         for (int i = 0; i < ring; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
-    for (int o = tid; o < 7 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
+    for (int o = tid; o < 8 * BT * 64; o += blockDim.x) v0[o] = CT<C>::zero();
     __syncthreads();   // barriers initialised, vectors zeroed
     const C* ct = ctab<C>(A.g);
-    if (producer) {
-        // load order: the chunk's blocks, then the group's separator chain (with the
-        // level-2 products) and the level-2 chain, whose slots come from global memory
+    if (producer && l2cta) {   // the level-2 CTA: the level-2 chain only
+        for (int i = 0; i < imin(n2, 64); ++i) l2s[i] = A.g.gq1[i];
+        nload = chain_order(order, n2, [&](int i) { return i < 64 ? l2s[i] : A.g.gq1[i]; });
+        nchunk = nload;
+    } else if (producer) {
+        // load order: the chunk's blocks (with the contribution blocks of its two
+        // separators), then the group's separator chain, whose slots come from global memory
         int G = 0;
         for (int s = 0; s < nmx; ++s) {
             if (s < nd) order[G++] = enc(kSinv, r0 + s);
@@ -419,16 +441,14 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             }
         if (has_below) order[G++] = enc(kRinv, p);
         if (has_above) order[G++] = enc(kRinv, p - 1);
+        if (q2dnA) order[G++] = enc(kQ2L, p);
+        if (q2dnB) order[G++] = enc(kQ2L, p - 1);
+        if (q2upA) order[G++] = enc(kQ2U, p);
+        if (q2upB) order[G++] = enc(kQ2U, p - 1);
         nchunk = G;
         if (Q > 0) {
             G += chain_order(order + G, n1, [&](int i) { return q0 + i; });
-            if (dn2) order[G++] = enc(kP2L, q1);
-            if (up2) order[G++] = enc(kP2U, q0 - 1);
             ngroup = G - nchunk;
-            if (NG > 1) {
-                for (int i = 0; i < imin(n2, 64); ++i) l2s[i] = A.g.gq1[i];
-                G += chain_order(order + G, n2, [&](int i) { return i < 64 ? l2s[i] : A.g.gq1[i]; });
-            }
         }
         nload = G;
     }
@@ -441,14 +461,15 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         // only the CTA that solves the group uses those, the others let them land
         cap = nchunk + imin(4, ngroup);
         refill();
-        // the group's first chunk stages the group's separator chain in L2, chunk 0
-        // the level-2 chain, for whichever CTA ends up solving them
+        // the group's first chunk stages the group's separator chain in L2 for whichever
+        // CTA ends up solving it
         auto stage_l2 = [&](int from, int to) {
             for (int G = from + plane; G < to; G += 32) bulk_prefetch_l2(src_of(G), sb);
         };
-        if (Q > 0 && p == q0) stage_l2(nchunk, nchunk + ngroup);
-        if (NG > 1 && p == 0) stage_l2(nchunk + ngroup, nload);
+        if (!l2cta && Q > 0 && p == q0) stage_l2(nchunk, nchunk + ngroup);
         pdl_wait();
+    } else if (l2cta) {
+        pdl_wait();   // the counters and buffers of the previous strip solve are settled
     } else {
         // tables and the source part of the right-hand sides S^(j) r of the chunk
         // rows and of the separator row below (the source field is complete before
@@ -711,6 +732,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         pf();
         return finish();
     };
+    C* parts = reinterpret_cast<C*>(A.parts);
+    auto pidx = [&](int b, int q, int k) -> int64_t { return (((int64_t)(b0 + b) * Q + q) * kParts + k) * A.Wmax; };
+    C* acc2 = reinterpret_cast<C*>(A.acc2);
+    auto a2idx = [&](int b, int r) -> int64_t { return ((int64_t)(b0 + b) * imax(NG - 1, 1) + r) * A.Wmax; };
+    int* cnt = A.counters + (int64_t)tile * (NG + 1);   // group arrivals [0, NG), level-2 arrivals [NG]
+    if (!l2cta) {   // ---- the chunk (the level-2 CTA skips to the level-2 solve)
     // ---- forward elimination: both halves while both have rows, then the longer one
     //   down: z_kd, kd = r0+s; next input b_{kd+1} - C_{kd+1} z_kd (if kd+1 < t)
     //   up:   z_ku, ku = r1-1-s; next input b_{ku-1} - C_ku z_ku (if ku-1 > t)
@@ -798,8 +825,6 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         yrow<C>(A, b0 + b, r0 + r)[c] = zb[(r * BT + b) * W + c];
     }
     if (Q == 0) return;   // every load of the sequence has been consumed
-    C* parts = reinterpret_cast<C*>(A.parts);
-    auto pidx = [&](int b, int q, int k) -> int64_t { return (((int64_t)(b0 + b) * Q + q) * kParts + k) * A.Wmax; };
     // ---- separator right-hand-side parts, both in one step:
     //   down chain: A_p     = Rinv_p     (b_s - C_s y(last)),   s = r1      (separator below)
     //   up chain:   B_{p-1} = -Rinv_{p-1} C_{s'+1} y(first),     s' = r0 - 1 (separator above)
@@ -812,11 +837,45 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             if (b < nb && rowok && (b & 3) == g) {
                 if (has_below) parts[pidx(b, p, 0) + row] = vd[b];
                 if (has_above) parts[pidx(b, p - 1, 1) + row] = vu[b];
+                // the parts as the next step's inputs (vout becomes vin at the barrier)
+                vout_d[b * 64 + row] = has_below ? vd[b] : CT<C>::zero();
+                vout_u[b * 64 + row] = has_above ? vu[b] : CT<C>::zero();
             }
         if (!finish()) return;
     }
+    if (NG > 1) {
+        // ---- the chunk's contributions to the level-2 right-hand sides below (dn) and above
+        // (up) its group: Q2L/Q2U of separator p times A_p, of separator p-1 times B_{p-1}
+        C dn[BT], up[BT];
+        auto contrib = [&](bool a, bool b, C (&out)[BT]) {
+#pragma unroll
+            for (int bb = 0; bb < BT; ++bb) out[bb] = CT<C>::zero();
+            if (!a && !b) return;
+            const C *SA, *SB;
+            consume_ab(a, b, SA, SB);
+            // an absent term multiplies the zero vector with the other term's block
+            step2(a ? SA : SB, a ? vin_d : vzero, b ? SB : SA, b ? vin_u : vzero);
+#pragma unroll
+            for (int bb = 0; bb < BT; ++bb) out[bb] = cadd(vd[bb], vu[bb]);
+        };
+        contrib(q2dnA, q2dnB, dn);
+        contrib(q2upA, q2upB, up);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+            if (b < nb && rowok && (b & 3) == g) {
+                // to the level-2 separator below the group (its index is the group's) and above it;
+                // the sums come out in arrival order, so the level-2 right-hand sides agree
+                // between runs to rounding, not bitwise
+                const int gg = q2dnA || q2upA ? grp_of(p) : grp_of(p - 1);
+                if (q2dnA || q2dnB) catomic_add(acc2 + a2idx(b, gg) + row, dn[b]);
+                if (q2upA || q2upB) catomic_add(acc2 + a2idx(b, gg - 1) + row, up[b]);
+            }
+        if (!finish()) return;
+        // release: this CTA's parts and contributions (ordered before by the barrier)
+        if (tid == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(cnt + NG) : "memory");
+    }
+    }   // ---- end of the chunk
     // ---- arrival: the last chunk CTA of group gi (chunks gq0..gq1) solves its separators
-    int* cnt = A.counters + (int64_t)tile * (NG + 1);
     auto arrive = [&](int* ctr, int expect) -> bool {   // after a barrier; true on the last arrival
         if (tid == 0) {
             // release: this CTA's writes (ordered before by the barrier); acquire: the
@@ -832,11 +891,6 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         land(consumed);   // not the last: let the copies already issued land before leaving
         return false;
     };
-    if (!arrive(&cnt[gi], n1)) return;
-    if (pwarp) {   // the rest of the group chain, then the level-2 chain, stream in
-        cap = nload;
-        refill();
-    }
     auto zq = [&](int i) -> C* { return zb + i * BT * W; };
     // one separator step: out_i = z_i - product, stored to z_i and to the chain's next input
     //   first: the step's blocks are consumed here (later steps of a loop have their rows
@@ -914,8 +968,11 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                     const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
                     const int64_t pb = pidx(b, lvl == 1 ? q0 + i : (i < 64 ? l2s[i] : A.g.gq1[i]), 0) + c;
                     v[u] = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
-                    if (lvl == 2)
-                        v[u] = cadd(v[u], cadd(__ldcg(parts + pb + 2 * A.Wmax), __ldcg(parts + pb + 3 * A.Wmax)));
+                    if (lvl == 2) {   // the group separators' shares, then zero for the next launch
+                        C* ap = acc2 + a2idx(b, i) + c;
+                        v[u] = cadd(v[u], __ldcg(ap));
+                        *ap = CT<C>::zero();
+                    }
                 }
             }
 #pragma unroll
@@ -931,34 +988,47 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
         }
         asm volatile("bar.sync 1, %0;" ::"r"(ptid) : "memory");
     };
-    // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at
-    //      zero; level 2: the level-2 separators (one code path for both levels)
-    for (int lvl = 1; lvl <= 2; ++lvl) {
-        const int n = lvl == 1 ? n1 : n2;
-        load_a(n, lvl);
-        if (!chain(n)) return;
-        for (int o = tid; o < n * nb * W; o += blockDim.x) {
+    // ---- level 1: the group's separators q0 .. q1-1 with the level-2 separators at zero,
+    //      by the last chunk of the group to arrive
+    if (!l2cta) {
+        if (!arrive(&cnt[gi], n1)) return;
+        if (pwarp) {   // the rest of the group chain streams in
+            cap = nload;
+            refill();
+        }
+        load_a(n1, 1);
+        if (!chain(n1)) return;
+        for (int o = tid; o < n1 * nb * W; o += blockDim.x) {
             const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-            yrow<C>(A, b0 + b, A.g.r1[lvl == 1 ? q0 + i : (i < 64 ? l2s[i] : A.g.gq1[i])])[c] =
-                zb[(i * BT + b) * W + c];
+            yrow<C>(A, b0 + b, A.g.r1[q0 + i])[c] = zb[(i * BT + b) * W + c];
         }
-        if (lvl == 2 || NG == 1) return;
-        // the group's parts of the level-2 right-hand sides:
-        //   -P2L_{gi} y(last) to the separator below, -P2U_{gi-1} y(first) to the one above
-        {   // x_{n1-1} (pv_u) and x_0 (pv_d), left by the chain's last steps
-            const C *SL, *SU;
-            consume_ab(dn2, up2, SL, SU);
-            step2(dn2 ? SL : SU, dn2 ? pv_u : pv_d, up2 ? SU : SL, up2 ? pv_d : pv_u);
-#pragma unroll
-            for (int b = 0; b < BT; ++b)
-                if (b < nb && rowok && (b & 3) == g) {
-                    if (dn2) parts[pidx(b, q1, 2) + row] = cneg(vd[b]);
-                    if (up2) parts[pidx(b, q0 - 1, 3) + row] = cneg(vu[b]);
-                }
-            if (!finish()) return;
+        return;
+    }
+    // ---- level 2 (the level-2 CTA): once every chunk has added its contributions
+    if (tid == 0) {
+        const unsigned* c2 = reinterpret_cast<const unsigned*>(cnt + NG);
+        const unsigned target = (unsigned)P;   // every chunk's contributions are in
+        unsigned v = 0;
+        uint32_t it = 0;
+        for (; it < kWaitLimit; ++it) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c2) : "memory");
+            if (v >= target) break;
+            __nanosleep(64);
         }
-        // arrival: the last group to finish solves the level-2 system
-        if (!arrive(&cnt[NG], NG - 1)) return;
+        const bool ok = v >= target;
+        if (ok) cnt[NG] = 0;   // next used by a later launch (every chunk of this one has arrived)
+        flags[0] = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (flags[0]) {
+        abort_wait();
+        return;
+    }
+    load_a(n2, 2);
+    if (!chain(n2)) return;
+    for (int o = tid; o < n2 * nb * W; o += blockDim.x) {
+        const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
+        yrow<C>(A, b0 + b, A.g.r1[i < 64 ? l2s[i] : A.g.gq1[i]])[c] = zb[(i * BT + b) * W + c];
     }
 }
 
@@ -1117,6 +1187,16 @@ __global__ void __launch_bounds__(256, 2) k_sweep_output(OutArgs O, const C* __r
 }
 
 // ------------------------------------------------------------------ host
+// Bytes of the separator-parts region of a strip solve ([B][P-1][kParts][Wmax]); the
+// level-2 accumulators ([B][G-1][Wmax], sized for G - 1 <= P) follow it.
+size_t sweep_parts_bytes(int P, int B, int Wmax, size_t esize) {
+    return (size_t)B * std::max(P - 1, 1) * kParts * Wmax * esize;
+}
+size_t sweep_parts_total_bytes(int P, int B, int Wmax, size_t esize) {
+    return sweep_parts_bytes(P, B, Wmax, esize) + sweep_parts2_bytes(P, B, Wmax, esize);
+}
+size_t sweep_parts2_bytes(int P, int B, int Wmax, size_t esize) { return (size_t)B * std::max(P, 1) * Wmax * esize; }
+
 template <typename C>
 static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& step, const SweepWork& wk,
                            void* const* pool, int Bt, int ring) {
@@ -1134,10 +1214,11 @@ static SweepArgs make_args(const Geom& g, const StripDev& st, const SweepStep& s
     A.Rinv = pool[3];
     A.E = pool[4];
     A.F = pool[5];
-    A.P2L = g.G > 1 ? pool[8] : nullptr;
-    A.P2U = g.G > 1 ? pool[9] : nullptr;
+    A.Q2L = g.G > 1 ? pool[11] : nullptr;
+    A.Q2U = g.G > 1 ? pool[12] : nullptr;
     A.ybuf = wk.ybuf;
     A.parts = wk.parts;
+    A.acc2 = reinterpret_cast<char*>(wk.parts) + sweep_parts_bytes(g.P, wk.B, wk.Wmax, sizeof(C));
     A.has_prev = 0;
     A.pybuf = wk.pybuf;
     A.GT = pool[1];
@@ -1238,8 +1319,8 @@ cudaError_t launch_strip_solve(const Geom& g, int j, const StripDev& st, const S
             default: HELM_CHUNK_FN(16); break;
         }
 #undef HELM_CHUNK_FN
-        // compute warps + the producer warp
-        const cudaLaunchConfig_t cfg = config(dim3(g.P, ntile), 32 * ((st.W + 7) / 8 + 1), smem);
+        // compute warps + the producer warp; with separator groups one more CTA for level 2
+        const cudaLaunchConfig_t cfg = config(dim3(g.P + (g.G > 1 ? 1 : 0), ntile), 32 * ((st.W + 7) / 8 + 1), smem);
         TimedLaunch t(tm, "sweep_chunk", s);
         err = cudaLaunchKernelEx(&cfg, kfn, A);
     }

@@ -18,9 +18,12 @@ from paper_1208_3956_gb300 import helm, media
 
 pytestmark = pytest.mark.gpu
 
-# the FP64 preconditioner bar of the parity tests; mixed precision compares the
-# same complex64 kernels on the same inputs, so it is held to the same bar
-TOL = 1e-10
+# the FP64 preconditioner bar of the parity tests.  Both calls run the same kernels on the
+# same inputs; with separator groups the chunks add their shares of the level-2 right-hand
+# sides atomically, in arrival order, so the two results agree to rounding rather than
+# bitwise: complex64 unit roundoff 6e-8 over the about 20 shares of a level-2 entry gives
+# 1e-6 at most (8e-7 measured), held to 1e-5 in mixed precision
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
 
 
 def _problem(prec, chunks=5):
@@ -43,7 +46,7 @@ def test_noalloc_matches_apply_precond_on_two_calls(prec, chunks):
         got = g.apply_precond_noalloc(f, out=out)
         torch.cuda.synchronize()
         err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
-        assert err <= TOL, (call, err)
+        assert err <= TOL[prec], (call, err)
     g.close()
 
 
@@ -63,7 +66,7 @@ def test_noalloc_matches_apply_precond_3d(prec):
         got = g.apply_precond_noalloc(f, out=out)
         torch.cuda.synchronize()
         err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
-        assert err <= TOL, (call, err)
+        assert err <= TOL[prec], (call, err)
     g.close()
 
 
@@ -85,7 +88,7 @@ def test_noalloc_first_call_of_a_fresh_handle_allocates_nothing():
     assert free1 == free0, (free0, free1)
     ref = g.apply_precond(f)
     err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
-    assert err <= TOL, err
+    assert err <= TOL["mixed"], err
     g.close()
 
 
