@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
             for (int G = from + plane; G < to; G += 32) bulk_prefetch_l2(src_of(G), sb);
         };
         if (!l2cta && Q > 0 && p == q0) stage_l2(nchunk, nchunk + ngroup);
+        if (l2cta) stage_l2(ring, nload);   // the level-2 chain's blocks beyond the ring, into L2
         pdl_wait();
     } else if (l2cta) {
         pdl_wait();   // the counters and buffers of the previous strip solve are settled
@@ -835,8 +836,16 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
 #pragma unroll
         for (int b = 0; b < BT; ++b)
             if (b < nb && rowok && (b & 3) == g) {
-                if (has_below) parts[pidx(b, p, 0) + row] = vd[b];
-                if (has_above) parts[pidx(b, p - 1, 1) + row] = vu[b];
+                // a level-2 separator's parts go straight into its accumulator (the level-2
+                // CTA then reads one value per entry)
+                if (has_below) {
+                    if (NG > 1 && grp_of(p) < 0) catomic_add(acc2 + a2idx(b, -grp_of(p) - 1) + row, vd[b]);
+                    else parts[pidx(b, p, 0) + row] = vd[b];
+                }
+                if (has_above) {
+                    if (NG > 1 && grp_of(p - 1) < 0) catomic_add(acc2 + a2idx(b, -grp_of(p - 1) - 1) + row, vu[b]);
+                    else parts[pidx(b, p - 1, 1) + row] = vu[b];
+                }
                 // the parts as the next step's inputs (vout becomes vin at the barrier)
                 vout_d[b * 64 + row] = has_below ? vd[b] : CT<C>::zero();
                 vout_u[b * 64 + row] = has_above ? vu[b] : CT<C>::zero();
@@ -966,11 +975,12 @@ __global__ void __launch_bounds__(288) k_sweep_chunk(SweepArgs A) {
                 const int o = o0 + u * ptid;
                 if (o < tot) {
                     const int c = o % W, b = (o / W) % nb, i = o / (W * nb);
-                    const int64_t pb = pidx(b, lvl == 1 ? q0 + i : (i < 64 ? l2s[i] : A.g.gq1[i]), 0) + c;
-                    v[u] = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
-                    if (lvl == 2) {   // the group separators' shares, then zero for the next launch
+                    if (lvl == 1) {
+                        const int64_t pb = pidx(b, q0 + i, 0) + c;
+                        v[u] = cadd(__ldcg(parts + pb), __ldcg(parts + pb + A.Wmax));
+                    } else {   // the whole right-hand side, summed by the chunks; zero for the next launch
                         C* ap = acc2 + a2idx(b, i) + c;
-                        v[u] = cadd(v[u], __ldcg(ap));
+                        v[u] = __ldcg(ap);
                         *ap = CT<C>::zero();
                     }
                 }
