@@ -9,7 +9,7 @@ device.  Metric: Mdof*RHS/s = padded unknowns x right-hand sides / solve time.
 
 On one GPU the line also carries (each skippable with its --no-... flag):
   fp64_sweep         the same solve with complex128 factors and sweep, and the ratio
-  batched            panels of 4, 16, 32 sources on the same handle
+  batched            panels of 4, 16, 32 sources, each on a handle factored for its width
   concurrent_sweeps  upward and downward sequences at once, against the double sweep
   layered4095        the 4095^2 layered medium, 64 sources, reduced space (Algorithms 2-5)
   gradient_blob1023  misfit and adjoint gradient, 32 sources, 256 receivers
@@ -376,12 +376,15 @@ def media_mod():
     return media
 
 
-def run_batched(helm, torch, stream, solver, wl, args):
-    """The same handle on panels of B point sources (B = 4, 16, 32 on the top row of the
-    interior): solve throughput, iterations, and the preconditioner's roofline at that
-    panel width.  Algorithmic bytes of one P application on a panel: the factor bytes
-    once (they are shared by the panel) plus, per right-hand side, the vector traffic of
-    the strip solves (2J-1 solves of 2 N_y W_j words read and written twice)."""
+def run_batched(helm, torch, stream, solver, wl, c, omega, args):
+    """Panels of B point sources (B = 4, 16, 32 on the top row of the interior), each on a
+    handle factored with that panel width, so that the built-in chunk count fits the
+    panel's tiles of 4 into one wave of the SMs (the headline handle's partition, made
+    for one right-hand side, is timed beside it): solve throughput, iterations, and the
+    preconditioner's roofline at that panel width.  Algorithmic bytes of one P
+    application on a panel: the factor bytes once (they are shared by the panel) plus,
+    per right-hand side, the vector traffic of the strip solves (2J-1 solves of 2 N_y W_j
+    words read and written twice)."""
     media = media_mod()
     peaks = load_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
@@ -389,35 +392,50 @@ def run_batched(helm, torch, stream, solver, wl, args):
     Ws = solver.strip_widths()
     esize = 8 if solver.precision == "mixed" else 16
     vec_per_rhs = sum(2 * Ny * w * esize * 4 for w in Ws) + sum(2 * Ny * w * esize * 4 for w in Ws[:-1])
-    p_bytes = solver.precond_factor_bytes()
     out = {}
+
+    def time_precond(g, x, kp=3):
+        g.apply_precond(x)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(kp):
+            g.apply_precond(x)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / kp
+
     for B in (4, 16, 32):
+        x = torch.as_tensor(media.random_rhs((B,) + solver.shape, 6), device="cuda")
+        t_builtin = time_precond(solver, x)
+        gb = solver
+        if not args.chunks:
+            gb = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, args.precision, panel=B)
+            gb.set_stream(stream.cuda_stream)
+            gb.factor()
+        p_bytes = gb.precond_factor_bytes()
         pts = [((wl.n[0] * (2 * s + 1)) // (2 * B), 0) for s in range(B)]
         f = torch.as_tensor(media.point_sources(wl.n, wl.w_outer, wl.h, pts), device="cuda")
-        solver.solve(f, tol=1e-6, restart=20, maxit=200)
+        gb.solve(f, tol=1e-6, restart=20, maxit=200)
         k = 2
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record()
         for _ in range(k):
-            _, info = solver.solve(f, tol=1e-6, restart=20, maxit=200)
+            _, info = gb.solve(f, tol=1e-6, restart=20, maxit=200)
         ev[1].record()
-        x = torch.as_tensor(media.random_rhs((B,) + solver.shape, 6), device="cuda")
-        solver.apply_precond(x)
-        kp = 3
-        ev[2].record()
-        for _ in range(kp):
-            solver.apply_precond(x)
-        ev[3].record()
         torch.cuda.synchronize()
         t = ev[0].elapsed_time(ev[1]) / k
-        tp = ev[2].elapsed_time(ev[3]) / kp
+        tp = time_precond(gb, x)
         alg = p_bytes + B * vec_per_rhs
         out[f"B{B}"] = {"nrhs": B, "value": solver.ndof * B / (t * 1e-3) / 1e6, "unit": "Mdof*RHS/s",
                         "ms_per_solve": t, "steps": k, "iters": [i["iters"] for i in info],
                         "rel_res": max(i["rel_res"] for i in info),
+                        "chunks": gb.chunks(), "sep_groups": gb.sep_groups(),
+                        "precond_ms_headline_partition": t_builtin,
                         "roofline": {"bound": "hbm", "kernel": "sweep_chunk", "achieved": alg / (tp * 1e-3) / 1e9,
                                      "peak": hbm, "unit": "GB/s", "frac": alg / (tp * 1e-3) / 1e9 / hbm,
                                      "alg_bytes_per_precond": alg, "precond_ms": tp}}
+        if gb is not solver:
+            gb.close()
         del f, x
     return out
 
@@ -830,7 +848,7 @@ def run_ours(args):
 
     batched = None
     if world == 1 and not args.no_batched:
-        batched = run_batched(helm, torch, stream, solver, wl, args)
+        batched = run_batched(helm, torch, stream, solver, wl, c, omega, args)
 
     layered = None
     if world == 1 and not args.no_layered:

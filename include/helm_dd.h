@@ -107,7 +107,9 @@ helm_status helm_dd_set_pml_speed(helm_dd* h, double c_ref);
 
 /* Number of chunks P the y-axis of every strip is cut into for the partitioned
  * block-tridiagonal factorisation (1 = plain sequential block LU).  0 selects the
- * built-in choice.  Must be called before helm_dd_factor. */
+ * built-in choice: about 0.93 N_y^(2/3), lowered when a panel of more than 4
+ * right-hand sides is set before helm_dd_factor (helm_dd_set_panel) so that the
+ * panel's tiles of 4 fit one wave of the SMs.  Must be called before helm_dd_factor. */
 helm_status helm_dd_set_chunks(helm_dd* h, int P);
 
 /* Number of groups G the P-1 separator rows of every strip are cut into (a
@@ -122,13 +124,18 @@ helm_status helm_dd_set_sep_groups(helm_dd* h, int G);
 /* G in use after helm_dd_factor (0 before). */
 int helm_dd_sep_groups(const helm_dd* h);
 
+/* P in use after helm_dd_factor (0 before). */
+int helm_dd_chunks(const helm_dd* h);
+
 /* Most right-hand sides per internal panel of helm_dd_solve, helm_dd_solve_reduced
  * and helm_dd_gradient (the batching of many-source runs, not the paper's own
  * parameter): a call with more right-hand sides runs them panel after panel, so
  * that the Krylov basis (2 restart + 2 complex128 fields per right-hand side in
  * the full space) and the sweep buffers are held for one panel only.  A panel is
  * never wider than the free device memory holds; 0 (the default) sets no other
- * cap.  Results do not depend on the panel width beyond rounding. */
+ * cap.  Results do not depend on the panel width beyond rounding.  Set before
+ * helm_dd_factor, a width above 4 also lowers the built-in chunk count
+ * (helm_dd_set_chunks); after it, only the cap changes. */
 helm_status helm_dd_set_panel(helm_dd* h, int nrhs);
 
 /* Order of the strip solves of P (before helm_dd_factor; default HELM_SWEEP_DOUBLE).

@@ -41,12 +41,15 @@ def builtin_chunks(Ny: int) -> int:
     return max(1, min((Ny + 1) // 2, int(round(0.93 * Ny ** (2.0 / 3.0)))))
 
 
-def candidates(Ny: int, dim: int = 2) -> list:
-    """(P, G) pairs around the built-in choice: P at 0.7 .. 1.3 of it, G around sqrt(P-1)."""
+def candidates(Ny: int, dim: int = 2, nrhs: int = 1) -> list:
+    """(P, G) pairs around the built-in choice: P at 0.7 .. 1.3 of it, G around sqrt(P-1).
+    Panels of more than 4 right-hand sides run as several tiles of P+1 CTAs, which favour
+    fewer, longer chunks: their P range reaches down to a sixth of the built-in one."""
     if dim == 3:
         return [(0, 0)]
     P0 = builtin_chunks(Ny)
-    Ps = sorted({max(1, min((Ny + 1) // 2, int(round(P0 * f)))) for f in (0.7, 0.85, 1.0, 1.15, 1.3)})
+    fs = (0.7, 0.85, 1.0, 1.15, 1.3) if nrhs <= 4 else (1 / 6, 0.25, 0.375, 0.5, 0.7, 1.0)
+    Ps = sorted({max(1, min((Ny + 1) // 2, int(round(P0 * f)))) for f in fs})
     out = []
     for P in Ps:
         Q = P - 1
@@ -115,7 +118,7 @@ def tune(c, h, omega, w_outer, w_sub, J, precision="mixed", nrhs=1, reps=3, path
     measure = measure or time_apply
     tried = []
     best = None
-    for P, G in (cands if cands is not None else candidates(N[1], dim)):
+    for P, G in (cands if cands is not None else candidates(N[1], dim, nrhs)):
         solver = None
         try:
             solver = make_solver(P, G)

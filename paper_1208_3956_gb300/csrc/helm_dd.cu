@@ -240,6 +240,15 @@ void chunk_layout(helm_dd* h) {
     // factor 0.93 (fewer, longer chunks) is the measured optimum on a 1055-row grid,
     // where the chunk steps are slightly cheaper than the separator steps.
     int P = h->P_req > 0 ? h->P_req : std::max(1, (int)lround(0.93 * pow((double)Ny, 2.0 / 3.0)));
+    // A panel of B > 4 right-hand sides (set before the factorisation) runs each strip
+    // solve as ceil(B/4) tiles of P+1 CTAs (one SM each).  Once the tiles exceed one wave
+    // of the SMs they run one after another, so the built-in count drops to the P whose
+    // tiles all fit one wave, but not below a sixth of it (longer chunk chains).  On 1055
+    // rows this halves the time per right-hand side at B = 32 (P = 18 against 96).
+    if (h->P_req == 0 && h->panel > 4 && h->nsm > 0) {
+        const int tiles = (h->panel + 3) / 4;
+        P = std::min(P, std::max(h->nsm / tiles - 1, (P + 5) / 6));
+    }
     // concurrent sweeps run three strip solves side by side (one CTA per chunk and SM, and
     // one for the level-2 system)
     if (h->P_req == 0 && h->sweep == HELM_SWEEP_CONCURRENT && h->nsm >= 6) P = std::min(P, h->nsm / 3 - 1);
@@ -765,8 +774,11 @@ int helm_dd_sep_groups(const helm_dd* h) { return h && h->prepared ? h->G : 0; }
 helm_status helm_dd_set_panel(helm_dd* h, int nrhs) {
     if (!h || nrhs < 0) return HELM_EINVAL;
     h->panel = nrhs;
+    if (!h->factored) h->prepared = false;   // the built-in chunk count depends on it
     return HELM_OK;
 }
+
+int helm_dd_chunks(const helm_dd* h) { return h && h->prepared ? h->P : 0; }
 
 helm_status helm_dd_set_sweep(helm_dd* h, helm_sweep mode) {
     if (!h || (mode != HELM_SWEEP_DOUBLE && mode != HELM_SWEEP_CONCURRENT)) return HELM_EINVAL;

@@ -56,6 +56,7 @@ def load() -> ctypes.CDLL:
         "helm_dd_set_chunks": (I, [P, I]),
         "helm_dd_set_sep_groups": (I, [P, I]),
         "helm_dd_sep_groups": (I, [P]),
+        "helm_dd_chunks": (I, [P]),
         "helm_dd_set_panel": (I, [P, I]),
         "helm_dd_set_transmission": (I, [P, I]),
         "helm_dd_set_sweep": (I, [P, I]),
@@ -202,6 +203,10 @@ class HelmDD:
 
     def sep_groups(self) -> int:
         return int(self.lib.helm_dd_sep_groups(self._h))
+
+    def chunks(self) -> int:
+        """The chunk count P in use after factor (0 before)."""
+        return int(self.lib.helm_dd_chunks(self._h))
 
     def precond_factor_bytes(self) -> float:
         return float(self.lib.helm_dd_precond_factor_bytes(self._h))

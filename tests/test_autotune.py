@@ -18,6 +18,9 @@ def test_candidates_surround_the_builtin_partition():
     assert autotune.candidates(79, dim=3) == [(0, 0)]
     # tiny grids: chunk counts clamped to (Ny+1)/2
     assert all(P <= 5 for P, _ in autotune.candidates(9))
+    # wide panels: down to a sixth of the built-in count (one wave of 8 tiles needs P = 18)
+    wide = sorted({P for P, _ in autotune.candidates(Ny, nrhs=32)})
+    assert min(wide) == 16 and max(wide) == P0 and 24 in wide
 
 
 class _Fake:

@@ -154,6 +154,30 @@ def test_chunking_does_not_change_the_preconditioner():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_panel_width_lowers_the_builtin_chunks_and_matches_oracle(prec, tol):
+    """A panel of 32 right-hand sides set before the factorisation: the built-in chunk
+    count drops from about 0.93 N_y^(2/3) to the count whose 8 tiles of 4 fit one wave of
+    the SMs (at least a sixth of it), and P f on all 32 stays the oracle's."""
+    import torch
+    from paper_1208_3956_gb300 import autotune
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n, w_o, w_s, J = (60, 300), 6, 5, 4
+    c = media.smooth_medium(n, 3.0, 1.0, 2.0, 5)
+    h = 1.0 / 32
+    omega = media.omega_for(c, h, 8.0)
+    g = helm.HelmDD(c, h, omega, w_o, w_s, J, prec, panel=32)
+    o = HelmholtzDD(c, h, omega, w_o, w_s, J)
+    g.factor()
+    o.factor()
+    P0 = autotune.builtin_chunks(g.N[1])
+    assert g.chunks() == min(P0, max(nsm // 8 - 1, (P0 + 5) // 6)) < P0
+    f = media.random_rhs((32,) + g.shape, 21)
+    ref = np.stack([o.apply_precond(f[b]) for b in range(32)])
+    assert rel(g.apply_precond(f), ref) <= tol
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
 def test_separator_groups_match_oracle(prec, tol):
     """The two-level separator solve (groups plus a level-2 system) for several
     group counts, including groups of one separator, single and batched RHS."""
