@@ -666,8 +666,10 @@ def run_gradient(helm, torch, stream, args):
     blob, 32 sources and 256 receivers on the top row): observed data from the background
     medium (GPU solves at tol 1e-8), then the misfit 1/2 sum_s ||R u_s - d_s||^2 and its
     adjoint gradient with respect to 1/c^2 at the blob model (helm_dd_gradient, forward and
-    adjoint solves of all 32 sources in panels, tol 1e-6), mixed precision, PML held at the
-    background's maximum speed.  Metric: gradients per second (factor excluded)."""
+    adjoint solves of all 32 sources in one panel, tol 1e-6), mixed precision, PML held at
+    the background's maximum speed.  The panel width is set before the factorisation, so
+    the strip partition is the one made for 32 right-hand sides.  Metric: gradients per
+    second (factor excluded)."""
     media = media_mod()
     wl = media.WORKLOADS["blob1023"]
     c0 = media.background_medium("blob1023")
@@ -676,7 +678,7 @@ def run_gradient(helm, torch, stream, args):
     cref = float(c0.max())
     src = [media.padded_index(p, wl.n, wl.w_outer) for p in media.source_positions("blob1023")]
     rec = [media.padded_index(p, wl.n, wl.w_outer) for p in media.receiver_positions("blob1023")]
-    g0 = helm.HelmDD(c0, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref)
+    g0 = helm.HelmDD(c0, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref, panel=len(src))
     g0.set_stream(stream.cuda_stream)
     g0.factor()
     F = torch.zeros((len(src),) + g0.shape, dtype=torch.complex128, device="cuda")
@@ -687,7 +689,7 @@ def run_gradient(helm, torch, stream, args):
     d = u0.view(len(src), -1)[:, torch.as_tensor(rec, device="cuda")].cpu().numpy()
     g0.close()
     del F, u0
-    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref)
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", c_ref=cref, panel=len(src))
     g.set_stream(stream.cuda_stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
@@ -699,10 +701,12 @@ def run_gradient(helm, torch, stream, args):
     ev[3].record()
     torch.cuda.synchronize()
     t = ev[2].elapsed_time(ev[3])
+    P = g.chunks()
     g.close()
     return {"workload": "blob1023", "nsrc": len(src), "nrec": len(rec), "precision": "mixed", "tol": 1e-6,
             "value": 1e3 / t, "unit": "gradients/s", "ms_per_gradient": t, "factor_ms": ev[0].elapsed_time(ev[1]),
-            "solves_per_gradient": 2 * len(src), "misfit": J, "grad_norm": float(np.linalg.norm(grad))}
+            "solves_per_gradient": 2 * len(src), "chunks": P,
+            "misfit": J, "grad_norm": float(np.linalg.norm(grad))}
 
 
 def run_const127(helm, torch, stream, args):
