@@ -443,7 +443,8 @@ def run_batched(helm, torch, stream, solver, wl, c, omega, args):
 def run_layered(helm, torch, stream, args):
     """The 2-D layered workload (4095^2 interior, 4135^2 padded, J = 256 strips of 16
     columns, 16-point added layers, 20-point outer layer), complex64 factors: its 64
-    sources on the top row as one batch.  The autotuner picks the panel width (the
+    sources on the top row as one batch, on a handle factored for a 64-wide panel (the
+    built-in chunk count then fits the panel's 16 tiles).  The autotuner picks the panel width (the
     preconditioner's time per right-hand side on panels B = 1, 2, 4, .. 64), then the
     batch is solved in the reduced space (Algorithms 2-5, interface vectors of 2(J-1) N_y
     entries) and in the full space (flexible GMRES on the whole grid), both in panels of
@@ -454,7 +455,7 @@ def run_layered(helm, torch, stream, args):
     wl = media.WORKLOADS["layered4095"]
     c = media.medium("layered4095")
     omega = media.omega_for(c, wl.h, wl.ppw)
-    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed")
+    g = helm.HelmDD(c, wl.h, omega, wl.w_outer, wl.w_sub, wl.J, "mixed", panel=64)   # chunk count for 64 sources
     g.set_stream(stream.cuda_stream)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     e[0].record()
@@ -497,7 +498,7 @@ def run_layered(helm, torch, stream, args):
     alg = p_bytes + Bp * vec_per_rhs
     out = {"workload": "layered4095", "grid": "4095x4095 interior, 4135x4135 padded", "J": wl.J,
            "w_sub": wl.w_sub, "w_outer": wl.w_outer, "precision": "mixed", "nrhs": 64, "factor_ms": factor_ms,
-           "panel": Bp, "panel_tuning_ms_per_rhs": tuned["tried"],
+           "panel": Bp, "chunks": g.chunks(), "panel_tuning_ms_per_rhs": tuned["tried"],
            "roofline": {"bound": "hbm", "kernel": "sweep_chunk", "achieved": alg / (t_p * 1e-3) / 1e9, "peak": hbm,
                         "unit": "GB/s", "frac": alg / (t_p * 1e-3) / 1e9 / hbm, "alg_bytes_per_precond": alg,
                         "precond_ms": t_p, "panel": Bp}}
