@@ -77,6 +77,18 @@ def test_small_ragged_geometry(lib):
     s.close()
 
 
+def test_partition_queries_before_factor(lib):
+    """The chunk and group counts are 0 until the factorisation fixes them; the panel and
+    chunk setters accept their arguments before it (no GPU is touched)."""
+    c = np.full((29, 37), 1.5)
+    s = helm.HelmDD(c, 0.05, 3.0, 5, 4, 3, "fp64", panel=32)
+    assert s.chunks() == 0 and s.sep_groups() == 0
+    s.set_panel(8)
+    with pytest.raises(helm.HelmError):
+        s.set_panel(-1)
+    s.close()
+
+
 @pytest.mark.parametrize("bad", [
     dict(c=-1.0), dict(c=float("nan")), dict(omega=0.0), dict(J=0), dict(w_sub=0),
     dict(J=40),            # cores thinner than 2 columns
